@@ -1,0 +1,23 @@
+"""CPU oracle for the space-variant box-spline filter -- TEST INFRASTRUCTURE ONLY.
+
+This package is a plain, slow, obviously correct restatement of what the
+filter computes, written from the paper (Chaudhury & Sanyal, "Improvements on
+'Fast space-variant elliptical filtering using box splines'").  Only the
+tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+may import it.  The CUDA library never links, imports or calls anything here,
+and nothing here imports the CUDA library: the two share no code.
+
+Modules
+-------
+params    covariance <-> scale-vector geometry, the minimum-kurtosis scale
+          solve, step rounding, elongation bound e(phi).
+kernels   discrete box-spline kernels and the direct (definition) filter.
+modular   the paper's pipeline -- running sums, then finite differences --
+          in exact two's-complement modular arithmetic.
+gaussian  Gaussian-approximation errors of continuous box splines (Theorem 1,
+          Table 2) by Parseval.
+
+Parity status of each function is stated in its docstring; "parity unpinned"
+marks a function with no independent pin.
+"""
+from . import params, kernels, modular, gaussian  # noqa: F401
