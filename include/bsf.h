@@ -1,0 +1,209 @@
+/*
+ * bsf.h -- C ABI of the GB300 space-variant box-spline filter library (libbsf.so).
+ *
+ * The filter (Chaudhury & Sanyal, "Improvements on 'Fast space-variant
+ * elliptical filtering using box splines'", Section 1.1, the BoxFilter
+ * algorithm) runs in two steps:
+ *
+ *   1. pre-integration: n-fold running sums of the (extended, fixed-point)
+ *      image along each of the N = 4 grid directions d1 = (1,0), d2 = (1,1),
+ *      d3 = (0,1), d4 = (-1,1)  (x is the column, y the row);
+ *   2. a per-pixel finite difference of order n along every direction, with
+ *      integer steps L_k set by that pixel's covariance, so each output pixel
+ *      combines (n+1)^4 samples of the running sum:
+ *         out(p) = sum_t w_t S(p + sum_k (c_k - t_k L_k) d_k) / (2^q prod_k L_k^n),
+ *         w_t = prod_k (-1)^t_k C(n, t_k),  c_k = n (L_k - 1) / 2.
+ *
+ * The steps come from the minimum-kurtosis scale vector of the pixel's
+ * covariance (Section 1.1; kurtosis matrix of Section 2.3 read for the
+ * Cartesian directions), solved in float32 with a fixed sequence of IEEE
+ * operations, then L_k = admissible integer nearest to sqrt(1 + a_k^2/|d_k|^2).
+ *
+ * Arithmetic: the input is quantised once, Q(f) = round-half-even(f 2^q); the
+ * running sums and the taps are exact two's-complement integers modulo 2^64
+ * (BSF_FIX64) or 2^128 (BSF_FIX128); the wrap-around cancels in the
+ * differences whenever |Q| max * prod L^n < 2^(b-1), which the library
+ * checks.  The only rounding after Q is the final one:
+ *    float32 out: RN32(RN32(acc) 2^-q) / RN32(D)   (IEEE float32 divide)
+ *    float64 out: RN64(RN64(acc) 2^-q) / RN64(D)   (IEEE float64 divide)
+ * with D = prod_k L_k^n and RNxx round-to-nearest-even of an exact integer.
+ *
+ * Conventions for every entry point
+ *   - Pointers named "device" must point to device memory of the current
+ *     device; the caller owns them.  Images are row-major [H][ld] (ld >= W
+ *     elements).  Covariance fields are three contiguous float32 planes
+ *     [3][H][W]: (C11, C12, C22) for BSF_COV_C.
+ *   - The context owns its workspace (running sums S, step field, scan
+ *     carries, status word) and allocates it in bsf_create / bsf_plan only.
+ *   - Every call is asynchronous on the context's stream unless stated;
+ *     calls on one context must not run concurrently from several threads.
+ *   - Return value: BSF_OK (0) or a negative BSF_E* code; no exception
+ *     crosses the ABI.  bsf_last_error() gives a message for the last failure.
+ *   - Errors found on the device (covariance beyond the elongation bound,
+ *     taps beyond the padding, fixed-point overflow) are recorded in a device
+ *     status word and reported by bsf_status().
+ */
+#ifndef BSF_H
+#define BSF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define BSF_OK         0
+#define BSF_EINVAL    (-1)  /* bad argument */
+#define BSF_ENOMEM    (-2)  /* device allocation failed */
+#define BSF_ECUDA     (-3)  /* a CUDA runtime call failed */
+#define BSF_ERANGE    (-4)  /* a pixel's taps reach beyond the padding R */
+#define BSF_ETIMEOUT  (-5)  /* a bounded device wait expired */
+#define BSF_EOVERFLOW (-6)  /* max|Q(f)| * prod L^n does not fit the modulus */
+#define BSF_ESTATE    (-7)  /* call order: e.g. filter before any pre-integration */
+#define BSF_ECOV      (-8)  /* non-finite covariance entries (treated as zero) */
+
+/* boundary extension of the image beyond its borders (the paper is silent) */
+#define BSF_ZERO       0    /* f = 0 outside */
+#define BSF_REPLICATE  1    /* nearest border sample */
+#define BSF_SYMMETRIC  2    /* half-sample mirror: d c b a | a b c d */
+
+/* element types of images */
+#define BSF_U8   0
+#define BSF_F32  1
+#define BSF_F64  2
+
+/* precision of the running sums */
+#define BSF_FIX64   1       /* uint64 modular fixed point (8 B per element) */
+#define BSF_FIX128  2       /* uint128 modular fixed point (16 B per element) */
+
+/* covariance field encodings */
+#define BSF_COV_C   0       /* (C11, C12, C22) in px^2 */
+
+/* step rules */
+#define BSF_STEP_D1        0  /* L = admissible integer nearest sqrt(1 + a^2/|d|^2) */
+#define BSF_STEP_D1_PAPER  1  /* L = admissible integer nearest a/|d| (paper's step scaling) */
+
+/* phases timed by bsf_set_profiling / bsf_read_profile */
+#define BSF_PHASE_STEPS    0  /* per-pixel step solve */
+#define BSF_PHASE_ROWS     1  /* extension + quantisation + running sums along d1 */
+#define BSF_PHASE_D3       2  /* running sums along d3 (three kernels) */
+#define BSF_PHASE_D2       3  /* running sums along d2 (three kernels) */
+#define BSF_PHASE_D4       4  /* running sums along d4 (three kernels) */
+#define BSF_PHASE_STENCIL  5  /* finite differences + final rounding */
+#define BSF_NUM_PHASES     6
+
+/* device status flags reported through bsf_info_t.flags */
+#define BSF_FLAG_CLAMPED  1u  /* some covariance exceeded e(phi) and was clamped */
+
+typedef struct bsf_ctx* bsf_t;
+
+/* Sizes and state of a context (bsf_get_info). */
+typedef struct {
+  int H, W;            /* image size */
+  int N, n;            /* directions (4) and order (1..3) */
+  int boundary;        /* BSF_ZERO / BSF_REPLICATE / BSF_SYMMETRIC */
+  int R;               /* padding reach; -1 until planned */
+  int Hp, Wp;          /* padded domain (H + 2R) x (W + 2R) */
+  long long pitch;     /* elements per row of S */
+  int elem_bytes;      /* bytes per element of S (8 or 16) */
+  int precision;       /* BSF_FIX64 / BSF_FIX128 */
+  int frac_bits;       /* q in use (-1 = not yet resolved) */
+  int step_rule;       /* BSF_STEP_* */
+  int max_reach;       /* largest tap reach seen by the last plan/filter */
+  double max_mass;     /* largest prod_k L_k^n seen by the last plan/filter */
+  unsigned clamp_count;/* pixels clamped to the elongation bound, last call */
+  unsigned flags;      /* BSF_FLAG_* */
+  long long workspace_bytes;
+} bsf_info_t;
+
+/* Create a context for H x W images, N = 4 directions, order n in 1..3.
+ * boundary: BSF_ZERO / BSF_REPLICATE / BSF_SYMMETRIC.
+ * max_reach: padding R >= 0 (fixes the workspace now), or -1 to size it from
+ * the first covariance field seen (bsf_plan, or the first bsf_filter).
+ * Defaults: precision BSF_FIX64 with automatic q, step rule BSF_STEP_D1,
+ * stream 0.  Synchronous; allocates device memory.
+ * Errors: BSF_EINVAL (sizes, N != 4, n outside 1..3, boundary), BSF_ENOMEM. */
+int bsf_create(bsf_t* out, int H, int W, int N, int n, int boundary, int max_reach);
+
+/* Free the context and its workspace (synchronises its stream). NULL is a no-op. */
+void bsf_destroy(bsf_t h);
+
+/* Issue all later work on this cudaStream_t (NULL = the legacy default stream). */
+int bsf_set_stream(bsf_t h, void* stream);
+
+/* Choose the running-sum modulus and the number q of fractional bits of the
+ * fixed-point input.  frac_bits in [0, 62] (BSF_FIX64) or [0, 100] (BSF_FIX128)
+ * fixes q; -1 chooses the largest q (at most b - 28) with
+ * (max|f| 2^q) * max prod L^n < 2^(b-2), from the value bound (see
+ * bsf_set_value_bound; uint8 images use 255; float images without a declared
+ * bound are reduced on the device, which synchronises) and the mass bound of
+ * the last plan.  Errors: BSF_EINVAL. */
+int bsf_set_precision(bsf_t h, int mode, int frac_bits);
+
+/* Declare max |f| of the images to come (used by automatic q; no sync). */
+int bsf_set_value_bound(bsf_t h, double max_abs);
+
+/* BSF_STEP_D1 (default) or BSF_STEP_D1_PAPER. */
+int bsf_set_step_rule(bsf_t h, int rule);
+
+/* Solve the steps of a covariance field (device, [3][H][W] float32), then
+ * synchronise: if the context was created with max_reach = -1, set R to the
+ * largest tap reach and allocate the running-sum workspace.  Also records the
+ * largest kernel mass for automatic q.  Errors: BSF_EINVAL, BSF_ENOMEM,
+ * BSF_ECUDA. */
+int bsf_plan(bsf_t h, const float* cov, int cov_kind);
+
+/* Pre-integration (step 1): extend the device image img ([H][ld], dtype
+ * BSF_U8 / BSF_F32 / BSF_F64) by the boundary rule onto the padded domain,
+ * quantise it, and run the n-fold running sums along d1, d3, d2, d4 into the
+ * context's workspace.  Requires R (max_reach or a plan).
+ * Errors: BSF_EINVAL, BSF_ESTATE (no R yet), BSF_ECUDA. */
+int bsf_preintegrate(bsf_t h, const void* img, int dtype, long long ld);
+
+/* Whole forward filter.  img != NULL: pre-integrate it first (as
+ * bsf_preintegrate; plans on the fly, synchronously, when R is not known);
+ * img == NULL: reuse the last pre-integration.  cov: device [3][H][W] float32.
+ * out: device [H][ldo] of out_dtype BSF_F32 or BSF_F64.
+ * Errors: BSF_EINVAL, BSF_ESTATE, BSF_ECUDA; device-side problems go to bsf_status. */
+int bsf_filter(bsf_t h, const void* img, int dtype, long long ld,
+               const float* cov, int cov_kind, void* out, int out_dtype, long long ldo);
+
+/* Synchronise the stream and return the first device-side error recorded
+ * since the last call (BSF_ERANGE, BSF_EOVERFLOW, BSF_ECOV) or BSF_OK, then
+ * clear it.  Refreshes the counters in bsf_get_info. */
+int bsf_status(bsf_t h);
+
+/* Message describing the last failure on this context (never NULL). */
+const char* bsf_last_error(bsf_t h);
+
+/* Fill *info (host pointer).  Does not synchronise. */
+int bsf_get_info(bsf_t h, bsf_info_t* info);
+
+/* Copy the integer step field of the last plan/filter into dst (device,
+ * uint16 [4][H][W]: L1, L2, L3, L4 planes).  For tests and diagnostics. */
+int bsf_copy_steps(bsf_t h, uint16_t* dst);
+
+/* Copy the running sums S of the last pre-integration into dst (device,
+ * [Hp][Wp] elements of elem_bytes each, row-major, no pitch padding).
+ * For tests and diagnostics. */
+int bsf_copy_preintegrated(bsf_t h, void* dst);
+
+/* Time every kernel phase with CUDA events recorded on the context's stream
+ * (on != 0), or stop (0).  Up to 4096 phase executions are kept between two
+ * bsf_read_profile calls; later ones are counted as dropped.
+ * Errors: BSF_ECUDA (event creation). */
+int bsf_set_profiling(bsf_t h, int on);
+
+/* Synchronise, then write per phase (BSF_PHASE_*) the summed device time in
+ * milliseconds (ms[BSF_NUM_PHASES]) and the number of executions
+ * (count[BSF_NUM_PHASES]) since the last read, and reset them.  Host arrays;
+ * either may be NULL.  Returns the number of dropped executions (>= 0) or an
+ * error code. */
+int bsf_read_profile(bsf_t h, double* ms, int* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSF_H */

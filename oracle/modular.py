@@ -226,7 +226,12 @@ def filter_modular(f: np.ndarray, cov: np.ndarray, n: int, boundary: int, q: int
     H, W = f.shape
     L, flags = params.integer_steps(cov[0], cov[1], cov[2], n, rule)
     if R is None:
-        R = int(params.reach(L, n).max(initial=0))
+        R = max(int(params.reach(L, n).max(initial=0)), 3 * n)
+    else:
+        # a pixel whose taps would leave the padded domain falls back to the
+        # identity steps (the library reports it as out of reach)
+        far = params.reach(L, n) > R
+        L = np.where(far[None], 1, L)
     fq = quantize(f, q, as_object=(bits == 128))
     fe = extend_image(fq, R, boundary)
     S = preintegrate(fe, n, bits)

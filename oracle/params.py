@@ -205,6 +205,7 @@ def solve_scales_f32(C11, C12, C22, n: int):
        monotonically; four steps are taken.
     4. u is clamped into the feasible interval [|b|, min(c1, c3)] and
        A1 = c1 - u, A2 = u + b, A3 = c3 - u, A4 = u - b (each floored at 0).
+       Minimum and maximum ignore a NaN operand (C fminf/fmaxf semantics).
     Returns (A[4, ...] float32, flags int32).
     Pinned by tests: against solve_scales_bruteforce, the isotropic closed form
     A_k = 6 sigma^2 / n, and covariance_of_scales(sqrt(A)) == C.
@@ -218,9 +219,9 @@ def solve_scales_f32(C11, C12, C22, n: int):
     bad = ~(np.isfinite(c11) & np.isfinite(c12) & np.isfinite(c22))
     flags[bad] |= BAD_FLAG
     c11[bad] = 0; c12[bad] = 0; c22[bad] = 0
-    c11 = np.maximum(c11, _F(0))
-    c22 = np.maximum(c22, _F(0))
-    m = np.minimum(c11, c22)
+    c11 = np.fmax(c11, _F(0))
+    c22 = np.fmax(c22, _F(0))
+    m = np.fmin(c11, c22)
     over = np.abs(c12) > m
     flags[over] |= CLAMP_FLAG
     c12 = np.where(over, np.copysign(m, c12), c12).astype(_F)
@@ -244,10 +245,10 @@ def solve_scales_f32(C11, C12, C22, n: int):
             v = np.where(dh > 0, v - h / np.where(dh > 0, dh, _F(1)), v).astype(_F)
     u = _F(0.25) * s + v
     lo = np.abs(b)
-    hi = np.minimum(c1, c3)
-    u = np.minimum(np.maximum(u, lo), hi)
-    A = np.stack([np.maximum(c1 - u, _F(0)), np.maximum(u + b, _F(0)),
-                  np.maximum(c3 - u, _F(0)), np.maximum(u - b, _F(0))]).astype(_F)
+    hi = np.fmin(c1, c3)
+    u = np.fmin(np.fmax(u, lo), hi)
+    A = np.stack([np.fmax(c1 - u, _F(0)), np.fmax(u + b, _F(0)),
+                  np.fmax(c3 - u, _F(0)), np.fmax(u - b, _F(0))]).astype(_F)
     return A, flags
 
 
@@ -282,13 +283,13 @@ def round_steps(lam, n: int) -> np.ndarray:
     n(L-1)/2 lies on the grid).  n odd: L = 2 floor(lambda/2) + 1;
     n even: L = floor(lambda + 1/2).  Capped at L_MAX.
     """
-    lam = np.minimum(np.asarray(lam, dtype=_F), _F(L_MAX))
+    lam = np.fmin(np.asarray(lam, dtype=_F), _F(L_MAX))
     if n % 2 == 1:
         L = _F(2) * np.floor(_F(0.5) * lam) + _F(1)
     else:
         L = np.floor(lam + _F(0.5))
-    L = np.maximum(L, _F(1))
-    return np.minimum(L, _F(L_MAX)).astype(np.int64)
+    L = np.fmax(L, _F(1))
+    return np.fmin(L, _F(L_MAX)).astype(np.int64)
 
 
 def integer_steps(C11, C12, C22, n: int, rule: str = "corrected"):

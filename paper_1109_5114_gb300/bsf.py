@@ -1,0 +1,228 @@
+"""ctypes binding of libbsf.so: the C ABI of include/bsf.h under the same names.
+
+Argument marshalling only: every step of the filter runs in the library's
+CUDA kernels.  Importing this module loads the library and fails loudly when
+it has not been built (there is no CPU fallback).  The ``BoxSplineFilter``
+class wraps a context for torch tensors (device memory and the current
+stream come from torch; torch does no arithmetic of the filter).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_PKG)
+LIB_PATH = os.path.join(_PKG, "lib", "libbsf.so")
+HEADER = os.path.join(_ROOT, "include", "bsf.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"libbsf.so is not built ({LIB_PATH}); run paper_1109_5114_gb300.build.build() "
+        "(nvcc for sm_103a). The filter has no CPU path.")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+
+def _constants_from_header(path: str) -> dict:
+    consts = {}
+    with open(path) as fh:
+        for line in fh:
+            m = re.match(r"#define\s+(BSF_\w+)\s+\(?(-?\d+)u?\)?", line)
+            if m:
+                consts[m.group(1)] = int(m.group(2))
+    return consts
+
+
+_C = _constants_from_header(HEADER)
+globals().update(_C)
+
+bsf_t = ctypes.c_void_p
+c_int, c_ll, c_void_p, c_double = ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_double
+
+
+class bsf_info_t(ctypes.Structure):
+    _fields_ = [("H", c_int), ("W", c_int), ("N", c_int), ("n", c_int), ("boundary", c_int),
+                ("R", c_int), ("Hp", c_int), ("Wp", c_int), ("pitch", c_ll),
+                ("elem_bytes", c_int), ("precision", c_int), ("frac_bits", c_int),
+                ("step_rule", c_int), ("max_reach", c_int), ("max_mass", c_double),
+                ("clamp_count", ctypes.c_uint), ("flags", ctypes.c_uint),
+                ("workspace_bytes", c_ll)]
+
+
+def _fn(name, restype, *argtypes):
+    f = getattr(_lib, name)
+    f.restype = restype
+    f.argtypes = list(argtypes)
+    return f
+
+
+bsf_create = _fn("bsf_create", c_int, ctypes.POINTER(bsf_t), c_int, c_int, c_int, c_int, c_int, c_int)
+bsf_destroy = _fn("bsf_destroy", None, bsf_t)
+bsf_set_stream = _fn("bsf_set_stream", c_int, bsf_t, c_void_p)
+bsf_set_precision = _fn("bsf_set_precision", c_int, bsf_t, c_int, c_int)
+bsf_set_value_bound = _fn("bsf_set_value_bound", c_int, bsf_t, c_double)
+bsf_set_step_rule = _fn("bsf_set_step_rule", c_int, bsf_t, c_int)
+bsf_plan = _fn("bsf_plan", c_int, bsf_t, c_void_p, c_int)
+bsf_preintegrate = _fn("bsf_preintegrate", c_int, bsf_t, c_void_p, c_int, c_ll)
+bsf_filter = _fn("bsf_filter", c_int, bsf_t, c_void_p, c_int, c_ll, c_void_p, c_int, c_void_p, c_int, c_ll)
+bsf_status = _fn("bsf_status", c_int, bsf_t)
+bsf_last_error = _fn("bsf_last_error", ctypes.c_char_p, bsf_t)
+bsf_get_info = _fn("bsf_get_info", c_int, bsf_t, ctypes.POINTER(bsf_info_t))
+bsf_copy_steps = _fn("bsf_copy_steps", c_int, bsf_t, c_void_p)
+bsf_copy_preintegrated = _fn("bsf_copy_preintegrated", c_int, bsf_t, c_void_p)
+bsf_set_profiling = _fn("bsf_set_profiling", c_int, bsf_t, c_int)
+bsf_read_profile = _fn("bsf_read_profile", c_int, bsf_t, ctypes.POINTER(c_double), ctypes.POINTER(c_int))
+
+ERROR_NAMES = {v: k for k, v in _C.items() if k.startswith("BSF_E")}
+
+
+class BsfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def check(h, rc: int) -> None:
+    if rc != 0:
+        msg = bsf_last_error(h).decode() if h else ""
+        raise BsfError(rc, msg)
+
+
+def declared_symbols(header: str = HEADER):
+    """Names of the functions include/bsf.h declares."""
+    with open(header) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bsf_\w+)\s*\(", text)))
+
+
+# --------------------------------------------------------------------------
+# torch convenience wrapper
+# --------------------------------------------------------------------------
+
+_DTYPES = None
+
+
+def _dtype_code(t) -> int:
+    import torch
+    global _DTYPES
+    if _DTYPES is None:
+        _DTYPES = {torch.uint8: BSF_U8, torch.float32: BSF_F32, torch.float64: BSF_F64}  # noqa: F821
+    return _DTYPES[t.dtype]
+
+
+_BOUNDARY = {"zero": 0, "replicate": 1, "symmetric": 2}
+
+
+class BoxSplineFilter:
+    """One library context for H x W images of order n on the current CUDA device.
+
+    filter(img, cov, out_dtype) runs the whole forward pass on torch's current
+    stream: step solve, extension + quantisation + running sums, finite
+    differences.  img: [H][W] uint8/float32/float64 CUDA tensor; cov: [3][H][W]
+    float32 CUDA tensor (C11, C12, C22).
+    """
+
+    def __init__(self, H: int, W: int, n: int, boundary="symmetric", max_reach: int = -1,
+                 precision: int = 1, frac_bits: int = -1, value_bound=None, step_rule: int = 0):
+        if isinstance(boundary, str):
+            boundary = _BOUNDARY[boundary]
+        self.H, self.W, self.n = H, W, n
+        h = bsf_t()
+        rc = bsf_create(ctypes.byref(h), H, W, 4, n, boundary, max_reach)
+        if rc != 0:
+            raise BsfError(rc, "bsf_create")
+        self._h = h
+        check(h, bsf_set_precision(h, precision, frac_bits))
+        check(h, bsf_set_step_rule(h, step_rule))
+        if value_bound is not None:
+            check(h, bsf_set_value_bound(h, float(value_bound)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            bsf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _stream(self):
+        import torch
+        check(self._h, bsf_set_stream(self._h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+
+    def plan(self, cov):
+        self._stream()
+        assert cov.is_cuda and cov.dtype.is_floating_point and cov.is_contiguous()
+        check(self._h, bsf_plan(self._h, ctypes.c_void_p(cov.data_ptr()), 0))
+        return self.info()
+
+    def filter(self, img, cov, out=None, out_dtype=None):
+        import torch
+        self._stream()
+        H, W = self.H, self.W
+        assert img is None or (img.is_cuda and img.shape == (H, W) and img.stride(1) == 1)
+        assert cov.is_cuda and cov.dtype == torch.float32 and cov.shape == (3, H, W) and cov.is_contiguous()
+        if out is None:
+            out = torch.empty((H, W), dtype=out_dtype or torch.float32, device=cov.device)
+        oc = BSF_F32 if out.dtype == torch.float32 else BSF_F64  # noqa: F821
+        if img is None:
+            rc = bsf_filter(self._h, None, 0, W, ctypes.c_void_p(cov.data_ptr()), 0,
+                            ctypes.c_void_p(out.data_ptr()), oc, out.stride(0))
+        else:
+            rc = bsf_filter(self._h, ctypes.c_void_p(img.data_ptr()), _dtype_code(img), img.stride(0),
+                            ctypes.c_void_p(cov.data_ptr()), 0, ctypes.c_void_p(out.data_ptr()), oc,
+                            out.stride(0))
+        check(self._h, rc)
+        return out
+
+    def preintegrate(self, img):
+        self._stream()
+        check(self._h, bsf_preintegrate(self._h, ctypes.c_void_p(img.data_ptr()), _dtype_code(img),
+                                        img.stride(0)))
+
+    def set_profiling(self, on: bool = True):
+        check(self._h, bsf_set_profiling(self._h, 1 if on else 0))
+
+    def read_profile(self):
+        """{phase name: (total ms, executions)} since the last read (syncs)."""
+        n = BSF_NUM_PHASES  # noqa: F821
+        ms = (c_double * n)()
+        cnt = (c_int * n)()
+        rc = bsf_read_profile(self._h, ms, cnt)
+        if rc < 0:
+            check(self._h, rc)
+        names = ["steps", "rows", "d3", "d2", "d4", "stencil"]
+        return {names[i]: (ms[i], cnt[i]) for i in range(n)}
+
+    def status(self) -> int:
+        return bsf_status(self._h)
+
+    def info(self) -> bsf_info_t:
+        inf = bsf_info_t()
+        check(self._h, bsf_get_info(self._h, ctypes.byref(inf)))
+        return inf
+
+    def steps(self):
+        import torch
+        dst = torch.empty((4, self.H, self.W), dtype=torch.int16, device="cuda")
+        self._stream()
+        check(self._h, bsf_copy_steps(self._h, ctypes.c_void_p(dst.data_ptr())))
+        return dst.view(torch.uint16) if hasattr(torch, "uint16") else dst
+
+    def preintegrated(self):
+        import torch
+        inf = self.info()
+        nb = inf.Hp * inf.Wp * inf.elem_bytes
+        dst = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        self._stream()
+        check(self._h, bsf_copy_preintegrated(self._h, ctypes.c_void_p(dst.data_ptr())))
+        return dst, inf

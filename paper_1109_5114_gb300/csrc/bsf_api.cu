@@ -1,0 +1,465 @@
+// C ABI of libbsf.so (declared in include/bsf.h): contexts, workspace,
+// argument checking, the order of the kernel launches, and the status word.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstddef>
+#include <cstring>
+#include <new>
+
+#include "bsf_internal.h"
+
+struct bsf_ctx {
+  int H = 0, W = 0, N = 4, n = 1, boundary = BSF_SYMMETRIC;
+  int R = -1;               // padding; -1 until known
+  bool R_fixed = false;     // given at create
+  int precision = BSF_FIX64;
+  int frac_req = -1;        // requested q (-1 = automatic)
+  int q = -1;               // q of the current pre-integration
+  int step_rule = BSF_STEP_D1;
+  bool has_bound = false;
+  double value_bound = 0.0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+
+  int Hp = 0, Wp = 0;
+  long long pitch = 0;
+  int elem = 8;
+  void* S = nullptr;
+  size_t S_bytes = 0;
+  void* agg = nullptr;
+  void* carry = nullptr;
+  size_t scan_bytes = 0;
+  ushort4* Lf = nullptr;
+  DevStatus* st = nullptr;
+  DevStatus host_st{};
+
+  bool planned = false;      // a step solve has set R and the mass bound
+  double plan_mass = 1.0;    // largest prod L^n of the plan
+  bool have_S = false;       // S holds a pre-integration made with (R, elem, q)
+  int S_R = -1, S_elem = 0, S_q = -1;
+  char msg[512] = "ok";
+
+  // phase timing (bsf_set_profiling)
+  static constexpr int kMaxRec = 4096;
+  bool profiling = false;
+  cudaEvent_t* ev = nullptr;   // 2 * kMaxRec events
+  int rec_phase[kMaxRec];
+  int nrec = 0;
+  int dropped = 0;
+};
+
+namespace {
+
+int fail(bsf_t h, int code, const char* fmt, ...) {
+  if (h) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(h->msg, sizeof(h->msg), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+int cuda_fail(bsf_t h, cudaError_t e, const char* where) {
+  return fail(h, e == cudaErrorMemoryAllocation ? BSF_ENOMEM : BSF_ECUDA, "%s: %s", where,
+              cudaGetErrorString(e));
+}
+
+#define BSF_CUDA(h, call)                                  \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+  } while (0)
+
+size_t elem_bytes_of(int precision) { return precision == BSF_FIX128 ? 16 : 8; }
+
+void free_workspace(bsf_t h) {
+  if (h->S) cudaFree(h->S);
+  if (h->agg) cudaFree(h->agg);
+  if (h->carry) cudaFree(h->carry);
+  h->S = h->agg = h->carry = nullptr;
+  h->S_bytes = h->scan_bytes = 0;
+  h->have_S = false;
+}
+
+// (Re)allocate S and the scan carries for the current R and precision.
+int ensure_workspace(bsf_t h) {
+  const int elem = (int)elem_bytes_of(h->precision);
+  const int Hp = h->H + 2 * h->R, Wp = h->W + 2 * h->R;
+  const long long align = 256 / elem;  // 256-byte aligned rows
+  const long long pitch = (Wp + align - 1) / align * align;
+  const size_t S_bytes = (size_t)pitch * Hp * elem;
+  const int nchunks = (Hp + kScanChunk - 1) / kScanChunk;
+  const size_t scan_bytes = (size_t)nchunks * h->n * (size_t)(Wp + Hp - 1) * elem;
+  if (h->S && h->S_bytes == S_bytes && h->scan_bytes == scan_bytes && h->Hp == Hp &&
+      h->Wp == Wp && h->elem == elem)
+    return BSF_OK;
+  BSF_CUDA(h, cudaStreamSynchronize(h->stream));
+  free_workspace(h);
+  BSF_CUDA(h, cudaMalloc(&h->S, S_bytes));
+  BSF_CUDA(h, cudaMalloc(&h->agg, scan_bytes));
+  BSF_CUDA(h, cudaMalloc(&h->carry, scan_bytes));
+  h->S_bytes = S_bytes;
+  h->scan_bytes = scan_bytes;
+  h->Hp = Hp;
+  h->Wp = Wp;
+  h->pitch = pitch;
+  h->elem = elem;
+  return BSF_OK;
+}
+
+int read_status(bsf_t h) {
+  BSF_CUDA(h, cudaMemcpyAsync(&h->host_st, h->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
+  BSF_CUDA(h, cudaStreamSynchronize(h->stream));
+  return BSF_OK;
+}
+
+double bits_to_double(unsigned long long b) {
+  double d;
+  std::memcpy(&d, &b, sizeof d);
+  return d;
+}
+
+double bits_to_float(unsigned b) {
+  float f;
+  std::memcpy(&f, &b, sizeof f);
+  return (double)f;
+}
+
+// Per-call counters and maxima start from zero; the first error code is kept
+// until bsf_status() reads it.
+int reset_counters(bsf_t h, bool steps, bool values) {
+  if (steps) {  // clamp/bad/range/overflow counts, max_reach, max_mass (0.0 bits)
+    const size_t a = offsetof(DevStatus, clamp_count);
+    const size_t b = offsetof(DevStatus, max_mass_bits) + sizeof(unsigned long long);
+    BSF_CUDA(h, cudaMemsetAsync(reinterpret_cast<char*>(h->st) + a, 0, b - a, h->stream));
+  }
+  if (values) {  // max |Q|
+    BSF_CUDA(h, cudaMemsetAsync(&h->st->max_absq_bits, 0, sizeof(unsigned long long), h->stream));
+  }
+  return BSF_OK;
+}
+
+// Scoped CUDA-event bracket of one phase execution on the context's stream.
+struct PhaseTimer {
+  bsf_t h;
+  int slot = -1;
+  PhaseTimer(bsf_t h_, int phase) : h(h_) {
+    if (!h->profiling) return;
+    if (h->nrec >= bsf_ctx::kMaxRec) { ++h->dropped; return; }
+    slot = h->nrec++;
+    h->rec_phase[slot] = phase;
+    cudaEventRecord(h->ev[2 * slot], h->stream);
+  }
+  ~PhaseTimer() {
+    if (slot >= 0) cudaEventRecord(h->ev[2 * slot + 1], h->stream);
+  }
+};
+
+int check_cov_kind(bsf_t h, int cov_kind) {
+  if (cov_kind != BSF_COV_C) return fail(h, BSF_EINVAL, "unsupported cov_kind %d", cov_kind);
+  return BSF_OK;
+}
+
+// Step solve over the field; sets R and the mass bound (with a sync) when R is
+// not yet known.
+int run_steps(bsf_t h, const float* cov, int cov_kind, bool sync_plan) {
+  int rc = check_cov_kind(h, cov_kind);
+  if (rc) return rc;
+  if (!cov) return fail(h, BSF_EINVAL, "cov is NULL");
+  if ((rc = reset_counters(h, true, false))) return rc;
+  // a plan of a context without a fixed R solves unbounded and resizes R
+  const bool bounded = h->R_fixed || (h->planned && !sync_plan);
+  cudaError_t e;
+  {
+    PhaseTimer t(h, BSF_PHASE_STEPS);
+    e = bsf_launch_steps(cov, cov_kind, h->H, h->W, h->n, h->step_rule, bounded ? h->R : -1,
+                         h->Lf, h->st, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "steps kernel");
+  if (sync_plan) {
+    if ((rc = read_status(h))) return rc;
+    h->plan_mass = bits_to_float(h->host_st.max_mass_bits);
+    if (!h->R_fixed) {
+      // the solve ran unbounded: every tap of this field fits this R
+      h->R = h->host_st.max_reach > 3 * h->n ? h->host_st.max_reach : 3 * h->n;
+    }
+    h->planned = true;
+    if ((rc = ensure_workspace(h))) return rc;
+  }
+  return BSF_OK;
+}
+
+// Choose q for this pre-integration.
+int resolve_q(bsf_t h, const void* img, int dtype, long long ld) {
+  const int b = h->precision == BSF_FIX128 ? 128 : 64;
+  if (h->frac_req >= 0) {
+    h->q = h->frac_req;
+    return BSF_OK;
+  }
+  double vmax;
+  if (dtype == BSF_U8) {
+    vmax = 255.0;
+  } else if (h->has_bound) {
+    vmax = h->value_bound;
+  } else {
+    BSF_CUDA(h, cudaMemsetAsync(&h->st->max_absf_bits, 0, sizeof(unsigned long long), h->stream));
+    cudaError_t e = bsf_launch_absmax(img, dtype, ld, h->H, h->W, h->st, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "absmax kernel");
+    int rc = read_status(h);
+    if (rc) return rc;
+    vmax = bits_to_double(h->host_st.max_absf_bits);
+    if (!(vmax == vmax)) return fail(h, BSF_EINVAL, "image contains NaN");
+  }
+  // largest q with (vmax 2^q + 1/2) * mass < 2^(b-2)
+  if (!h->planned)
+    return fail(h, BSF_ESTATE, "automatic q needs the mass bound of a plan (bsf_plan) or explicit frac_bits");
+  const double mass = h->plan_mass > 1.0 ? h->plan_mass : 1.0;
+  const double lv = std::log2(vmax > 1e-300 ? vmax : 1e-300);
+  const double lm = std::log2(mass);
+  int q = (int)std::floor((b - 2) - lv - lm) - 1;
+  if (q > b - 28) q = b - 28;
+  if (q < 0) q = 0;
+  h->q = q;
+  return BSF_OK;
+}
+
+int preintegrate_impl(bsf_t h, const void* img, int dtype, long long ld) {
+  if (!img) return fail(h, BSF_EINVAL, "img is NULL");
+  if (dtype != BSF_U8 && dtype != BSF_F32 && dtype != BSF_F64)
+    return fail(h, BSF_EINVAL, "bad image dtype %d", dtype);
+  if (ld < h->W) return fail(h, BSF_EINVAL, "ld %lld < W %d", ld, h->W);
+  if (h->R < 0) return fail(h, BSF_ESTATE, "padding unknown: give max_reach or call bsf_plan");
+  int rc;
+  if ((rc = ensure_workspace(h))) return rc;
+  if ((rc = resolve_q(h, img, dtype, ld))) return rc;
+  if ((rc = reset_counters(h, false, true))) return rc;
+  cudaError_t e;
+  {
+    PhaseTimer t(h, BSF_PHASE_ROWS);
+    e = bsf_launch_scan_rows(h->elem, h->n, img, dtype, ld, h->H, h->W, h->R, h->boundary, h->q,
+                             h->S, h->pitch, h->Hp, h->Wp, h->st, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "row scan");
+  // d3, d2, d4
+  const int skews[3] = {0, 1, -1};
+  const int phases[3] = {BSF_PHASE_D3, BSF_PHASE_D2, BSF_PHASE_D4};
+  for (int i = 0; i < 3; ++i) {
+    PhaseTimer t(h, phases[i]);
+    e = bsf_launch_vscan(h->elem, h->n, skews[i], h->S, h->pitch, h->Hp, h->Wp, h->agg, h->carry,
+                         h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "vertical scan");
+  }
+  h->have_S = true;
+  h->S_R = h->R;
+  h->S_elem = h->elem;
+  h->S_q = h->q;
+  return BSF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bsf_create(bsf_t* out, int H, int W, int N, int n, int boundary, int max_reach) {
+  if (!out) return BSF_EINVAL;
+  *out = nullptr;
+  if (H <= 0 || W <= 0 || N != 4 || n < 1 || n > 3 || boundary < BSF_ZERO ||
+      boundary > BSF_SYMMETRIC || max_reach < -1)
+    return BSF_EINVAL;
+  if ((long long)H * W > (1LL << 31)) return BSF_EINVAL;
+  bsf_t h = new (std::nothrow) bsf_ctx();
+  if (!h) return BSF_ENOMEM;
+  h->H = H; h->W = W; h->N = N; h->n = n; h->boundary = boundary;
+  if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return BSF_ECUDA; }
+  if (max_reach >= 0) {
+    h->R = max_reach > 3 * n ? max_reach : 3 * n;
+    h->R_fixed = true;
+  }
+  cudaError_t e = cudaMalloc(&h->st, sizeof(DevStatus));
+  if (e == cudaSuccess) e = cudaMemset(h->st, 0, sizeof(DevStatus));
+  if (e == cudaSuccess) e = cudaMalloc(&h->Lf, (size_t)H * W * sizeof(ushort4));
+  if (e == cudaSuccess && h->R_fixed && ensure_workspace(h) != BSF_OK) e = cudaErrorMemoryAllocation;
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    bsf_destroy(h);
+    return e == cudaErrorMemoryAllocation ? BSF_ENOMEM : BSF_ECUDA;
+  }
+  *out = h;
+  return BSF_OK;
+}
+
+void bsf_destroy(bsf_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  free_workspace(h);
+  if (h->ev) {
+    for (int i = 0; i < 2 * bsf_ctx::kMaxRec; ++i) cudaEventDestroy(h->ev[i]);
+    delete[] h->ev;
+  }
+  if (h->Lf) cudaFree(h->Lf);
+  if (h->st) cudaFree(h->st);
+  delete h;
+}
+
+int bsf_set_stream(bsf_t h, void* stream) {
+  if (!h) return BSF_EINVAL;
+  h->stream = (cudaStream_t)stream;
+  return BSF_OK;
+}
+
+int bsf_set_precision(bsf_t h, int mode, int frac_bits) {
+  if (!h) return BSF_EINVAL;
+  if (mode != BSF_FIX64 && mode != BSF_FIX128) return fail(h, BSF_EINVAL, "bad precision mode %d", mode);
+  const int qmax = mode == BSF_FIX64 ? 62 : 100;
+  if (frac_bits < -1 || frac_bits > qmax)
+    return fail(h, BSF_EINVAL, "frac_bits %d outside [-1, %d]", frac_bits, qmax);
+  if (mode != h->precision) h->have_S = false;
+  h->precision = mode;
+  h->frac_req = frac_bits;
+  return BSF_OK;
+}
+
+int bsf_set_value_bound(bsf_t h, double max_abs) {
+  if (!h) return BSF_EINVAL;
+  if (!(max_abs >= 0.0) || std::isinf(max_abs)) return fail(h, BSF_EINVAL, "bad value bound");
+  h->has_bound = true;
+  h->value_bound = max_abs;
+  return BSF_OK;
+}
+
+int bsf_set_step_rule(bsf_t h, int rule) {
+  if (!h) return BSF_EINVAL;
+  if (rule != BSF_STEP_D1 && rule != BSF_STEP_D1_PAPER) return fail(h, BSF_EINVAL, "bad step rule %d", rule);
+  h->step_rule = rule;
+  return BSF_OK;
+}
+
+int bsf_plan(bsf_t h, const float* cov, int cov_kind) {
+  if (!h) return BSF_EINVAL;
+  return run_steps(h, cov, cov_kind, true);
+}
+
+int bsf_preintegrate(bsf_t h, const void* img, int dtype, long long ld) {
+  if (!h) return BSF_EINVAL;
+  return preintegrate_impl(h, img, dtype, ld);
+}
+
+int bsf_filter(bsf_t h, const void* img, int dtype, long long ld, const float* cov, int cov_kind,
+               void* out, int out_dtype, long long ldo) {
+  if (!h) return BSF_EINVAL;
+  if (!out) return fail(h, BSF_EINVAL, "out is NULL");
+  if (out_dtype != BSF_F32 && out_dtype != BSF_F64) return fail(h, BSF_EINVAL, "bad out dtype %d", out_dtype);
+  if (ldo < h->W) return fail(h, BSF_EINVAL, "ldo %lld < W %d", ldo, h->W);
+  int rc;
+  const bool need_plan = h->R < 0 || (img && h->frac_req < 0 && !h->planned);
+  if ((rc = run_steps(h, cov, cov_kind, need_plan))) return rc;
+  if (img) {
+    if ((rc = preintegrate_impl(h, img, dtype, ld))) return rc;
+  } else if (!h->have_S || h->S_R != h->R || h->S_elem != h->elem) {
+    return fail(h, BSF_ESTATE, "img is NULL and no matching pre-integration is held");
+  }
+  cudaError_t e;
+  {
+    PhaseTimer t(h, BSF_PHASE_STENCIL);
+    e = bsf_launch_stencil_d1(h->elem, h->n, h->S, h->pitch, h->R, h->Lf, h->H, h->W, h->S_q, out,
+                              out_dtype, ldo, h->st, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "stencil");
+  return BSF_OK;
+}
+
+int bsf_status(bsf_t h) {
+  if (!h) return BSF_EINVAL;
+  int rc = read_status(h);
+  if (rc) return rc;
+  const int err = h->host_st.err;
+  BSF_CUDA(h, cudaMemsetAsync(&h->st->err, 0, sizeof(int), h->stream));
+  BSF_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (err) {
+    fail(h, err, "device status %d (clamped %u, non-finite %u, out of reach %u, overflow %u)", err,
+         h->host_st.clamp_count, h->host_st.bad_count, h->host_st.range_count,
+         h->host_st.overflow_count);
+  }
+  return err;
+}
+
+const char* bsf_last_error(bsf_t h) { return h ? h->msg : "NULL context"; }
+
+int bsf_get_info(bsf_t h, bsf_info_t* info) {
+  if (!h || !info) return BSF_EINVAL;
+  std::memset(info, 0, sizeof *info);
+  info->H = h->H; info->W = h->W; info->N = h->N; info->n = h->n;
+  info->boundary = h->boundary;
+  info->R = h->R;
+  info->Hp = h->R >= 0 ? h->H + 2 * h->R : 0;
+  info->Wp = h->R >= 0 ? h->W + 2 * h->R : 0;
+  info->pitch = h->pitch;
+  info->elem_bytes = (int)elem_bytes_of(h->precision);
+  info->precision = h->precision;
+  info->frac_bits = h->q;
+  info->step_rule = h->step_rule;
+  info->max_reach = h->host_st.max_reach;
+  info->max_mass = bits_to_float(h->host_st.max_mass_bits);
+  info->clamp_count = h->host_st.clamp_count;
+  info->flags = h->host_st.clamp_count ? BSF_FLAG_CLAMPED : 0u;
+  info->workspace_bytes = (long long)(h->S_bytes + 2 * h->scan_bytes) +
+                          (long long)h->H * h->W * (long long)sizeof(ushort4) + (long long)sizeof(DevStatus);
+  return BSF_OK;
+}
+
+int bsf_copy_steps(bsf_t h, uint16_t* dst) {
+  if (!h || !dst) return BSF_EINVAL;
+  const size_t HW = (size_t)h->H * h->W;
+  for (int k = 0; k < 4; ++k) {
+    BSF_CUDA(h, cudaMemcpy2DAsync(dst + k * HW, sizeof(uint16_t),
+                                  reinterpret_cast<const char*>(h->Lf) + k * sizeof(uint16_t),
+                                  sizeof(ushort4), sizeof(uint16_t), HW, cudaMemcpyDeviceToDevice,
+                                  h->stream));
+  }
+  return BSF_OK;
+}
+
+int bsf_copy_preintegrated(bsf_t h, void* dst) {
+  if (!h || !dst) return BSF_EINVAL;
+  if (!h->have_S) return fail(h, BSF_ESTATE, "no pre-integration held");
+  BSF_CUDA(h, cudaMemcpy2DAsync(dst, (size_t)h->Wp * h->elem, h->S, (size_t)h->pitch * h->elem,
+                                (size_t)h->Wp * h->elem, h->Hp, cudaMemcpyDeviceToDevice, h->stream));
+  return BSF_OK;
+}
+
+int bsf_set_profiling(bsf_t h, int on) {
+  if (!h) return BSF_EINVAL;
+  if (on && !h->ev) {
+    h->ev = new (std::nothrow) cudaEvent_t[2 * bsf_ctx::kMaxRec];
+    if (!h->ev) return fail(h, BSF_ENOMEM, "event table");
+    for (int i = 0; i < 2 * bsf_ctx::kMaxRec; ++i) BSF_CUDA(h, cudaEventCreate(&h->ev[i]));
+  }
+  h->profiling = on != 0;
+  return BSF_OK;
+}
+
+int bsf_read_profile(bsf_t h, double* ms, int* count) {
+  if (!h) return BSF_EINVAL;
+  double acc[BSF_NUM_PHASES] = {0};
+  int cnt[BSF_NUM_PHASES] = {0};
+  if (h->nrec) BSF_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (int i = 0; i < h->nrec; ++i) {
+    float t = 0.f;
+    BSF_CUDA(h, cudaEventElapsedTime(&t, h->ev[2 * i], h->ev[2 * i + 1]));
+    acc[h->rec_phase[i]] += t;
+    cnt[h->rec_phase[i]] += 1;
+  }
+  for (int p = 0; p < BSF_NUM_PHASES; ++p) {
+    if (ms) ms[p] = acc[p];
+    if (count) count[p] = cnt[p];
+  }
+  const int dropped = h->dropped;
+  h->nrec = 0;
+  h->dropped = 0;
+  return dropped;
+}
+
+}  // extern "C"

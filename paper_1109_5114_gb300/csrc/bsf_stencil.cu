@@ -1,0 +1,165 @@
+// Per-pixel finite differences on the running sums (Section 1.1: the 16-tap
+// finite-difference mesh of the BoxFilter algorithm, generalised to order n,
+// whose mesh grows to (n+1)^4 taps -- Section 2.1 counts 2^N points per
+// order, two per box distribution).
+//
+// For pixel p with integer steps L_k and centring c_k = n (L_k - 1)/2:
+//   acc = sum_{t in {0..n}^4} prod_k (-1)^t_k C(n, t_k) S(p + sum_k (c_k - t_k L_k) d_k)
+// evaluated exactly modulo 2^b as the nested order-n backward differences
+// along d1, d2, d3, d4 (innermost first), then
+//   out = RN32(RN32(acc) 2^-q) / RN32(D)  or  RN64(RN64(acc) 2^-q) / RN64(D),
+//   D = prod_k L_k^n.
+// One thread per output pixel; a warp covers 32 consecutive pixels of a row,
+// so each tap is a coalesced row segment of S whenever neighbouring pixels
+// share their steps (the covariance field is smooth).
+#include "bsf_device.cuh"
+
+namespace {
+
+template <typename T, int NF>
+__device__ __forceinline__ T diff1(const T* p, long long s) {
+  const T v0 = bsf_load(p);
+  const T v1 = bsf_load(p - s);
+  if constexpr (NF == 1) {
+    return v0 - v1;
+  } else if constexpr (NF == 2) {
+    const T v2 = bsf_load(p - 2 * s);
+    return (v0 + v2) - (v1 << 1);
+  } else {
+    const T v2 = bsf_load(p - 2 * s);
+    const T v3 = bsf_load(p - 3 * s);
+    const T a = v1 - v2;
+    return (v0 - v3) - ((a << 1) + a);
+  }
+}
+
+// Nested differences: level LVL applies the order-NF difference along
+// direction LVL-1 to the result of level LVL-1.
+template <typename T, int NF, int LVL>
+__device__ __forceinline__ T comb(const T* p, const long long* s) {
+  if constexpr (LVL == 1) {
+    return diff1<T, NF>(p, s[0]);
+  } else {
+    const long long sk = s[LVL - 1];
+    const T v0 = comb<T, NF, LVL - 1>(p, s);
+    const T v1 = comb<T, NF, LVL - 1>(p - sk, s);
+    if constexpr (NF == 1) {
+      return v0 - v1;
+    } else if constexpr (NF == 2) {
+      const T v2 = comb<T, NF, LVL - 1>(p - 2 * sk, s);
+      return (v0 + v2) - (v1 << 1);
+    } else {
+      const T v2 = comb<T, NF, LVL - 1>(p - 2 * sk, s);
+      const T v3 = comb<T, NF, LVL - 1>(p - 3 * sk, s);
+      const T a = v1 - v2;
+      return (v0 - v3) - ((a << 1) + a);
+    }
+  }
+}
+
+template <typename T> __device__ __forceinline__ float to_f32(T acc, T D);
+template <> __device__ __forceinline__ float to_f32<uint64_t>(uint64_t acc, uint64_t D) {
+  (void)D;
+  return bsf_rn32_i64((long long)acc);
+}
+template <> __device__ __forceinline__ float to_f32<u128>(u128 acc, u128 D) {
+  (void)D;
+  return bsf_rn32((i128)acc);
+}
+template <typename T> __device__ __forceinline__ double to_f64(T acc);
+template <> __device__ __forceinline__ double to_f64<uint64_t>(uint64_t acc) {
+  return __ll2double_rn((long long)acc);
+}
+template <> __device__ __forceinline__ double to_f64<u128>(u128 acc) { return bsf_rn64((i128)acc); }
+
+template <typename T> __device__ __forceinline__ float mass_f32(T D);
+template <> __device__ __forceinline__ float mass_f32<uint64_t>(uint64_t D) { return bsf_rn32_u64(D); }
+template <> __device__ __forceinline__ float mass_f32<u128>(u128 D) { return bsf_rn32_u(D); }
+template <typename T> __device__ __forceinline__ double mass_f64(T D);
+template <> __device__ __forceinline__ double mass_f64<uint64_t>(uint64_t D) { return __ull2double_rn(D); }
+template <> __device__ __forceinline__ double mass_f64<u128>(u128 D) { return bsf_rn64_u(D); }
+
+// Resident blocks per SM requested from the register allocator: enough warps
+// to cover the latency of the (n+1)^4 gathers.
+template <typename T, int NF> struct StencilOcc {
+  static constexpr int value = sizeof(T) == 8 ? (NF == 1 ? 6 : NF == 2 ? 4 : 1) : (NF == 1 ? 4 : NF == 2 ? 2 : 1);
+};
+
+template <typename T, int NF, typename Out>
+__global__ void __launch_bounds__(256, (StencilOcc<T, NF>::value))
+k_stencil_d1(const T* __restrict__ S, long long pitch, int R, const ushort4* __restrict__ Lf,
+             int H, int W, float scale_f, double scale_d, Out* __restrict__ out, long long ldo,
+             DevStatus* st) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= W || y >= H) return;
+  const ushort4 L4 = Lf[(long long)y * W + x];
+  const long long L1 = L4.x, L2 = L4.y, L3 = L4.z, L4w = L4.w;
+  // element strides of d1 = (1,0), d2 = (1,1), d3 = (0,1), d4 = (-1,1)
+  const long long e1 = 1, e2 = pitch + 1, e3 = pitch, e4 = pitch - 1;
+  const long long c1 = NF * (L1 - 1) / 2, c2 = NF * (L2 - 1) / 2, c3 = NF * (L3 - 1) / 2,
+                  c4 = NF * (L4w - 1) / 2;
+  const T* base = S + (long long)(y + R) * pitch + (x + R) + c1 * e1 + c2 * e2 + c3 * e3 + c4 * e4;
+  const long long s[4] = {L1 * e1, L2 * e2, L3 * e3, L4w * e4};
+  const T acc = comb<T, NF, 4>(base, s);
+
+  // D = prod_k L_k^n (exact) and the bound max|Q| * D < 2^(b-1) that makes
+  // the modular accumulator equal the true one (checked in float32 with a
+  // margin far above its rounding: |acc| <= D max|Q| and max|Q| <= bound + 1/2)
+  T D = 1;
+  const T D1 = (T)(L1 * L2) * (T)(L3 * L4w);
+  const float Df1 = (float)(L1 * L2) * (float)(L3 * L4w);
+  float Df = Df1;
+#pragma unroll
+  for (int j = 0; j < NF; ++j) D *= D1;
+#pragma unroll
+  for (int j = 1; j < NF; ++j) Df *= Df1;
+  const float maxq = __uint_as_float(st->max_absq_bits) + 1.f;
+  const float lim = bsf_pow2_f32(ElemBits<T>::value - 1);
+  if (maxq * Df * 1.0001f >= lim) {
+    atomicAdd(&st->overflow_count, 1u);
+    bsf_set_error(st, BSF_EOVERFLOW);
+  }
+  if constexpr (sizeof(Out) == 4) {
+    const float xa = __fmul_rn(to_f32<T>(acc, D), scale_f);
+    out[(long long)y * ldo + x] = __fdiv_rn(xa, mass_f32<T>(D));
+  } else {
+    const double xa = __dmul_rn(to_f64<T>(acc), scale_d);
+    out[(long long)y * ldo + x] = __ddiv_rn(xa, mass_f64<T>(D));
+  }
+}
+
+template <typename T, int NF>
+cudaError_t launch_t(const T* S, long long pitch, int R, const ushort4* Lf, int H, int W, int q,
+                     void* out, int out_dtype, long long ldo, DevStatus* st, cudaStream_t s) {
+  dim3 block(32, 8);
+  dim3 grid((W + 31) / 32, (H + 7) / 8);
+  const float sf = ldexpf(1.f, -q);
+  const double sd = ldexp(1.0, -q);
+  if (out_dtype == BSF_F32)
+    k_stencil_d1<T, NF, float><<<grid, block, 0, s>>>(S, pitch, R, Lf, H, W, sf, sd, (float*)out, ldo, st);
+  else if (out_dtype == BSF_F64)
+    k_stencil_d1<T, NF, double><<<grid, block, 0, s>>>(S, pitch, R, Lf, H, W, sf, sd, (double*)out, ldo, st);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t bsf_launch_stencil_d1(int elem_bytes, int n, const void* S, long long pitch, int R,
+                                  const ushort4* Lf, int H, int W, int q, void* out,
+                                  int out_dtype, long long ldo, DevStatus* st, cudaStream_t s) {
+#define BSF_ST(T, NF) return launch_t<T, NF>((const T*)S, pitch, R, Lf, H, W, q, out, out_dtype, ldo, st, s)
+  if (elem_bytes == 8) {
+    if (n == 1) BSF_ST(uint64_t, 1);
+    if (n == 2) BSF_ST(uint64_t, 2);
+    if (n == 3) BSF_ST(uint64_t, 3);
+  } else if (elem_bytes == 16) {
+    if (n == 1) BSF_ST(u128, 1);
+    if (n == 2) BSF_ST(u128, 2);
+    if (n == 3) BSF_ST(u128, 3);
+  }
+#undef BSF_ST
+  return cudaErrorInvalidValue;
+}

@@ -1,0 +1,57 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the C ABI
+and the oracle on the same seeded inputs."""
+import numpy as np
+
+from oracle import kernels, modular, params
+from oracle.rounding import quantize
+
+
+def torch_mod():
+    import torch
+    return torch
+
+
+def run_gpu(img, cov, n, boundary, q, precision=1, out_dtype=np.float32, max_reach=-1,
+            step_rule=0, want_S=False, want_steps=False):
+    """Forward filter on cuda:0; returns dict(out, R, q, info[, S, L])."""
+    torch = torch_mod()
+    from paper_1109_5114_gb300 import bsf
+    H, W = img.shape
+    f = bsf.BoxSplineFilter(H, W, n, boundary, max_reach=max_reach, precision=precision,
+                            frac_bits=q, step_rule=step_rule)
+    ti = torch.from_numpy(np.ascontiguousarray(img)).cuda()
+    tc = torch.from_numpy(np.ascontiguousarray(cov, dtype=np.float32)).cuda()
+    tdt = torch.float32 if np.dtype(out_dtype) == np.float32 else torch.float64
+    out = f.filter(ti, tc, out_dtype=tdt)
+    torch.cuda.synchronize()
+    st = f.status()
+    info = f.info()
+    res = dict(out=out.cpu().numpy(), R=info.R, q=info.frac_bits, info=info, status=st)
+    if want_steps:
+        res["L"] = f.steps().cpu().numpy().astype(np.int64) & 0xFFFF
+    if want_S:
+        raw, inf = f.preintegrated()
+        raw = raw.cpu().numpy()
+        if inf.elem_bytes == 8:
+            res["S"] = raw.view(np.uint64).reshape(inf.Hp, inf.Wp)
+        else:
+            v = raw.view(np.uint64).reshape(inf.Hp, inf.Wp, 2)
+            res["S"] = (v[..., 0].copy(), v[..., 1].copy())
+    f.close()
+    return res
+
+
+def run_oracle(img, cov, n, boundary, q, R, bits=64, out_dtype=np.float32, rule="corrected"):
+    return modular.filter_modular(img, cov, n, boundary, q=q, bits=bits, out_dtype=out_dtype, R=R,
+                                  rule=rule, return_all=True)
+
+
+def oracle_S(img, n, boundary, q, R, bits):
+    fq = quantize(img, q, as_object=(bits == 128))
+    fe = kernels.extend_image(fq, R, boundary)
+    return modular.preintegrate(fe, n, bits)
+
+
+def oracle_steps(cov, n, rule="corrected"):
+    L, fl = params.integer_steps(cov[0], cov[1], cov[2], n, rule)
+    return L, fl

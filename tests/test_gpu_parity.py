@@ -1,0 +1,186 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Integer work (steps, running sums) must match bit for bit; outputs of the
+fixed-point path must match the oracle's modular pipeline bit for bit (same
+quantisation, same single final rounding), and the oracle's direct definition
+exactly on its exact accumulators.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import kernels, params
+from oracle.rounding import finalize, quantize
+from tests.gpu_helpers import oracle_S, oracle_steps, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1109_5114_gb300 import build
+    build.build()
+
+
+def _cov(H, W, seed, smax=4.0, rmax=3.5):
+    return wl.random_cov_field(H, W, seed=seed, sigma_range=(0.3, smax), rho_range=(1.0, rmax))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+@pytest.mark.parametrize("rule", [0, 1])
+def test_steps_bit_exact(n, rule):
+    H, W = 67, 45
+    cov = _cov(H, W, seed=10 + n, smax=20.0, rmax=6.0)   # includes clamped pixels
+    img = wl.random_integer_image(H, W, seed=1).astype(np.float32)
+    g = run_gpu(img, cov, n, 2, q=4, want_steps=True, step_rule=rule)
+    L, fl = oracle_steps(cov, n, "paper" if rule else "corrected")
+    np.testing.assert_array_equal(g["L"], L)
+    assert g["info"].clamp_count == int((fl & params.CLAMP_FLAG != 0).sum())
+
+
+@pytest.mark.parametrize("n,boundary,prec", list(itertools.product([1, 2, 3], [0, 1, 2], [1, 2])))
+def test_running_sums_bit_exact(n, boundary, prec):
+    H, W = 29, 70   # several warps per row, ragged chunks
+    img = wl.random_integer_image(H, W, seed=n + 3 * boundary, lo=-300, hi=300).astype(np.float64)
+    cov = _cov(H, W, seed=n)
+    g = run_gpu(img, cov, n, boundary, q=5, precision=prec, want_S=True)
+    bits = 64 if prec == 1 else 128
+    S = oracle_S(img, n, boundary, 5, g["R"], bits)
+    if bits == 64:
+        np.testing.assert_array_equal(g["S"], S)
+    else:
+        np.testing.assert_array_equal(g["S"][0], S.lo)
+        np.testing.assert_array_equal(g["S"][1], S.hi)
+
+
+@pytest.mark.parametrize("n,boundary", list(itertools.product([1, 2, 3], [0, 1, 2])))
+@pytest.mark.parametrize("dtype", [np.uint8, np.float32, np.float64])
+def test_filter_bit_exact_vs_modular_oracle(n, boundary, dtype):
+    H, W = 53, 77
+    if dtype == np.uint8:
+        img = wl.blob_image_u8(H, W, seed=n, n_blobs=8)
+    else:
+        img = wl.blob_image(H, W, seed=n, n_blobs=8, sigma_range=(2, 9)).astype(dtype)
+    cov = _cov(H, W, seed=20 + n, smax=5.0)
+    q = 0 if dtype == np.uint8 else 24
+    for out_dtype in (np.float32, np.float64):
+        g = run_gpu(img, cov, n, boundary, q=q, out_dtype=out_dtype)
+        assert g["status"] == 0
+        o = run_oracle(img, cov, n, boundary, q, g["R"], out_dtype=out_dtype)
+        np.testing.assert_array_equal(g["out"], o["out"])
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_filter_bit_exact_128(n):
+    H, W = 41, 38
+    img = wl.blob_image(H, W, seed=7, n_blobs=6, sigma_range=(2, 6)).astype(np.float32)
+    cov = _cov(H, W, seed=30 + n)
+    for out_dtype in (np.float32, np.float64):
+        g = run_gpu(img, cov, n, 2, q=70, precision=2, out_dtype=out_dtype)
+        assert g["status"] == 0
+        o = run_oracle(img, cov, n, 2, 70, g["R"], bits=128, out_dtype=out_dtype)
+        np.testing.assert_array_equal(g["out"], o["out"])
+
+
+def test_filter_equals_direct_definition():
+    H, W, n = 24, 31, 2
+    img = wl.random_integer_image(H, W, seed=4, lo=0, hi=255).astype(np.float32)
+    cov = _cov(H, W, seed=5)
+    g = run_gpu(img, cov, n, 2, q=8, out_dtype=np.float64, want_steps=True)
+    acc = kernels.correlate_exact(quantize(img, 8), g["L"], n, 2)
+    D = np.array([[kernels.kernel_mass(g["L"][:, y, x], n) for x in range(W)] for y in range(H)],
+                 dtype=np.int64)
+    ref = finalize(acc.astype(object), D, 8, np.float64)
+    np.testing.assert_array_equal(g["out"], ref)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 37), (29, 1), (2, 3), (64, 64)])
+def test_degenerate_shapes(shape):
+    H, W = shape
+    img = wl.random_integer_image(H, W, seed=2, lo=-50, hi=50).astype(np.float32)
+    cov = wl.constant_cov_field(H, W, 2.0, 0.3, 1.0)
+    for n in (1, 2, 3):
+        g = run_gpu(img, cov, n, 2, q=12)
+        o = run_oracle(img, cov, n, 2, 12, g["R"])
+        np.testing.assert_array_equal(g["out"], o["out"])
+
+
+def test_zero_covariance_is_identity():
+    H, W = 33, 40
+    img = wl.blob_image(H, W, seed=3, n_blobs=4).astype(np.float32)
+    cov = np.zeros((3, H, W), np.float32)
+    for n in (1, 2, 3):
+        g = run_gpu(img, cov, n, 0, q=30)
+        np.testing.assert_array_equal(g["out"], quantize(img, 30).astype(np.float64) * 2.0 ** -30)
+
+
+def test_constant_image_preserved_exactly():
+    # unit mass: acc = c 2^q D exactly.  float64 output rounds nothing (acc and D
+    # below 2^53); float32 output rounds acc and D once each, so it stays within
+    # 1.5 units in the last place.
+    H, W = 50, 61
+    img = np.full((H, W), 3.25, np.float32)
+    cov = _cov(H, W, seed=8, smax=6.0)
+    for n in (1, 2, 3):
+        for b in (1, 2):
+            g = run_gpu(img, cov, n, b, q=20, out_dtype=np.float64)
+            assert (g["out"] == 3.25).all()
+            g = run_gpu(img, cov, n, b, q=20, out_dtype=np.float32)
+            np.testing.assert_allclose(g["out"], 3.25, rtol=1.5 * 2.0 ** -23, atol=0)
+
+
+def test_out_of_reach_and_overflow_are_reported():
+    from paper_1109_5114_gb300 import bsf
+    H, W = 40, 40
+    img = wl.random_integer_image(H, W, seed=1, lo=0, hi=100).astype(np.float32)
+    cov = wl.constant_cov_field(H, W, 25.0, 0.0, 25.0)
+    g = run_gpu(img, cov, 2, 2, q=10, max_reach=8)          # needs R ~ 40
+    assert g["status"] == bsf.BSF_ERANGE
+    o = run_oracle(img, cov, 2, 2, 10, g["R"])
+    np.testing.assert_array_equal(g["out"], o["out"])       # identity fallback, same as oracle
+    g = run_gpu(img, cov, 2, 2, q=60)                       # 100 * 2^60 * mass >= 2^63
+    assert g["status"] == bsf.BSF_EOVERFLOW
+
+
+def test_clamped_covariance_flagged():
+    H, W = 16, 16
+    img = np.ones((H, W), np.float32)
+    cov = wl.constant_cov_field(H, W, 4.0, 6.0, 9.0)        # |C12| > min(C11, C22)
+    g = run_gpu(img, cov, 1, 2, q=10)
+    assert g["info"].clamp_count == H * W
+    assert g["status"] == 0
+
+
+def test_automatic_q():
+    # q is the largest value with (max|f| 2^q) * max prod L^n < 2^62, less one bit
+    import math
+    H, W, n = 48, 52, 2
+    img = wl.blob_image(H, W, seed=9, n_blobs=5).astype(np.float32)
+    cov = _cov(H, W, seed=9, smax=12.0)
+    g = run_gpu(img, cov, n, 2, q=-1, want_steps=True)
+    L = g["L"]
+    mass = float(np.prod(L.astype(np.float64) ** n, axis=0).max())
+    assert abs(g["info"].max_mass - mass) <= 1e-6 * mass
+    vmax = float(np.abs(img).max())
+    q_expect = min(math.floor(62 - math.log2(vmax) - math.log2(mass)) - 1, 64 - 28)
+    assert g["q"] == q_expect
+    assert g["status"] == 0
+    o = run_oracle(img, cov, n, 2, g["q"], g["R"])
+    np.testing.assert_array_equal(g["out"], o["out"])
+
+
+def test_auto_q_on_large_kernels_does_not_overflow():
+    # big steps (mass ~ 2^37): the automatic q must leave room for them
+    H, W, n = 300, 300, 2
+    img = wl.blob_image(H, W, seed=1, n_blobs=20).astype(np.float32)
+    cov = wl.diagonal_ramp_cov_field(H, W, sigma_lo=8.0, sigma_hi=16.0)
+    g = run_gpu(img, cov, n, 2, q=-1)
+    assert g["status"] == 0
+    assert g["info"].max_mass > 2.0 ** 30
+    o = run_oracle(img, cov, n, 2, g["q"], g["R"])
+    np.testing.assert_array_equal(g["out"], o["out"])
