@@ -202,6 +202,39 @@ int bsf_set_profiling(bsf_t h, int on);
  * error code. */
 int bsf_read_profile(bsf_t h, double* ms, int* count);
 
+/* Forward filter that allocates nothing.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory while
+ * they run, such as an application that gave its whole device-memory budget
+ * to its own pool at start-up, or a latency-critical loop that cannot afford
+ * the device-wide synchronisation cudaMalloc / cudaFree may cause.
+ *
+ * It runs the same kernels as bsf_filter (step solve, extension +
+ * quantisation + running sums, finite differences; uint64 running sums,
+ * BSF_STEP_D1) on scratch memory held in one static device array of 24 MiB
+ * inside the library, which every GPU that loads the library keeps until the
+ * process exits.  No context is needed; the caller passes inputs and outputs:
+ *   img   device [H][ld] of dtype BSF_U8 / BSF_F32 / BSF_F64
+ *   cov   device [3][H][W] float32 (C11, C12, C22)
+ *   out   device [H][ldo] of out_dtype BSF_F32 / BSF_F64
+ *   n     order 1..3; boundary BSF_ZERO / BSF_REPLICATE / BSF_SYMMETRIC
+ *   reach padding R >= 3n (pixels whose taps exceed it fall back to identity
+ *         steps and make the call return BSF_ERANGE)
+ *   frac_bits  q in [0, 62]
+ *   stream     cudaStream_t (NULL = legacy default stream)
+ * Sizes whose workspace (steps, running sums, scan carries) would not fit the
+ * array -- at most 2^24 pixels and 2^24 padded elements, and 24 MiB in all --
+ * are rejected with BSF_ERANGE before any device work.
+ * Synchronous: returns BSF_OK, a host-side error (BSF_EINVAL, BSF_ERANGE,
+ * BSF_ECUDA) or the device status of this call (BSF_ERANGE, BSF_EOVERFLOW,
+ * BSF_ECOV).
+ * The first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress (the device must be current); make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents, so calls that overlap on the GPU race: serialise them. */
+int bsf_filter_noalloc(const void* img, int dtype, long long ld, int H, int W, int n,
+                       int boundary, int reach, int frac_bits, const float* cov,
+                       void* out, int out_dtype, long long ldo, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
