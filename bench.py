@@ -154,6 +154,8 @@ def run_gpu(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
     f = bsf.BoxSplineFilter(H, W, ORDER, "symmetric", precision=1, frac_bits=-1, value_bound=vmax)
+    f.set_option(bsf.BSF_OPT_SCAN_MODE, bsf.BSF_SCAN_THREE_PHASE)
+    kernels_per_vscan = 3
     info = f.plan(d_cov)
     stream = torch.cuda.current_stream()
 
@@ -191,6 +193,35 @@ def run_gpu(args):
     rc = f.status()
     if rc != 0:
         raise RuntimeError(f"device status {rc}")
+
+    # ---- forward + backward (image gradient of <out, gout>) ---------------
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    d_gout = torch.randn((H, W), generator=gen, device="cuda", dtype=torch.float32)
+    d_gimg = torch.empty_like(d_gout)
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+        f.backward(d_gout, d_cov, gimg=d_gimg)
+    torch.cuda.synchronize()
+    f.set_profiling(True)
+    f.read_profile()
+    bs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    be = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(world)
+    for i in range(args.steps):
+        flush.zero_()
+        bs[i].record(stream)
+        step()
+        f.backward(d_gout, d_cov, gimg=d_gimg)
+        be[i].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    prof_fb = f.read_profile()
+    f.set_profiling(False)
+    fb_ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(bs, be)), world)
+    rc = f.status()
+    if rc != 0:
+        raise RuntimeError(f"device status {rc} (backward)")
 
     # ---- end to end through the public API with host buffers --------------
     h_img = torch.from_numpy(img).pin_memory()
@@ -234,6 +265,7 @@ def run_gpu(args):
 
     px = H * W
     value = world * px * args.steps / (total_ms * 1e-3) / 1e6
+    fb_value = world * px * args.steps / (fb_ms * 1e-3) / 1e6
     e2e_value = world * px * args.steps / (e2e_ms * 1e-3) / 1e6
 
     # ---- roofline of the dominant kernel ------------------------------------
@@ -242,12 +274,17 @@ def run_gpu(args):
     elem = info.elem_bytes
     Sbytes = info.Hp * info.Wp * elem
     alg = {
-        # S read once (the taps of neighbouring pixels overlap), steps in, out
-        "stencil": Sbytes + px * 8 + px * 4,
+        # S read once (the taps of neighbouring pixels overlap), covariance in
+        # (the step solve is fused into the stencil), output out
+        "stencil": Sbytes + px * 12 + px * 4,
         "steps": px * 12 + px * 8,
         "rows": px * 4 + Sbytes,
         "d3": 2 * Sbytes, "d2": 2 * Sbytes, "d4": 2 * Sbytes,
     }
+    # our kernels per timed step: steps (only when planning), rows, one kernel
+    # per vertical direction (look-back) and the stencil
+    launches = sum(c for k, (ms, c) in prof.items() if k in ("steps", "rows", "stencil"))
+    launches += sum(c * kernels_per_vscan for k, (ms, c) in prof.items() if k in ("d3", "d2", "d4"))
     hbm_peak, peak_src = peaks()
     dom_ms = per_phase[dominant][0]
     achieved = alg[dominant] / (dom_ms * 1e-3) / 1e9
@@ -272,7 +309,10 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": 12 * args.steps,
+        "gpu_launches": launches,
+        "fwd_bwd": {"value": round(fb_value, 2), "unit": UNIT,
+                    "ms_per_step": round(fb_ms / args.steps, 5),
+                    "phases_ms": {k: round(ms / max(c, 1), 5) for k, (ms, c) in prof_fb.items() if c}},
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1),
                      "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
                      "frac": round(achieved / hbm_peak, 4), "traffic": traffic,

@@ -91,7 +91,23 @@ extern "C" {
 #define BSF_PHASE_D2       3  /* running sums along d2 (three kernels) */
 #define BSF_PHASE_D4       4  /* running sums along d4 (three kernels) */
 #define BSF_PHASE_STENCIL  5  /* finite differences + final rounding */
-#define BSF_NUM_PHASES     6
+#define BSF_PHASE_BWD_SCATTER 6  /* backward: weight quantisation + tap scatter */
+#define BSF_PHASE_BWD_SCANS   7  /* backward: suffix sums along d4, d2, d3, d1 */
+#define BSF_PHASE_BWD_FOLD    8  /* backward: extension adjoint + output */
+#define BSF_NUM_PHASES        9
+
+/* options of bsf_set_option */
+#define BSF_OPT_SCAN_MODE    1  /* value BSF_SCAN_THREE_PHASE (default) or BSF_SCAN_LOOKBACK */
+#define BSF_OPT_WAIT_LIMIT   2  /* polls a block may spend waiting for a predecessor
+                                   (default 1048576, >= 0); past it: BSF_ETIMEOUT */
+#define BSF_OPT_SCAN_CHUNK   4  /* rows per chunk of the three-phase scan, 16..4096 (default 64) */
+#define BSF_OPT_SCAN_SHORT_TILES 5  /* 1 = look-back tiles of half the rows (16 for uint64) */
+#define BSF_OPT_TEST_UNPUBLISHED 3  /* failure injection for tests: 1 = the look-back
+                                       scan's first chunk never marks its results
+                                       ready, so every wait on it runs out */
+#define BSF_SCAN_LOOKBACK     0 /* single pass, decoupled look-back between blocks */
+#define BSF_SCAN_THREE_PHASE  1 /* reduce / carry / rescan; no block waits on another
+                                   (measured faster on GB300 for 2048^2, n = 2) */
 
 /* device status flags reported through bsf_info_t.flags */
 #define BSF_FLAG_CLAMPED  1u  /* some covariance exceeded e(phi) and was clamped */
@@ -110,8 +126,8 @@ typedef struct {
   int precision;       /* BSF_FIX64 / BSF_FIX128 */
   int frac_bits;       /* q in use (-1 = not yet resolved) */
   int step_rule;       /* BSF_STEP_* */
-  int max_reach;       /* largest tap reach seen by the last plan/filter */
-  double max_mass;     /* largest prod_k L_k^n seen by the last plan/filter */
+  int max_reach;       /* largest tap reach of the last plan (-1 before any) */
+  double max_mass;     /* largest prod_k L_k^n of the last plan */
   unsigned clamp_count;/* pixels clamped to the elongation bound, last call */
   unsigned flags;      /* BSF_FLAG_* */
   long long workspace_bytes;
@@ -147,6 +163,14 @@ int bsf_set_value_bound(bsf_t h, double max_abs);
 /* BSF_STEP_D1 (default) or BSF_STEP_D1_PAPER. */
 int bsf_set_step_rule(bsf_t h, int rule);
 
+/* Set an execution option (BSF_OPT_*); it affects how, not what, the filter
+ * computes.  BSF_OPT_SCAN_MODE picks the scheme of the running sums along
+ * d3/d2/d4; BSF_OPT_WAIT_LIMIT bounds every wait of one block for another
+ * (look-back scan): when it runs out the block records BSF_ETIMEOUT in the
+ * status word and finishes without hanging (its results are then invalid).
+ * Errors: BSF_EINVAL. */
+int bsf_set_option(bsf_t h, int option, long long value);
+
 /* Solve the steps of a covariance field (device, [3][H][W] float32), then
  * synchronise: if the context was created with max_reach = -1, set R to the
  * largest tap reach and allocate the running-sum workspace.  Also records the
@@ -169,6 +193,41 @@ int bsf_preintegrate(bsf_t h, const void* img, int dtype, long long ld);
 int bsf_filter(bsf_t h, const void* img, int dtype, long long ld,
                const float* cov, int cov_kind, void* out, int out_dtype, long long ldo);
 
+/* Forward filter of the band of rows [y0, y1) only (0 <= y0 < y1 <= H).
+ * img and cov are the whole image and field ([H][ld], [3][H][W]); out
+ * receives the band's rows ([y1-y0][ldo], row 0 = image row y0).  The
+ * running sums restart at zero R rows above the band and cover its padded
+ * rows [y0 - R, y1 + R) only: every tap of a band pixel lies in that padded
+ * band, and the running sums restricted to any rectangle that holds all taps
+ * give the same finite differences (every line crosses a rectangle once), so
+ * the result equals the whole-image filter bit for bit.  This is the
+ * row-band decomposition of one image over several devices (each filters its
+ * band; no exchange in the forward).  Requires R (max_reach or a plan).
+ * Errors: as bsf_filter. */
+int bsf_filter_rows(bsf_t h, const void* img, int dtype, long long ld, const float* cov,
+                    int cov_kind, void* out, int out_dtype, long long ldo, int y0, int y1);
+
+/* Backward pass with respect to the image (adjoint of Section 1.1's
+ * BoxFilter; the paper has no backward, this is the exact transpose of the
+ * forward operator): gimg(i) = sum over the padded positions r that extend
+ * onto pixel i of sum_p gout(p) K_p(r - p) / D_p.  Runs as a scatter of
+ * w_t gout(p)/D_p at the (n+1)^4 taps of every pixel (64-bit integer
+ * reductions, order-independent), reversed n-fold running sums along d4, d2,
+ * d3, d1, and the adjoint of the boundary extension.  Fixed point: each
+ * gout(p)/D_p is quantised once, RNE(RN32(RN32(gout 2^qg) / RN32(D))), with
+ * qg = 54 - ceil(log2 max|gout|) in [0, 100] (found on the device); the
+ * result is RN32(acc) 2^-qg.
+ *   gout  device [H][ldg] float32;  cov  device [3][H][W] float32 (the field
+ *         of the forward call);  gimg device [H][ldgi] float32 (written);
+ *   gcov  NULL or device [3][H][W] float32: the integer steps of D1 are
+ *         piecewise constant in the covariance, so this gradient is zero
+ *         almost everywhere and is written as zeros.
+ * Requires a known R (plan or max_reach) and BSF_FIX64.  The first call
+ * allocates the backward workspace (synchronous).
+ * Errors: BSF_EINVAL, BSF_ESTATE, BSF_ENOMEM, BSF_ECUDA. */
+int bsf_filter_backward(bsf_t h, const float* gout, long long ldg, const float* cov, int cov_kind,
+                        float* gimg, long long ldgi, float* gcov);
+
 /* Synchronise the stream and return the first device-side error recorded
  * since the last call (BSF_ERANGE, BSF_EOVERFLOW, BSF_ECOV) or BSF_OK, then
  * clear it.  Refreshes the counters in bsf_get_info. */
@@ -181,12 +240,16 @@ const char* bsf_last_error(bsf_t h);
 int bsf_get_info(bsf_t h, bsf_info_t* info);
 
 /* Copy the integer step field of the last plan/filter into dst (device,
- * uint16 [4][H][W]: L1, L2, L3, L4 planes).  For tests and diagnostics. */
+ * uint16 [4][H][W]: L1, L2, L3, L4 planes).  The filter solves the steps
+ * inside its stencil kernel, so this solves the last covariance field passed
+ * to bsf_filter again (that device buffer must still hold it).  For tests and
+ * diagnostics. */
 int bsf_copy_steps(bsf_t h, uint16_t* dst);
 
 /* Copy the running sums S of the last pre-integration into dst (device,
- * [Hp][Wp] elements of elem_bytes each, row-major, no pitch padding).
- * For tests and diagnostics. */
+ * [Hp][Wp] elements of elem_bytes each, row-major, no pitch padding; for a
+ * band of bsf_filter_rows, its rows + 2R padded rows).  For tests and
+ * diagnostics. */
 int bsf_copy_preintegrated(bsf_t h, void* dst);
 
 /* Time every kernel phase with CUDA events recorded on the context's stream
@@ -221,7 +284,7 @@ int bsf_read_profile(bsf_t h, double* ms, int* count);
  *         steps and make the call return BSF_ERANGE)
  *   frac_bits  q in [0, 62]
  *   stream     cudaStream_t (NULL = legacy default stream)
- * Sizes whose workspace (steps, running sums, scan carries) would not fit the
+ * Sizes whose workspace (running sums, scan carries) would not fit the
  * array -- at most 2^24 pixels and 2^24 padded elements, and 24 MiB in all --
  * are rejected with BSF_ERANGE before any device work.
  * Synchronous: returns BSF_OK, a host-side error (BSF_EINVAL, BSF_ERANGE,

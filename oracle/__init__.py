@@ -20,4 +20,4 @@ gaussian  Gaussian-approximation errors of continuous box splines (Theorem 1,
 Parity status of each function is stated in its docstring; "parity unpinned"
 marks a function with no independent pin.
 """
-from . import params, kernels, modular, gaussian  # noqa: F401
+from . import params, kernels, modular, gaussian, backward  # noqa: F401

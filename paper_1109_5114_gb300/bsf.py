@@ -73,6 +73,11 @@ bsf_get_info = _fn("bsf_get_info", c_int, bsf_t, ctypes.POINTER(bsf_info_t))
 bsf_copy_steps = _fn("bsf_copy_steps", c_int, bsf_t, c_void_p)
 bsf_copy_preintegrated = _fn("bsf_copy_preintegrated", c_int, bsf_t, c_void_p)
 bsf_set_profiling = _fn("bsf_set_profiling", c_int, bsf_t, c_int)
+bsf_set_option = _fn("bsf_set_option", c_int, bsf_t, c_int, c_ll)
+bsf_filter_rows = _fn("bsf_filter_rows", c_int, bsf_t, c_void_p, c_int, c_ll, c_void_p, c_int,
+                      c_void_p, c_int, c_ll, c_int, c_int)
+bsf_filter_backward = _fn("bsf_filter_backward", c_int, bsf_t, c_void_p, c_ll, c_void_p, c_int,
+                          c_void_p, c_ll, c_void_p)
 bsf_read_profile = _fn("bsf_read_profile", c_int, bsf_t, ctypes.POINTER(c_double), ctypes.POINTER(c_int))
 
 ERROR_NAMES = {v: k for k, v in _C.items() if k.startswith("BSF_E")}
@@ -184,10 +189,40 @@ class BoxSplineFilter:
         check(self._h, rc)
         return out
 
+    def filter_rows(self, img, cov, y0: int, y1: int, out=None):
+        """Rows [y0, y1) of the filtered image (float32), from the band's own running sums."""
+        import torch
+        self._stream()
+        if out is None:
+            out = torch.empty((y1 - y0, self.W), dtype=torch.float32, device=cov.device)
+        rc = bsf_filter_rows(self._h, ctypes.c_void_p(img.data_ptr()), _dtype_code(img), img.stride(0),
+                             ctypes.c_void_p(cov.data_ptr()), 0, ctypes.c_void_p(out.data_ptr()),
+                             BSF_F32 if out.dtype == torch.float32 else BSF_F64, out.stride(0), y0, y1)  # noqa: F821
+        check(self._h, rc)
+        return out
+
+    def backward(self, gout, cov, gimg=None, want_gcov=False):
+        """Image gradient (and zero covariance gradient) of the last filter."""
+        import torch
+        self._stream()
+        H, W = self.H, self.W
+        assert gout.is_cuda and gout.dtype == torch.float32 and gout.shape == (H, W) and gout.stride(1) == 1
+        if gimg is None:
+            gimg = torch.empty((H, W), dtype=torch.float32, device=gout.device)
+        gcov = torch.empty((3, H, W), dtype=torch.float32, device=gout.device) if want_gcov else None
+        rc = bsf_filter_backward(self._h, ctypes.c_void_p(gout.data_ptr()), gout.stride(0),
+                                 ctypes.c_void_p(cov.data_ptr()), 0, ctypes.c_void_p(gimg.data_ptr()),
+                                 gimg.stride(0), ctypes.c_void_p(gcov.data_ptr()) if want_gcov else None)
+        check(self._h, rc)
+        return gimg, gcov
+
     def preintegrate(self, img):
         self._stream()
         check(self._h, bsf_preintegrate(self._h, ctypes.c_void_p(img.data_ptr()), _dtype_code(img),
                                         img.stride(0)))
+
+    def set_option(self, option: int, value: int):
+        check(self._h, bsf_set_option(self._h, option, value))
 
     def set_profiling(self, on: bool = True):
         check(self._h, bsf_set_profiling(self._h, 1 if on else 0))
@@ -200,7 +235,7 @@ class BoxSplineFilter:
         rc = bsf_read_profile(self._h, ms, cnt)
         if rc < 0:
             check(self._h, rc)
-        names = ["steps", "rows", "d3", "d2", "d4", "stencil"]
+        names = ["steps", "rows", "d3", "d2", "d4", "stencil", "bwd_scatter", "bwd_scans", "bwd_fold"]
         return {names[i]: (ms[i], cnt[i]) for i in range(n)}
 
     def status(self) -> int:
@@ -226,3 +261,37 @@ class BoxSplineFilter:
         self._stream()
         check(self._h, bsf_copy_preintegrated(self._h, ctypes.c_void_p(dst.data_ptr())))
         return dst, inf
+
+
+def _make_autograd():
+    import torch
+
+    class BoxSplineFilterFunction(torch.autograd.Function):
+        """out = filter(img, cov); backward gives d/dimg through the library's
+        adjoint kernels (the D1 steps are piecewise constant, so d/dcov = 0)."""
+
+        @staticmethod
+        def forward(ctx, img, cov, filt):
+            out = filt.filter(img.contiguous(), cov.contiguous())
+            ctx.filt = filt
+            ctx.save_for_backward(cov)
+            return out
+
+        @staticmethod
+        def backward(ctx, gout):
+            (cov,) = ctx.saved_tensors
+            gimg, gcov = ctx.filt.backward(gout.contiguous().float(), cov,
+                                           want_gcov=ctx.needs_input_grad[1])
+            return gimg, gcov, None
+
+    return BoxSplineFilterFunction
+
+
+def box_spline_filter(img, cov, filt: "BoxSplineFilter"):
+    """Differentiable forward filter (torch.autograd) through the library."""
+    global _AUTOGRAD
+    try:
+        fn = _AUTOGRAD
+    except NameError:
+        fn = _AUTOGRAD = _make_autograd()
+    return fn.apply(img, cov, filt)

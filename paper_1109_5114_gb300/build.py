@@ -26,7 +26,8 @@ COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
 # contraction of multiplies and adds into fused multiply-adds in that unit.
 EXTRA = {"bsf_steps.cu": ["-fmad=false"]}
 
-SOURCES = ["bsf_api.cu", "bsf_steps.cu", "bsf_scan.cu", "bsf_stencil.cu", "bsf_noalloc.cu"]
+SOURCES = ["bsf_api.cu", "bsf_steps.cu", "bsf_scan.cu", "bsf_stencil.cu", "bsf_backward.cu",
+           "bsf_noalloc.cu"]
 
 
 def nvcc() -> str:

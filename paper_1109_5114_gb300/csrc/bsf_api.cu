@@ -30,14 +30,28 @@ struct bsf_ctx {
   void* agg = nullptr;
   void* carry = nullptr;
   size_t scan_bytes = 0;
+  void* G = nullptr;               // backward: adjoint running sums [Hp][pitch] (uint64)
+  void* Gx = nullptr;              // backward: row-folded [Hp][W]
+  size_t G_bytes = 0, Gx_bytes = 0;
+  unsigned* sync_words = nullptr;  // look-back ticket + tile flags
+  size_t sync_bytes = 0;
+  int scan_mode = BSF_SCAN_THREE_PHASE;
+  int scan_chunk = kScanChunk;   // rows per chunk, three-phase scan
+  int short_tiles = 0;           // look-back tiles of half height
+  int wait_limit = 1 << 20;
+  int test_unpublished = 0;
   ushort4* Lf = nullptr;
   DevStatus* st = nullptr;
   DevStatus host_st{};
 
   bool planned = false;      // a step solve has set R and the mass bound
   double plan_mass = 1.0;    // largest prod L^n of the plan
+  int plan_reach = -1;       // largest tap reach of the plan
+  const float* last_cov = nullptr;  // covariance of the last filter call (bsf_copy_steps)
+  bool steps_current = false;       // Lf holds the steps of last_cov
   bool have_S = false;       // S holds a pre-integration made with (R, elem, q)
   int S_R = -1, S_elem = 0, S_q = -1;
+  int S_row0 = 0, S_rows = 0;        // image rows the held running sums cover
   char msg[512] = "ok";
 
   // phase timing (bsf_set_profiling)
@@ -78,7 +92,14 @@ void free_workspace(bsf_t h) {
   if (h->S) cudaFree(h->S);
   if (h->agg) cudaFree(h->agg);
   if (h->carry) cudaFree(h->carry);
+  if (h->sync_words) cudaFree(h->sync_words);
+  if (h->G) cudaFree(h->G);
+  if (h->Gx) cudaFree(h->Gx);
+  h->G = h->Gx = nullptr;
+  h->G_bytes = h->Gx_bytes = 0;
   h->S = h->agg = h->carry = nullptr;
+  h->sync_words = nullptr;
+  h->sync_bytes = 0;
   h->S_bytes = h->scan_bytes = 0;
   h->have_S = false;
 }
@@ -90,8 +111,13 @@ int ensure_workspace(bsf_t h) {
   const long long align = 256 / elem;  // 256-byte aligned rows
   const long long pitch = (Wp + align - 1) / align * align;
   const size_t S_bytes = (size_t)pitch * Hp * elem;
-  const int nchunks = (Hp + kScanChunk - 1) / kScanChunk;
-  const size_t scan_bytes = (size_t)nchunks * h->n * (size_t)(Wp + Hp - 1) * elem;
+  if ((long long)pitch * Hp >= (1LL << 31))
+    return fail(h, BSF_EINVAL, "padded domain of %lld elements exceeds 2^31", (long long)pitch * Hp);
+  const int nchunks = (Hp + kScanChunkMin - 1) / kScanChunkMin;
+  size_t sync_bytes = 0;
+  size_t scan_bytes = (size_t)nchunks * h->n * (size_t)(Wp + Hp - 1) * elem;
+  const size_t lb_bytes = bsf_vscan_lb_bytes(elem, h->n, Hp, Wp, &sync_bytes);
+  if (lb_bytes > scan_bytes) scan_bytes = lb_bytes;
   if (h->S && h->S_bytes == S_bytes && h->scan_bytes == scan_bytes && h->Hp == Hp &&
       h->Wp == Wp && h->elem == elem)
     return BSF_OK;
@@ -100,6 +126,8 @@ int ensure_workspace(bsf_t h) {
   BSF_CUDA(h, cudaMalloc(&h->S, S_bytes));
   BSF_CUDA(h, cudaMalloc(&h->agg, scan_bytes));
   BSF_CUDA(h, cudaMalloc(&h->carry, scan_bytes));
+  BSF_CUDA(h, cudaMalloc(&h->sync_words, sync_bytes));
+  h->sync_bytes = sync_bytes;
   h->S_bytes = S_bytes;
   h->scan_bytes = scan_bytes;
   h->Hp = Hp;
@@ -178,9 +206,12 @@ int run_steps(bsf_t h, const float* cov, int cov_kind, bool sync_plan) {
                          h->Lf, h->st, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "steps kernel");
+  h->last_cov = cov;
+  h->steps_current = true;
   if (sync_plan) {
     if ((rc = read_status(h))) return rc;
     h->plan_mass = bits_to_float(h->host_st.max_mass_bits);
+    h->plan_reach = h->host_st.max_reach;
     if (!h->R_fixed) {
       // the solve ran unbounded: every tap of this field fits this R
       h->R = h->host_st.max_reach > 3 * h->n ? h->host_st.max_reach : 3 * h->n;
@@ -225,7 +256,9 @@ int resolve_q(bsf_t h, const void* img, int dtype, long long ld) {
   return BSF_OK;
 }
 
-int preintegrate_impl(bsf_t h, const void* img, int dtype, long long ld) {
+// Running sums of the band of image rows [row0, row0 + rows) (the whole
+// image: row0 = 0, rows = H) on its padded domain of rows + 2R rows.
+int preintegrate_impl(bsf_t h, const void* img, int dtype, long long ld, int row0, int rows) {
   if (!img) return fail(h, BSF_EINVAL, "img is NULL");
   if (dtype != BSF_U8 && dtype != BSF_F32 && dtype != BSF_F64)
     return fail(h, BSF_EINVAL, "bad image dtype %d", dtype);
@@ -235,11 +268,12 @@ int preintegrate_impl(bsf_t h, const void* img, int dtype, long long ld) {
   if ((rc = ensure_workspace(h))) return rc;
   if ((rc = resolve_q(h, img, dtype, ld))) return rc;
   if ((rc = reset_counters(h, false, true))) return rc;
+  const int Hb = rows + 2 * h->R;  // padded rows of the band
   cudaError_t e;
   {
     PhaseTimer t(h, BSF_PHASE_ROWS);
-    e = bsf_launch_scan_rows(h->elem, h->n, img, dtype, ld, h->H, h->W, h->R, h->boundary, h->q,
-                             h->S, h->pitch, h->Hp, h->Wp, h->st, h->stream);
+    e = bsf_launch_scan_rows(h->elem, h->n, img, dtype, ld, h->H, h->W, h->R, row0, h->boundary,
+                             h->q, h->S, h->pitch, Hb, h->Wp, h->st, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "row scan");
   // d3, d2, d4
@@ -247,14 +281,21 @@ int preintegrate_impl(bsf_t h, const void* img, int dtype, long long ld) {
   const int phases[3] = {BSF_PHASE_D3, BSF_PHASE_D2, BSF_PHASE_D4};
   for (int i = 0; i < 3; ++i) {
     PhaseTimer t(h, phases[i]);
-    e = bsf_launch_vscan(h->elem, h->n, skews[i], h->S, h->pitch, h->Hp, h->Wp, h->agg, h->carry,
-                         h->stream);
+    if (h->scan_mode == BSF_SCAN_LOOKBACK)
+      e = bsf_launch_vscan_lb(h->elem, h->n, skews[i], false, h->short_tiles != 0, h->S, h->pitch,
+                              Hb, h->Wp, h->agg, h->carry, h->sync_words, h->wait_limit,
+                              h->test_unpublished, h->st, h->stream);
+    else
+      e = bsf_launch_vscan(h->elem, h->n, skews[i], false, h->S, h->pitch, Hb, h->Wp,
+                           h->scan_chunk, h->agg, h->carry, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "vertical scan");
   }
   h->have_S = true;
   h->S_R = h->R;
   h->S_elem = h->elem;
   h->S_q = h->q;
+  h->S_row0 = row0;
+  h->S_rows = rows;
   return BSF_OK;
 }
 
@@ -337,6 +378,33 @@ int bsf_set_step_rule(bsf_t h, int rule) {
   return BSF_OK;
 }
 
+int bsf_set_option(bsf_t h, int option, long long value) {
+  if (!h) return BSF_EINVAL;
+  switch (option) {
+    case BSF_OPT_SCAN_MODE:
+      if (value != BSF_SCAN_LOOKBACK && value != BSF_SCAN_THREE_PHASE)
+        return fail(h, BSF_EINVAL, "bad scan mode %lld", value);
+      h->scan_mode = (int)value;
+      return BSF_OK;
+    case BSF_OPT_WAIT_LIMIT:
+      if (value < 0 || value > (1LL << 30)) return fail(h, BSF_EINVAL, "bad wait limit %lld", value);
+      h->wait_limit = (int)value;
+      return BSF_OK;
+    case BSF_OPT_SCAN_CHUNK:
+      if (value < kScanChunkMin || value > 4096) return fail(h, BSF_EINVAL, "bad scan chunk %lld", value);
+      h->scan_chunk = (int)value;
+      return BSF_OK;
+    case BSF_OPT_SCAN_SHORT_TILES:
+      h->short_tiles = value != 0;
+      return BSF_OK;
+    case BSF_OPT_TEST_UNPUBLISHED:
+      h->test_unpublished = value != 0;
+      return BSF_OK;
+    default:
+      return fail(h, BSF_EINVAL, "unknown option %d", option);
+  }
+}
+
 int bsf_plan(bsf_t h, const float* cov, int cov_kind) {
   if (!h) return BSF_EINVAL;
   return run_steps(h, cov, cov_kind, true);
@@ -344,30 +412,113 @@ int bsf_plan(bsf_t h, const float* cov, int cov_kind) {
 
 int bsf_preintegrate(bsf_t h, const void* img, int dtype, long long ld) {
   if (!h) return BSF_EINVAL;
-  return preintegrate_impl(h, img, dtype, ld);
+  return preintegrate_impl(h, img, dtype, ld, 0, h->H);
 }
 
-int bsf_filter(bsf_t h, const void* img, int dtype, long long ld, const float* cov, int cov_kind,
-               void* out, int out_dtype, long long ldo) {
+static int filter_impl(bsf_t h, const void* img, int dtype, long long ld, const float* cov,
+                       int cov_kind, void* out, int out_dtype, long long ldo, int row0, int rows) {
   if (!h) return BSF_EINVAL;
   if (!out) return fail(h, BSF_EINVAL, "out is NULL");
   if (out_dtype != BSF_F32 && out_dtype != BSF_F64) return fail(h, BSF_EINVAL, "bad out dtype %d", out_dtype);
   if (ldo < h->W) return fail(h, BSF_EINVAL, "ldo %lld < W %d", ldo, h->W);
-  int rc;
+  if (row0 < 0 || rows <= 0 || row0 + rows > h->H) return fail(h, BSF_EINVAL, "bad row band");
+  int rc = check_cov_kind(h, cov_kind);
+  if (rc) return rc;
+  if (!cov) return fail(h, BSF_EINVAL, "cov is NULL");
+  // the step field itself is solved inside the stencil; a separate solve
+  // runs only to plan R and the mass bound
   const bool need_plan = h->R < 0 || (img && h->frac_req < 0 && !h->planned);
-  if ((rc = run_steps(h, cov, cov_kind, need_plan))) return rc;
+  if (need_plan) {
+    if ((rc = run_steps(h, cov, cov_kind, true))) return rc;
+  }
+  if ((rc = reset_counters(h, true, false))) return rc;
   if (img) {
-    if ((rc = preintegrate_impl(h, img, dtype, ld))) return rc;
-  } else if (!h->have_S || h->S_R != h->R || h->S_elem != h->elem) {
+    if ((rc = preintegrate_impl(h, img, dtype, ld, row0, rows))) return rc;
+  } else if (!h->have_S || h->S_R != h->R || h->S_elem != h->elem || h->S_row0 != row0 ||
+             h->S_rows != rows) {
     return fail(h, BSF_ESTATE, "img is NULL and no matching pre-integration is held");
   }
   cudaError_t e;
   {
     PhaseTimer t(h, BSF_PHASE_STENCIL);
-    e = bsf_launch_stencil_d1(h->elem, h->n, h->S, h->pitch, h->R, h->Lf, h->H, h->W, h->S_q, out,
-                              out_dtype, ldo, h->st, h->stream);
+    e = bsf_launch_stencil_d1(h->elem, h->n, h->S, h->pitch, h->R, cov, h->step_rule, h->H, h->W,
+                              row0, rows, h->S_q, out, out_dtype, ldo, h->st, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "stencil");
+  if (h->last_cov != cov) h->steps_current = false;
+  h->last_cov = cov;
+  return BSF_OK;
+}
+
+int bsf_filter(bsf_t h, const void* img, int dtype, long long ld, const float* cov, int cov_kind,
+               void* out, int out_dtype, long long ldo) {
+  if (!h) return BSF_EINVAL;
+  return filter_impl(h, img, dtype, ld, cov, cov_kind, out, out_dtype, ldo, 0, h->H);
+}
+
+int bsf_filter_rows(bsf_t h, const void* img, int dtype, long long ld, const float* cov,
+                    int cov_kind, void* out, int out_dtype, long long ldo, int y0, int y1) {
+  if (!h) return BSF_EINVAL;
+  if (!img) return fail(h, BSF_EINVAL, "img is NULL");
+  return filter_impl(h, img, dtype, ld, cov, cov_kind, out, out_dtype, ldo, y0, y1 - y0);
+}
+
+int bsf_filter_backward(bsf_t h, const float* gout, long long ldg, const float* cov, int cov_kind,
+                        float* gimg, long long ldgi, float* gcov) {
+  if (!h) return BSF_EINVAL;
+  int rc = check_cov_kind(h, cov_kind);
+  if (rc) return rc;
+  if (!gout || !cov || !gimg) return fail(h, BSF_EINVAL, "NULL gout, cov or gimg");
+  if (ldg < h->W || ldgi < h->W) return fail(h, BSF_EINVAL, "leading dimension < W");
+  if (h->precision != BSF_FIX64) return fail(h, BSF_EINVAL, "backward needs BSF_FIX64");
+  if (h->R < 0) return fail(h, BSF_ESTATE, "padding unknown: plan or filter first");
+  if ((rc = ensure_workspace(h))) return rc;
+  const size_t G_bytes = (size_t)h->pitch * h->Hp * 8, Gx_bytes = (size_t)h->Hp * h->W * 8;
+  if (h->G_bytes != G_bytes || h->Gx_bytes != Gx_bytes) {
+    BSF_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->G) cudaFree(h->G);
+    if (h->Gx) cudaFree(h->Gx);
+    h->G = h->Gx = nullptr;
+    h->G_bytes = h->Gx_bytes = 0;
+    BSF_CUDA(h, cudaMalloc(&h->G, G_bytes));
+    BSF_CUDA(h, cudaMalloc(&h->Gx, Gx_bytes));
+    h->G_bytes = G_bytes;
+    h->Gx_bytes = Gx_bytes;
+  }
+  if ((rc = reset_counters(h, true, false))) return rc;
+  cudaError_t e;
+  {
+    PhaseTimer t(h, BSF_PHASE_BWD_SCATTER);
+    BSF_CUDA(h, cudaMemsetAsync(&h->st->max_absg_bits, 0, sizeof(unsigned), h->stream));
+    BSF_CUDA(h, cudaMemsetAsync(h->G, 0, G_bytes, h->stream));
+    e = bsf_launch_gabsmax(gout, ldg, h->H, h->W, h->st, h->stream);
+    if (e == cudaSuccess)
+      e = bsf_launch_scatter_d1(h->n, h->G, h->pitch, h->R, cov, h->step_rule, gout, ldg, h->H,
+                                h->W, h->st, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "backward scatter");
+  {
+    PhaseTimer t(h, BSF_PHASE_BWD_SCANS);
+    const int skews[3] = {-1, 1, 0};  // transposes in reverse order: d4, d2, d3
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+      if (h->scan_mode == BSF_SCAN_LOOKBACK)
+        e = bsf_launch_vscan_lb(8, h->n, skews[i], true, h->short_tiles != 0, h->G, h->pitch,
+                                h->Hp, h->Wp, h->agg, h->carry, h->sync_words, h->wait_limit, 0,
+                                h->st, h->stream);
+      else
+        e = bsf_launch_vscan(8, h->n, skews[i], true, h->G, h->pitch, h->Hp, h->Wp, h->scan_chunk,
+                             h->agg, h->carry, h->stream);
+    }
+    if (e == cudaSuccess) e = bsf_launch_suffix_rows(8, h->n, h->G, h->pitch, h->Hp, h->Wp, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "backward running sums");
+  {
+    PhaseTimer t(h, BSF_PHASE_BWD_FOLD);
+    e = bsf_launch_fold(h->G, h->pitch, h->Hp, h->H, h->W, h->R, h->boundary, h->Gx, gimg, ldgi,
+                        h->st, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "backward fold");
+  if (gcov) BSF_CUDA(h, cudaMemsetAsync(gcov, 0, (size_t)3 * h->H * h->W * sizeof(float), h->stream));
   return BSF_OK;
 }
 
@@ -401,17 +552,25 @@ int bsf_get_info(bsf_t h, bsf_info_t* info) {
   info->precision = h->precision;
   info->frac_bits = h->q;
   info->step_rule = h->step_rule;
-  info->max_reach = h->host_st.max_reach;
-  info->max_mass = bits_to_float(h->host_st.max_mass_bits);
+  info->max_reach = h->plan_reach;
+  info->max_mass = h->plan_mass;
   info->clamp_count = h->host_st.clamp_count;
   info->flags = h->host_st.clamp_count ? BSF_FLAG_CLAMPED : 0u;
-  info->workspace_bytes = (long long)(h->S_bytes + 2 * h->scan_bytes) +
+  info->workspace_bytes = (long long)(h->S_bytes + 2 * h->scan_bytes + h->sync_bytes + h->G_bytes + h->Gx_bytes) +
                           (long long)h->H * h->W * (long long)sizeof(ushort4) + (long long)sizeof(DevStatus);
   return BSF_OK;
 }
 
 int bsf_copy_steps(bsf_t h, uint16_t* dst) {
   if (!h || !dst) return BSF_EINVAL;
+  if (!h->last_cov) return fail(h, BSF_ESTATE, "no covariance seen yet");
+  if (!h->steps_current) {  // solve the last field again (it must still be valid)
+    const bool planned = h->planned;
+    h->planned = true;  // bounded by the current R, no plan
+    int rc = run_steps(h, h->last_cov, BSF_COV_C, false);
+    h->planned = planned;
+    if (rc) return rc;
+  }
   const size_t HW = (size_t)h->H * h->W;
   for (int k = 0; k < 4; ++k) {
     BSF_CUDA(h, cudaMemcpy2DAsync(dst + k * HW, sizeof(uint16_t),
@@ -426,7 +585,8 @@ int bsf_copy_preintegrated(bsf_t h, void* dst) {
   if (!h || !dst) return BSF_EINVAL;
   if (!h->have_S) return fail(h, BSF_ESTATE, "no pre-integration held");
   BSF_CUDA(h, cudaMemcpy2DAsync(dst, (size_t)h->Wp * h->elem, h->S, (size_t)h->pitch * h->elem,
-                                (size_t)h->Wp * h->elem, h->Hp, cudaMemcpyDeviceToDevice, h->stream));
+                                (size_t)h->Wp * h->elem, h->S_rows + 2 * h->S_R,
+                                cudaMemcpyDeviceToDevice, h->stream));
   return BSF_OK;
 }
 

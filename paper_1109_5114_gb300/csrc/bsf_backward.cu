@@ -1,0 +1,174 @@
+// Backward pass of the D1 filter with respect to the image: the transpose of
+// the forward pipeline (Section 1.1's BoxFilter: extension, running sums,
+// finite differences), read backwards.
+//
+//   forward:   out(p) = sum_t w_t S(tap_t(p)) / D_p,  S = C4^n C2^n C3^n C1^n E f
+//   backward:  G = sum_p (gout(p)/D_p) sum_t w_t delta_{tap_t(p)}     (scatter)
+//              G <- (C1^T)^n (C3^T)^n (C2^T)^n (C4^T)^n G                (suffix sums)
+//              gimg = E^T G                                           (extension fold)
+//
+// Fixed point: each weight gout(p)/D_p is quantised once,
+//   g(p) = RNE(RN32(RN32(gout(p) 2^qg) / RN32(D_p))),  qg = 54 - ceil(log2 max|gout|)
+// (clamped to [0, 100]; the max is reduced on the device and every thread
+// derives the same qg), the scatter adds w_t g(p) with 64-bit integer
+// reductions (exact and order-independent, hence deterministic), the suffix
+// sums wrap modulo 2^64, and gimg = RN32(acc) 2^-qg.
+#include "bsf_solve.cuh"
+
+namespace {
+
+__global__ void k_gabsmax(const float* __restrict__ g, long long ld, int H, int W, DevStatus* st) {
+  float m = 0.f;
+  const long long HW = (long long)H * W;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HW;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long y = i / W, x = i - y * W;
+    m = fmaxf(m, fabsf(g[y * ld + x]));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) bsf_atomic_max_pos_float(&st->max_absg_bits, m);
+}
+
+// qg from the float32 bits of max|gout|: 54 - ceil(log2 m), clamped to [0, 100]
+__device__ __forceinline__ int grad_q(unsigned mbits) {
+  const unsigned E = (mbits >> 23) & 0xffu, M = mbits & 0x7fffffu;
+  int c;
+  if (E == 0 || E == 0xffu) c = E == 0 && M != 0 ? -126 : 0;  // subnormal / zero / non-finite
+  else c = (int)E - 127 + (M != 0 ? 1 : 0);
+  const int q = 54 - c;
+  return q < 0 ? 0 : (q > 100 ? 100 : q);
+}
+
+template <int NF, int LVL>
+__device__ __forceinline__ void scatter(unsigned long long* p, const long long* s,
+                                        unsigned long long v) {
+  if constexpr (LVL == 0) {
+    atomicAdd(p, v);
+  } else {
+    const long long sk = s[LVL - 1];
+    scatter<NF, LVL - 1>(p, s, v);
+    if constexpr (NF == 1) {
+      scatter<NF, LVL - 1>(p - sk, s, 0ull - v);
+    } else if constexpr (NF == 2) {
+      scatter<NF, LVL - 1>(p - sk, s, 0ull - (v << 1));
+      scatter<NF, LVL - 1>(p - 2 * sk, s, v);
+    } else {
+      scatter<NF, LVL - 1>(p - sk, s, 0ull - 3ull * v);
+      scatter<NF, LVL - 1>(p - 2 * sk, s, 3ull * v);
+      scatter<NF, LVL - 1>(p - 3 * sk, s, 0ull - v);
+    }
+  }
+}
+
+template <int NF>
+__global__ void __launch_bounds__(256)
+k_scatter_d1(unsigned long long* __restrict__ G, long long pitch, int R,
+             const float* __restrict__ cov, int rule, const float* __restrict__ gout,
+             long long ldg, int H, int W, DevStatus* st) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= W || y >= H) return;
+  const long long HW = (long long)H * W, i = (long long)y * W + x;
+  int L[4], flags, reach;
+  bsf_solve::pixel_steps(cov[i], cov[HW + i], cov[2 * HW + i], NF, rule, R, L, flags, reach);
+  const int qg = grad_q(st->max_absg_bits);
+  unsigned long long D = (unsigned long long)(L[0] * L[1]) * (unsigned long long)(L[2] * L[3]);
+  const unsigned long long D1 = D;
+#pragma unroll
+  for (int j = 1; j < NF; ++j) D *= D1;
+  const float xg = __fmul_rn(gout[(long long)y * ldg + x], bsf_pow2_f32(qg));  // exact scaling
+  bool ok;
+  const unsigned long long g =
+      bsf_quantize_f32<unsigned long long>(__fdiv_rn(xg, bsf_rn32_u64(D)), 0, ok);
+  if (!ok) bsf_set_error(st, BSF_EOVERFLOW);
+  if (g == 0) return;
+  const long long L1 = L[0], L2 = L[1], L3 = L[2], L4 = L[3];
+  const long long e1 = 1, e2 = pitch + 1, e3 = pitch, e4 = pitch - 1;
+  const long long c1 = NF * (L1 - 1) / 2, c2 = NF * (L2 - 1) / 2, c3 = NF * (L3 - 1) / 2,
+                  c4 = NF * (L4 - 1) / 2;
+  unsigned long long* base =
+      G + (long long)(y + R) * pitch + (x + R) + c1 * e1 + c2 * e2 + c3 * e3 + c4 * e4;
+  const long long s[4] = {L1 * e1, L2 * e2, L3 * e3, L4 * e4};
+  scatter<NF, 4>(base, s, g);
+}
+
+// Padded coordinates z in [-R, N + R) whose extension maps onto image
+// coordinate i, visited as padded indices z + R.
+template <typename F>
+__device__ __forceinline__ void for_preimages(int i, int N, int R, int boundary, F&& f) {
+  if (boundary == BSF_ZERO) {
+    f(i + R);
+  } else if (boundary == BSF_REPLICATE) {
+    const int lo = i == 0 ? -R : i, hi = i == N - 1 ? N - 1 + R : i;
+    for (int z = lo; z <= hi; ++z) f(z + R);
+  } else {  // half-sample symmetric: z = i + 2kN or z = 2kN - 1 - i
+    const int P = 2 * N;
+    for (int fam = 0; fam < 2; ++fam) {
+      const int b = fam == 0 ? i : P - 1 - i;  // representative in [0, 2N)
+      // smallest z >= -R with z = b (mod 2N)
+      int z = b - ((b + R + P - 1) / P) * P;
+      if (z < -R) z += P;
+      for (; z < N + R; z += P) f(z + R);
+    }
+  }
+}
+
+__global__ void k_fold_x(const unsigned long long* __restrict__ G, long long pitch, int Hp, int W,
+                         int R, int boundary, unsigned long long* __restrict__ Gx) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int yr = blockIdx.y;
+  if (x >= W || yr >= Hp) return;
+  const unsigned long long* row = G + (long long)yr * pitch;
+  unsigned long long acc = 0;
+  for_preimages(x, W, R, boundary, [&](int xp) { acc += row[xp]; });
+  Gx[(long long)yr * W + x] = acc;
+}
+
+__global__ void k_fold_y_out(const unsigned long long* __restrict__ Gx, int H, int W, int R,
+                             int boundary, float* __restrict__ gimg, long long ldo,
+                             const DevStatus* st) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= W || y >= H) return;
+  unsigned long long acc = 0;
+  for_preimages(y, H, R, boundary, [&](int yp) { acc += Gx[(long long)yp * W + x]; });
+  const int qg = grad_q(st->max_absg_bits);
+  gimg[(long long)y * ldo + x] = __fmul_rn(bsf_rn32_i64((long long)acc), bsf_pow2_f32(-qg));
+}
+
+int grid_for(long long work, int threads) {
+  long long g = (work + threads - 1) / threads;
+  const long long cap = 152LL * 16;
+  return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+}  // namespace
+
+cudaError_t bsf_launch_gabsmax(const float* gout, long long ldg, int H, int W, DevStatus* st,
+                               cudaStream_t s) {
+  k_gabsmax<<<grid_for((long long)H * W, 256), 256, 0, s>>>(gout, ldg, H, W, st);
+  return cudaGetLastError();
+}
+
+cudaError_t bsf_launch_scatter_d1(int n, void* G, long long pitch, int R, const float* cov,
+                                  int rule, const float* gout, long long ldg, int H, int W,
+                                  DevStatus* st, cudaStream_t s) {
+  dim3 block(32, 8), grid((W + 31) / 32, (H + 7) / 8);
+  auto* g = (unsigned long long*)G;
+  if (n == 1) k_scatter_d1<1><<<grid, block, 0, s>>>(g, pitch, R, cov, rule, gout, ldg, H, W, st);
+  else if (n == 2) k_scatter_d1<2><<<grid, block, 0, s>>>(g, pitch, R, cov, rule, gout, ldg, H, W, st);
+  else if (n == 3) k_scatter_d1<3><<<grid, block, 0, s>>>(g, pitch, R, cov, rule, gout, ldg, H, W, st);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t bsf_launch_fold(const void* G, long long pitch, int Hp, int H, int W, int R,
+                            int boundary, void* Gx, float* gimg, long long ldo, const DevStatus* st,
+                            cudaStream_t s) {
+  dim3 blk(128);
+  k_fold_x<<<dim3((W + 127) / 128, Hp), blk, 0, s>>>((const unsigned long long*)G, pitch, Hp, W,
+                                                      R, boundary, (unsigned long long*)Gx);
+  k_fold_y_out<<<dim3((W + 127) / 128, H), blk, 0, s>>>((const unsigned long long*)Gx, H, W, R,
+                                                         boundary, gimg, ldo, st);
+  return cudaGetLastError();
+}

@@ -19,10 +19,13 @@ struct DevStatus {
   unsigned max_mass_bits;           // float32 bits of the largest prod L^n (non-negative)
   unsigned max_absq_bits;           // float32 bits of an upper bound of max |Q(f)|
   unsigned long long max_absf_bits; // float64 bits of max |f| (value reduction kernel)
+  unsigned max_absg_bits;           // float32 bits of max |gout| (backward)
 };
 
-// Scan chunk height (rows per chunk) of the vertical running sums.
+// Default and smallest chunk height (rows per chunk) of the three-phase
+// vertical running sums; workspace is sized for the smallest.
 constexpr int kScanChunk = 64;
+constexpr int kScanChunkMin = 16;
 
 // Launchers; each returns the launch status (cudaGetLastError()).
 cudaError_t bsf_launch_steps(const float* cov, int cov_kind, int H, int W, int n, int rule,
@@ -31,15 +34,45 @@ cudaError_t bsf_launch_steps(const float* cov, int cov_kind, int H, int W, int n
 cudaError_t bsf_launch_absmax(const void* img, int dtype, long long ld, int H, int W,
                               DevStatus* st, cudaStream_t s);
 
+// Row running sums of image rows row0 - R .. row0 - R + Hp - 1 (extended).
 cudaError_t bsf_launch_scan_rows(int elem_bytes, int n, const void* img, int dtype, long long ld,
-                                 int H, int W, int R, int boundary, int q, void* S,
+                                 int H, int W, int R, int row0, int boundary, int q, void* S,
                                  long long pitch, int Hp, int Wp, DevStatus* st, cudaStream_t s);
 
 // Vertical running sums along d3 (skew 0), d2 (skew +1), d4 (skew -1), in place
 // on S.  agg and carry each hold nchunks * n * Nu elements, Nu = Wp + Hp - 1.
-cudaError_t bsf_launch_vscan(int elem_bytes, int n, int skew, void* S, long long pitch,
-                             int Hp, int Wp, void* agg, void* carry, cudaStream_t s);
+cudaError_t bsf_launch_vscan(int elem_bytes, int n, int skew, bool reverse, void* S, long long pitch,
+                             int Hp, int Wp, int chunk, void* agg, void* carry, cudaStream_t s);
 
+// Single-pass vertical running sums (decoupled look-back).  aggs and incls
+// each hold bsf_vscan_lb_bytes() bytes; sync_words holds *sync_bytes (zeroed
+// by the launcher).  Waits poll at most spin_limit times.
+size_t bsf_vscan_lb_bytes(int elem_bytes, int n, int Hp, int Wp, size_t* sync_bytes);
+// reverse: suffix sums (the transpose).  test_unpublished != 0 leaves the
+// first chunk's flags unset (failure injection).
+cudaError_t bsf_launch_vscan_lb(int elem_bytes, int n, int skew, bool reverse, bool short_tiles,
+                                void* S, long long pitch, int Hp, int Wp, void* aggs, void* incls,
+                                unsigned* sync_words, int spin_limit, int test_unpublished,
+                                DevStatus* st, cudaStream_t s);
+
+// In-place n-fold suffix sums along each padded row (transpose of the d1 sum).
+cudaError_t bsf_launch_suffix_rows(int elem_bytes, int n, void* S, long long pitch, int Hp, int Wp,
+                                   cudaStream_t s);
+
+// Backward of the D1 filter (uint64): max|gout| reduction, tap scatter into G
+// (zeroed by the caller), extension fold of G (via Gx: [Hp][W]) into gimg.
+cudaError_t bsf_launch_gabsmax(const float* gout, long long ldg, int H, int W, DevStatus* st,
+                               cudaStream_t s);
+cudaError_t bsf_launch_scatter_d1(int n, void* G, long long pitch, int R, const float* cov,
+                                  int rule, const float* gout, long long ldg, int H, int W,
+                                  DevStatus* st, cudaStream_t s);
+cudaError_t bsf_launch_fold(const void* G, long long pitch, int Hp, int H, int W, int R,
+                            int boundary, void* Gx, float* gimg, long long ldo, const DevStatus* st,
+                            cudaStream_t s);
+
+// Finite differences with the per-pixel step solve fused in (cov: [3][H][W]).
+// Output rows row0 .. row0 + rows - 1 of an H x W image (S holds that band).
 cudaError_t bsf_launch_stencil_d1(int elem_bytes, int n, const void* S, long long pitch, int R,
-                                  const ushort4* Lf, int H, int W, int q, void* out,
-                                  int out_dtype, long long ldo, DevStatus* st, cudaStream_t s);
+                                  const float* cov, int rule, int H, int W, int row0, int rows,
+                                  int q, void* out, int out_dtype, long long ldo, DevStatus* st,
+                                  cudaStream_t s);

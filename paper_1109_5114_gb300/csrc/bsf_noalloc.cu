@@ -65,12 +65,11 @@ extern "C" int bsf_filter_noalloc(const void* img, int dtype, long long ld, int 
   if (out_dtype != BSF_F32 && out_dtype != BSF_F64) return BSF_EINVAL;
   if (ld < W || ldo < W || reach < 3 * n || frac_bits < 0 || frac_bits > 62) return BSF_EINVAL;
 
-  // carve the scratch: status | steps [H][W] | S [Hp][pitch] | agg | carry
+  // carve the scratch: status | S [Hp][pitch] | agg | carry
   const long long Hp = (long long)H + 2LL * reach, Wp = (long long)W + 2LL * reach;
   const long long pitch = round_up((size_t)Wp, 32);
   const long long nchunks = (Hp + kScanChunk - 1) / kScanChunk;
-  const size_t off_steps = round_up(sizeof(DevStatus), 256);
-  const size_t off_S = off_steps + round_up((size_t)H * W * sizeof(ushort4), 256);
+  const size_t off_S = round_up(sizeof(DevStatus), 256);
   const size_t scan_bytes = (size_t)nchunks * n * (size_t)(Wp + Hp - 1) * 8;
   const size_t off_agg = off_S + round_up((size_t)pitch * Hp * 8, 256);
   const size_t off_carry = off_agg + round_up(scan_bytes, 256);
@@ -83,7 +82,6 @@ extern "C" int bsf_filter_noalloc(const void* img, int dtype, long long ld, int 
   cudaStream_t s = (cudaStream_t)stream;
   unsigned char* b = static_cast<unsigned char*>(base);
   DevStatus* st = reinterpret_cast<DevStatus*>(b);
-  ushort4* Lf = reinterpret_cast<ushort4*>(b + off_steps);
   void* S = b + off_S;
   void* agg = b + off_agg;
   void* carry = b + off_carry;
@@ -91,17 +89,16 @@ extern "C" int bsf_filter_noalloc(const void* img, int dtype, long long ld, int 
   // the status word must start from zero; everything else is fully written
   // before it is read
   if (cudaMemsetAsync(st, 0, sizeof(DevStatus), s) != cudaSuccess) return BSF_ECUDA;
-  if (bsf_launch_steps(cov, BSF_COV_C, H, W, n, BSF_STEP_D1, reach, Lf, st, s) != cudaSuccess)
-    return BSF_ECUDA;
-  if (bsf_launch_scan_rows(8, n, img, dtype, ld, H, W, reach, boundary, frac_bits, S, pitch,
+  if (bsf_launch_scan_rows(8, n, img, dtype, ld, H, W, reach, 0, boundary, frac_bits, S, pitch,
                            (int)Hp, (int)Wp, st, s) != cudaSuccess)
     return BSF_ECUDA;
   const int skews[3] = {0, 1, -1};
   for (int i = 0; i < 3; ++i)
-    if (bsf_launch_vscan(8, n, skews[i], S, pitch, (int)Hp, (int)Wp, agg, carry, s) != cudaSuccess)
+    if (bsf_launch_vscan(8, n, skews[i], false, S, pitch, (int)Hp, (int)Wp, kScanChunk, agg, carry, s) !=
+        cudaSuccess)
       return BSF_ECUDA;
-  if (bsf_launch_stencil_d1(8, n, S, pitch, reach, Lf, H, W, frac_bits, out, out_dtype, ldo, st,
-                            s) != cudaSuccess)
+  if (bsf_launch_stencil_d1(8, n, S, pitch, reach, cov, BSF_STEP_D1, H, W, 0, H, frac_bits, out,
+                            out_dtype, ldo, st, s) != cudaSuccess)
     return BSF_ECUDA;
 
   // synchronous: report the device-side status of this call

@@ -17,7 +17,8 @@
 //                  s'_f = sum_{j<=f} C(m-1+j, j) s_{f-j} + agg_f;
 //         apply -- per (line, chunk): rescan with the carried-in state and
 //                  write the result in place.
-//       No block waits on another block.
+//       No block waits on another block.  (The single-pass look-back variant
+//       below is the default; this one needs no inter-block waits.)
 //
 // Arithmetic wraps modulo 2^64 or 2^128 (the element type), which the final
 // finite differences cancel exactly.
@@ -51,7 +52,7 @@ __device__ __forceinline__ T quantize_one(In fv, int q, float scale_f, bool& ok,
 
 template <typename T, int NF, typename In, int V>
 __global__ void __launch_bounds__(kRowThreads)
-k_scan_rows(const In* __restrict__ img, long long ld, int H, int W, int R, int boundary,
+k_scan_rows(const In* __restrict__ img, long long ld, int H, int W, int R, int row0, int boundary,
             float scale_f, int q, T* __restrict__ S, long long pitch, int Hp, int Wp,
             DevStatus* st) {
   constexpr int NW = kRowThreads / 32;
@@ -59,7 +60,7 @@ k_scan_rows(const In* __restrict__ img, long long ld, int H, int W, int R, int b
   const int yp = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   bool yvalid;
-  const int ys = bsf_map_index(yp - R, H, boundary, yvalid);
+  const int ys = bsf_map_index(row0 + yp - R, H, boundary, yvalid);  // row0: first row of a band
   const In* src = img + (long long)ys * ld;
   T* row = S + (long long)yp * pitch;
   T carry[NF];
@@ -128,20 +129,21 @@ k_scan_rows(const In* __restrict__ img, long long ld, int H, int W, int R, int b
 // ---------------------------------------------------------------------------
 // d3 / d2 / d4 in skewed coordinates
 // ---------------------------------------------------------------------------
-template <typename T, int NF, int SKEW>
+template <typename T, int NF, int SKEW, bool REV>
 __global__ void __launch_bounds__(128)
-k_vscan_agg(const T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, int Nu,
+k_vscan_agg(const T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, int Nu, int ch,
             T* __restrict__ agg) {
   const int ui = blockIdx.x * blockDim.x + threadIdx.x;
   if (ui >= Nu) return;
   const int u = umin + ui;
   const int c = blockIdx.y;
-  const int y0 = c * kScanChunk, y1 = min(y0 + kScanChunk, Hp);
+  const int y0 = c * ch, y1 = min(y0 + ch, Hp);
   T s[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) s[f] = 0;
 #pragma unroll 8
-  for (int y = y0; y < y1; ++y) {
+  for (int yl = y0; yl < y1; ++yl) {
+    const int y = REV ? Hp - 1 - yl : yl;  // REV: suffix sums, rows bottom-up
     const int x = u + SKEW * y;
     T v = 0;
     if (x >= 0 && x < Wp) v = S[(long long)y * pitch + x];
@@ -155,7 +157,8 @@ k_vscan_agg(const T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, 
 
 template <typename T, int NF>
 __global__ void __launch_bounds__(128)
-k_vscan_carry(const T* __restrict__ agg, T* __restrict__ carry, int nchunks, int Hp, int Nu) {
+k_vscan_carry(const T* __restrict__ agg, T* __restrict__ carry, int nchunks, int Hp, int Nu,
+              int ch) {
   const int ui = blockIdx.x * blockDim.x + threadIdx.x;
   if (ui >= Nu) return;
   T s[NF];
@@ -169,7 +172,7 @@ k_vscan_carry(const T* __restrict__ agg, T* __restrict__ carry, int nchunks, int
       carry[((long long)c * NF + f) * Nu + ui] = s[f];
       a[f] = agg[((long long)c * NF + f) * Nu + ui];
     }
-    const T m = (T)min(kScanChunk, Hp - c * kScanChunk);
+    const T m = (T)min(ch, Hp - c * ch);
     // state after m zero-input steps plus the chunk's own contribution
     T ns[NF];
     ns[0] = s[0] + a[0];
@@ -180,23 +183,25 @@ k_vscan_carry(const T* __restrict__ agg, T* __restrict__ carry, int nchunks, int
   }
 }
 
-template <typename T, int NF, int SKEW>
+template <typename T, int NF, int SKEW, bool REV>
 __global__ void __launch_bounds__(128)
-k_vscan_apply(T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, int Nu,
+k_vscan_apply(T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, int Nu, int ch,
               const T* __restrict__ carry) {
   const int ui = blockIdx.x * blockDim.x + threadIdx.x;
   if (ui >= Nu) return;
   const int u = umin + ui;
   const int c = blockIdx.y;
-  const int y0 = c * kScanChunk, y1 = min(y0 + kScanChunk, Hp);
+  const int y0 = c * ch, y1 = min(y0 + ch, Hp);
   // skip lines that do not cross this chunk
-  const int xa = u + SKEW * y0, xb = u + SKEW * (y1 - 1);
+  const int ya = REV ? Hp - 1 - y0 : y0, yb = REV ? Hp - y1 : y1 - 1;
+  const int xa = u + SKEW * ya, xb = u + SKEW * yb;
   if (max(xa, xb) < 0 || min(xa, xb) >= Wp) return;
   T s[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) s[f] = carry[((long long)c * NF + f) * Nu + ui];
 #pragma unroll 8
-  for (int y = y0; y < y1; ++y) {
+  for (int yl = y0; yl < y1; ++yl) {
+    const int y = REV ? Hp - 1 - yl : yl;
     const int x = u + SKEW * y;
     const bool in = x >= 0 && x < Wp;
     T* p = S + (long long)y * pitch + x;
@@ -209,8 +214,255 @@ k_vscan_apply(T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, int 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Single-pass variant: chained scan with decoupled look-back.
+//
+// A tile is kLbLines consecutive lines x LbRows<T> rows.  Tiles take a ticket
+// from a global counter in launch order and map it chunk-major, so a tile's
+// predecessors (same lines, earlier chunks) always hold smaller tickets and
+// are already running or done: every wait ends.  Each tile loads its values
+// into registers, publishes its zero-carry state (flag 1), walks back over
+// its predecessors -- combining published states until it meets an inclusive
+// one (flag 2) -- publishes its own inclusive state and rescans its registers
+// with the carried-in state.  S is read and written once.
+//
+// Every wait is bounded: after spin_limit polls the tile records
+// BSF_ETIMEOUT, continues with a zero carry and still publishes, so its
+// successors finish too (the result is then wrong and reported, never hung).
+// ---------------------------------------------------------------------------
+constexpr int kLbLines = 128;
+// rows per tile: the default, and a shorter option (more resident tiles)
+template <typename T, bool SHORT> struct LbRows {
+  static constexpr int value = (sizeof(T) == 8 ? 32 : 16) / (SHORT ? 2 : 1);
+};
+
+// state after prefix state P followed by a segment of m rows whose
+// zero-carry state is X:  r_f = sum_{i<=f} C(m-1+i, i) P_{f-i} + X_f
 template <typename T, int NF>
-cudaError_t launch_rows_t(const void* img, int dtype, long long ld, int H, int W, int R,
+__device__ __forceinline__ void lb_combine(const T* P, const T* X, long long m, T* r) {
+  const T tm = (T)m;
+  r[0] = P[0] + X[0];
+  if constexpr (NF >= 2) r[1] = P[1] + tm * P[0] + X[1];
+  if constexpr (NF >= 3) r[2] = P[2] + tm * P[1] + ((tm * (tm + 1)) >> 1) * P[0] + X[2];
+}
+
+__device__ __forceinline__ unsigned lb_load_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <typename T> __device__ __forceinline__ T lb_load_l2(const T* p);
+template <> __device__ __forceinline__ uint64_t lb_load_l2<uint64_t>(const uint64_t* p) {
+  return __ldcg(reinterpret_cast<const unsigned long long*>(p));
+}
+template <> __device__ __forceinline__ u128 lb_load_l2<u128>(const u128* p) {
+  const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2*>(p));
+  return ((u128)v.y << 64) | (u128)v.x;
+}
+
+template <typename T, int NF, int SKEW, bool REV, bool SHORT>
+__global__ void __launch_bounds__(kLbLines)
+k_vscan_lb(T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, int Nu, int NS,
+           T* __restrict__ aggs, T* __restrict__ incls, unsigned* __restrict__ flags,
+           unsigned* __restrict__ ticket, int spin_limit, int test_unpublished, DevStatus* st) {
+  constexpr int CH = LbRows<T, SHORT>::value;
+  __shared__ int s_tile;
+  __shared__ unsigned s_flag;
+  const int t = threadIdx.x;
+  if (t == 0) s_tile = (int)atomicAdd(ticket, 1u);
+  __syncthreads();
+  const int tile = s_tile;
+  const int c = tile / NS, sidx = tile - c * NS;
+  const int ui = sidx * kLbLines + t;
+  const bool line_ok = ui < Nu;
+  const int u = umin + ui;
+  const int y0 = c * CH;
+  const int rows = min(CH, Hp - y0);
+
+  // REV: the running sum goes up the line (suffix sum, the transpose); the
+  // logical row y0 + r is then the physical row Hp - 1 - (y0 + r)
+  T v[CH];
+#pragma unroll
+  for (int r = 0; r < CH; ++r) {
+    const int y = REV ? Hp - 1 - (y0 + r) : y0 + r;
+    const int x = u + SKEW * y;
+    v[r] = 0;
+    if (line_ok && r < rows && x >= 0 && x < Wp) v[r] = S[y * (int)pitch + x];
+  }
+  T a[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) a[f] = 0;
+#pragma unroll
+  for (int r = 0; r < CH; ++r) {
+    a[0] += v[r];
+#pragma unroll
+    for (int f = 1; f < NF; ++f) a[f] += a[f - 1];
+  }
+  // the last chunk may be short; zero rows past it only add the higher folds
+  // of a[] after its end, which no successor reads (it is the last chunk)
+
+  const long long slot = (long long)tile * NF * kLbLines + t;
+  T E[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) E[f] = 0;
+  if (c == 0) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) incls[slot + f * kLbLines] = a[f];
+    __threadfence();  // every writer makes its own state visible before the flag
+    __syncthreads();
+    // failure injection for tests: leave the first chunk's flags unset so its
+    // successors' bounded waits run out
+    if (t == 0 && !test_unpublished) atomicExch(&flags[tile], 2u);
+  } else {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) aggs[slot + f * kLbLines] = a[f];
+    __threadfence();
+    __syncthreads();
+    if (t == 0) atomicExch(&flags[tile], 1u);
+    T X[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) X[f] = 0;
+    long long mx = 0;
+    for (int j = c - 1; j >= 0; --j) {
+      const int pj = j * NS + sidx;
+      if (t == 0) {
+        unsigned fl = 0;
+        for (int spins = 0; spins <= spin_limit; ++spins) {
+          fl = lb_load_acquire(&flags[pj]);
+          if (fl) break;
+          __nanosleep(64);
+        }
+        s_flag = fl;
+      }
+      __syncthreads();
+      const unsigned fl = s_flag;
+      __syncthreads();
+      if (fl == 0) {  // the bounded wait ran out
+        if (t == 0) bsf_set_error(st, BSF_ETIMEOUT);
+        break;
+      }
+      const T* src = (fl == 2 ? incls : aggs) + (long long)pj * NF * kLbLines + t;
+      T P[NF], R2[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) P[f] = lb_load_l2(src + f * kLbLines);
+      lb_combine<T, NF>(P, X, mx, R2);
+      if (fl == 2) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) E[f] = R2[f];
+        break;
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) X[f] = R2[f];
+      mx += CH;
+    }
+    T I[NF];
+    lb_combine<T, NF>(E, a, rows, I);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) incls[slot + f * kLbLines] = I[f];
+    __threadfence();
+    __syncthreads();
+    if (t == 0) atomicExch(&flags[tile], 2u);
+  }
+  // rescan with the carried-in state
+#pragma unroll
+  for (int r = 0; r < CH; ++r) {
+    E[0] += v[r];
+#pragma unroll
+    for (int f = 1; f < NF; ++f) E[f] += E[f - 1];
+    const int y = REV ? Hp - 1 - (y0 + r) : y0 + r;
+    const int x = u + SKEW * y;
+    if (line_ok && r < rows && x >= 0 && x < Wp) S[y * (int)pitch + x] = E[NF - 1];
+  }
+}
+
+template <typename T, int NF, int SKEW, bool REV, bool SHORT>
+cudaError_t launch_lb_t(T* S, long long pitch, int Hp, int Wp, T* aggs, T* incls,
+                        unsigned* sync_words, int spin_limit, int test_unpublished, DevStatus* st,
+                        cudaStream_t s) {
+  constexpr int CH = LbRows<T, SHORT>::value;
+  const int umin = SKEW == 1 ? -(Hp - 1) : 0;
+  const int Nu = SKEW == 0 ? Wp : Wp + Hp - 1;
+  const int NS = (Nu + kLbLines - 1) / kLbLines;
+  const int NC = (Hp + CH - 1) / CH;
+  cudaError_t e = cudaMemsetAsync(sync_words, 0, sizeof(unsigned) * (1 + (size_t)NS * NC), s);
+  if (e != cudaSuccess) return e;
+  k_vscan_lb<T, NF, SKEW, REV, SHORT><<<NS * NC, kLbLines, 0, s>>>(S, pitch, Hp, Wp, umin, Nu, NS, aggs, incls,
+                                                      sync_words + 1, sync_words, spin_limit,
+                                                      test_unpublished, st);
+  return cudaGetLastError();
+}
+
+template <typename T, int NF, bool REV, bool SHORT>
+cudaError_t launch_lb_skew(int skew, T* S, long long pitch, int Hp, int Wp, T* aggs, T* incls,
+                           unsigned* sync_words, int spin_limit, int tu, DevStatus* st,
+                           cudaStream_t s) {
+  switch (skew) {
+    case 0: return launch_lb_t<T, NF, 0, REV, SHORT>(S, pitch, Hp, Wp, aggs, incls, sync_words, spin_limit, tu, st, s);
+    case 1: return launch_lb_t<T, NF, 1, REV, SHORT>(S, pitch, Hp, Wp, aggs, incls, sync_words, spin_limit, tu, st, s);
+    case -1: return launch_lb_t<T, NF, -1, REV, SHORT>(S, pitch, Hp, Wp, aggs, incls, sync_words, spin_limit, tu, st, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// In-place n-fold suffix sums along rows (the transpose of the d1 running
+// sum): one block per row, chunks from the right end; the logical index x'
+// maps to the physical column Wp - 1 - x'.
+// ---------------------------------------------------------------------------
+template <typename T, int NF, int V>
+__global__ void __launch_bounds__(kRowThreads)
+k_suffix_rows(T* __restrict__ S, long long pitch, int Wp) {
+  constexpr int NW = kRowThreads / 32;
+  __shared__ T s_warp[NF][NW];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  T* row = S + (long long)blockIdx.x * pitch;
+  T carry[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) carry[f] = 0;
+  for (int x0 = 0; x0 < Wp; x0 += kRowThreads * V) {
+    T v[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      const int xl = x0 + tid * V + j;
+      v[j] = xl < Wp ? row[Wp - 1 - xl] : (T)0;
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+#pragma unroll
+      for (int j = 1; j < V; ++j) v[j] += v[j - 1];
+      const T tot = v[V - 1];
+      T incl = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const T t = bsf_shfl_up(incl, o);
+        if (lane >= o) incl += t;
+      }
+      if (lane == 31) s_warp[f][wid] = incl;
+      __syncthreads();
+      T wpre = 0, btot = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const T t = s_warp[f][w];
+        if (w < wid) wpre += t;
+        btot += t;
+      }
+      const T add = carry[f] + wpre + (incl - tot);
+#pragma unroll
+      for (int j = 0; j < V; ++j) v[j] += add;
+      carry[f] += btot;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      const int xl = x0 + tid * V + j;
+      if (xl < Wp) row[Wp - 1 - xl] = v[j];
+    }
+  }
+}
+
+template <typename T, int NF>
+cudaError_t launch_rows_t(const void* img, int dtype, long long ld, int H, int W, int R, int row0,
                           int boundary, int q, T* S, long long pitch, int Hp, int Wp,
                           DevStatus* st, cudaStream_t s) {
   constexpr int V = sizeof(T) == 8 ? 4 : 2;
@@ -218,42 +470,43 @@ cudaError_t launch_rows_t(const void* img, int dtype, long long ld, int H, int W
   switch (dtype) {
     case BSF_U8:
       k_scan_rows<T, NF, uint8_t, V><<<Hp, kRowThreads, 0, s>>>(
-          (const uint8_t*)img, ld, H, W, R, boundary, scale, q, S, pitch, Hp, Wp, st);
+          (const uint8_t*)img, ld, H, W, R, row0, boundary, scale, q, S, pitch, Hp, Wp, st);
       break;
     case BSF_F32:
       k_scan_rows<T, NF, float, V><<<Hp, kRowThreads, 0, s>>>(
-          (const float*)img, ld, H, W, R, boundary, scale, q, S, pitch, Hp, Wp, st);
+          (const float*)img, ld, H, W, R, row0, boundary, scale, q, S, pitch, Hp, Wp, st);
       break;
     case BSF_F64:
       k_scan_rows<T, NF, double, V><<<Hp, kRowThreads, 0, s>>>(
-          (const double*)img, ld, H, W, R, boundary, scale, q, S, pitch, Hp, Wp, st);
+          (const double*)img, ld, H, W, R, row0, boundary, scale, q, S, pitch, Hp, Wp, st);
       break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-template <typename T, int NF, int SKEW>
-cudaError_t launch_v_t(T* S, long long pitch, int Hp, int Wp, T* agg, T* carry, cudaStream_t s) {
+template <typename T, int NF, int SKEW, bool REV>
+cudaError_t launch_v_t(T* S, long long pitch, int Hp, int Wp, int ch, T* agg, T* carry,
+                       cudaStream_t s) {
   // u = x - SKEW * y ranges over [umin, umin + Nu)
   const int umin = SKEW == 1 ? -(Hp - 1) : 0;
   const int Nu = SKEW == 0 ? Wp : Wp + Hp - 1;
-  const int nchunks = (Hp + kScanChunk - 1) / kScanChunk;
+  const int nchunks = (Hp + ch - 1) / ch;
   const int threads = 128;
   dim3 grid((Nu + threads - 1) / threads, nchunks);
-  k_vscan_agg<T, NF, SKEW><<<grid, threads, 0, s>>>(S, pitch, Hp, Wp, umin, Nu, agg);
-  k_vscan_carry<T, NF><<<(Nu + threads - 1) / threads, threads, 0, s>>>(agg, carry, nchunks, Hp, Nu);
-  k_vscan_apply<T, NF, SKEW><<<grid, threads, 0, s>>>(S, pitch, Hp, Wp, umin, Nu, carry);
+  k_vscan_agg<T, NF, SKEW, REV><<<grid, threads, 0, s>>>(S, pitch, Hp, Wp, umin, Nu, ch, agg);
+  k_vscan_carry<T, NF><<<(Nu + threads - 1) / threads, threads, 0, s>>>(agg, carry, nchunks, Hp, Nu, ch);
+  k_vscan_apply<T, NF, SKEW, REV><<<grid, threads, 0, s>>>(S, pitch, Hp, Wp, umin, Nu, ch, carry);
   return cudaGetLastError();
 }
 
-template <typename T, int NF>
-cudaError_t launch_v_skew(int skew, T* S, long long pitch, int Hp, int Wp, T* agg, T* carry,
+template <typename T, int NF, bool REV>
+cudaError_t launch_v_skew(int skew, T* S, long long pitch, int Hp, int Wp, int ch, T* agg, T* carry,
                           cudaStream_t s) {
   switch (skew) {
-    case 0: return launch_v_t<T, NF, 0>(S, pitch, Hp, Wp, agg, carry, s);
-    case 1: return launch_v_t<T, NF, 1>(S, pitch, Hp, Wp, agg, carry, s);
-    case -1: return launch_v_t<T, NF, -1>(S, pitch, Hp, Wp, agg, carry, s);
+    case 0: return launch_v_t<T, NF, 0, REV>(S, pitch, Hp, Wp, ch, agg, carry, s);
+    case 1: return launch_v_t<T, NF, 1, REV>(S, pitch, Hp, Wp, ch, agg, carry, s);
+    case -1: return launch_v_t<T, NF, -1, REV>(S, pitch, Hp, Wp, ch, agg, carry, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -261,10 +514,10 @@ cudaError_t launch_v_skew(int skew, T* S, long long pitch, int Hp, int Wp, T* ag
 }  // namespace
 
 cudaError_t bsf_launch_scan_rows(int elem_bytes, int n, const void* img, int dtype, long long ld,
-                                 int H, int W, int R, int boundary, int q, void* S,
+                                 int H, int W, int R, int row0, int boundary, int q, void* S,
                                  long long pitch, int Hp, int Wp, DevStatus* st, cudaStream_t s) {
 #define BSF_ROWS(T, NF) \
-  return launch_rows_t<T, NF>(img, dtype, ld, H, W, R, boundary, q, (T*)S, pitch, Hp, Wp, st, s)
+  return launch_rows_t<T, NF>(img, dtype, ld, H, W, R, row0, boundary, q, (T*)S, pitch, Hp, Wp, st, s)
   if (elem_bytes == 8) {
     if (n == 1) BSF_ROWS(uint64_t, 1);
     if (n == 2) BSF_ROWS(uint64_t, 2);
@@ -278,9 +531,79 @@ cudaError_t bsf_launch_scan_rows(int elem_bytes, int n, const void* img, int dty
   return cudaErrorInvalidValue;
 }
 
-cudaError_t bsf_launch_vscan(int elem_bytes, int n, int skew, void* S, long long pitch,
-                             int Hp, int Wp, void* agg, void* carry, cudaStream_t s) {
-#define BSF_V(T, NF) return launch_v_skew<T, NF>(skew, (T*)S, pitch, Hp, Wp, (T*)agg, (T*)carry, s)
+cudaError_t bsf_launch_suffix_rows(int elem_bytes, int n, void* S, long long pitch, int Hp, int Wp,
+                                   cudaStream_t s) {
+#define BSF_SR(T, NF, V) k_suffix_rows<T, NF, V><<<Hp, kRowThreads, 0, s>>>((T*)S, pitch, Wp); break
+  switch (elem_bytes * 10 + n) {
+    case 81: BSF_SR(uint64_t, 1, 4);
+    case 82: BSF_SR(uint64_t, 2, 4);
+    case 83: BSF_SR(uint64_t, 3, 4);
+    case 161: BSF_SR(u128, 1, 2);
+    case 162: BSF_SR(u128, 2, 2);
+    case 163: BSF_SR(u128, 3, 2);
+    default: return cudaErrorInvalidValue;
+  }
+#undef BSF_SR
+  return cudaGetLastError();
+}
+
+size_t bsf_vscan_lb_bytes(int elem_bytes, int n, int Hp, int Wp, size_t* sync_bytes) {
+  // sized for the short tiles (the larger number of tiles)
+  const int CH = elem_bytes == 8 ? LbRows<uint64_t, true>::value : LbRows<u128, true>::value;
+  const size_t Nu = (size_t)Wp + Hp - 1;
+  const size_t NS = (Nu + kLbLines - 1) / kLbLines;
+  const size_t NC = (size_t)(Hp + CH - 1) / CH;
+  if (sync_bytes) *sync_bytes = sizeof(unsigned) * (1 + NS * NC);
+  return NS * NC * (size_t)n * kLbLines * elem_bytes;  // one of the two state arrays
+}
+
+namespace {
+
+template <typename T, int NF>
+cudaError_t launch_lb_any(int skew, bool reverse, bool short_tiles, void* S, long long pitch,
+                          int Hp, int Wp, void* aggs, void* incls, unsigned* sync_words,
+                          int spin_limit, int test_unpublished, DevStatus* st, cudaStream_t s) {
+  T* S_ = (T*)S;
+  T* a_ = (T*)aggs;
+  T* i_ = (T*)incls;
+  if (reverse) {
+    if (short_tiles)
+      return launch_lb_skew<T, NF, true, true>(skew, S_, pitch, Hp, Wp, a_, i_, sync_words,
+                                               spin_limit, test_unpublished, st, s);
+    return launch_lb_skew<T, NF, true, false>(skew, S_, pitch, Hp, Wp, a_, i_, sync_words,
+                                              spin_limit, test_unpublished, st, s);
+  }
+  if (short_tiles)
+    return launch_lb_skew<T, NF, false, true>(skew, S_, pitch, Hp, Wp, a_, i_, sync_words,
+                                              spin_limit, test_unpublished, st, s);
+  return launch_lb_skew<T, NF, false, false>(skew, S_, pitch, Hp, Wp, a_, i_, sync_words,
+                                             spin_limit, test_unpublished, st, s);
+}
+
+}  // namespace
+
+cudaError_t bsf_launch_vscan_lb(int elem_bytes, int n, int skew, bool reverse, bool short_tiles,
+                                void* S, long long pitch, int Hp, int Wp, void* aggs, void* incls,
+                                unsigned* sync_words, int spin_limit, int test_unpublished,
+                                DevStatus* st, cudaStream_t s) {
+  switch (elem_bytes * 10 + n) {
+    case 81: return launch_lb_any<uint64_t, 1>(skew, reverse, short_tiles, S, pitch, Hp, Wp, aggs, incls, sync_words, spin_limit, test_unpublished, st, s);
+    case 82: return launch_lb_any<uint64_t, 2>(skew, reverse, short_tiles, S, pitch, Hp, Wp, aggs, incls, sync_words, spin_limit, test_unpublished, st, s);
+    case 83: return launch_lb_any<uint64_t, 3>(skew, reverse, short_tiles, S, pitch, Hp, Wp, aggs, incls, sync_words, spin_limit, test_unpublished, st, s);
+    case 161: return launch_lb_any<u128, 1>(skew, reverse, short_tiles, S, pitch, Hp, Wp, aggs, incls, sync_words, spin_limit, test_unpublished, st, s);
+    case 162: return launch_lb_any<u128, 2>(skew, reverse, short_tiles, S, pitch, Hp, Wp, aggs, incls, sync_words, spin_limit, test_unpublished, st, s);
+    case 163: return launch_lb_any<u128, 3>(skew, reverse, short_tiles, S, pitch, Hp, Wp, aggs, incls, sync_words, spin_limit, test_unpublished, st, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t bsf_launch_vscan(int elem_bytes, int n, int skew, bool reverse, void* S, long long pitch,
+                             int Hp, int Wp, int chunk, void* agg, void* carry, cudaStream_t s) {
+#define BSF_V(T, NF)                                                                              \
+  return reverse ? launch_v_skew<T, NF, true>(skew, (T*)S, pitch, Hp, Wp, chunk, (T*)agg,        \
+                                              (T*)carry, s)                                      \
+                 : launch_v_skew<T, NF, false>(skew, (T*)S, pitch, Hp, Wp, chunk, (T*)agg,       \
+                                               (T*)carry, s)
   if (elem_bytes == 8) {
     if (n == 1) BSF_V(uint64_t, 1);
     if (n == 2) BSF_V(uint64_t, 2);

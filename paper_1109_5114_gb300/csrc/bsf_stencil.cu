@@ -12,45 +12,30 @@
 // One thread per output pixel; a warp covers 32 consecutive pixels of a row,
 // so each tap is a coalesced row segment of S whenever neighbouring pixels
 // share their steps (the covariance field is smooth).
-#include "bsf_device.cuh"
+#include "bsf_solve.cuh"
 
 namespace {
 
-template <typename T, int NF>
-__device__ __forceinline__ T diff1(const T* p, long long s) {
-  const T v0 = bsf_load(p);
-  const T v1 = bsf_load(p - s);
-  if constexpr (NF == 1) {
-    return v0 - v1;
-  } else if constexpr (NF == 2) {
-    const T v2 = bsf_load(p - 2 * s);
-    return (v0 + v2) - (v1 << 1);
-  } else {
-    const T v2 = bsf_load(p - 2 * s);
-    const T v3 = bsf_load(p - 3 * s);
-    const T a = v1 - v2;
-    return (v0 - v3) - ((a << 1) + a);
-  }
-}
-
-// Nested differences: level LVL applies the order-NF difference along
-// direction LVL-1 to the result of level LVL-1.
+// Nested order-n differences.  Taps are addressed by 32-bit element indices
+// into S (the padded domain holds fewer than 2^31 elements); level LVL applies
+// the difference along direction LVL-1 (stride s[LVL-1] elements) to level
+// LVL-1, and level 0 loads one element.
 template <typename T, int NF, int LVL>
-__device__ __forceinline__ T comb(const T* p, const long long* s) {
-  if constexpr (LVL == 1) {
-    return diff1<T, NF>(p, s[0]);
+__device__ __forceinline__ T comb(const T* __restrict__ S, int idx, const int* s) {
+  if constexpr (LVL == 0) {
+    return bsf_load(S + idx);
   } else {
-    const long long sk = s[LVL - 1];
-    const T v0 = comb<T, NF, LVL - 1>(p, s);
-    const T v1 = comb<T, NF, LVL - 1>(p - sk, s);
+    const int sk = s[LVL - 1];
+    const T v0 = comb<T, NF, LVL - 1>(S, idx, s);
+    const T v1 = comb<T, NF, LVL - 1>(S, idx - sk, s);
     if constexpr (NF == 1) {
       return v0 - v1;
     } else if constexpr (NF == 2) {
-      const T v2 = comb<T, NF, LVL - 1>(p - 2 * sk, s);
+      const T v2 = comb<T, NF, LVL - 1>(S, idx - 2 * sk, s);
       return (v0 + v2) - (v1 << 1);
     } else {
-      const T v2 = comb<T, NF, LVL - 1>(p - 2 * sk, s);
-      const T v3 = comb<T, NF, LVL - 1>(p - 3 * sk, s);
+      const T v2 = comb<T, NF, LVL - 1>(S, idx - 2 * sk, s);
+      const T v3 = comb<T, NF, LVL - 1>(S, idx - 3 * sk, s);
       const T a = v1 - v2;
       return (v0 - v3) - ((a << 1) + a);
     }
@@ -85,29 +70,47 @@ template <typename T, int NF> struct StencilOcc {
   static constexpr int value = sizeof(T) == 8 ? (NF == 1 ? 6 : NF == 2 ? 4 : 1) : (NF == 1 ? 4 : NF == 2 ? 2 : 1);
 };
 
+// The step solve of bsf_solve.cuh runs here, per pixel, so its arithmetic
+// overlaps the gathers of other warps and no step field goes through HBM.
 template <typename T, int NF, typename Out>
 __global__ void __launch_bounds__(256, (StencilOcc<T, NF>::value))
-k_stencil_d1(const T* __restrict__ S, long long pitch, int R, const ushort4* __restrict__ Lf,
-             int H, int W, float scale_f, double scale_d, Out* __restrict__ out, long long ldo,
-             DevStatus* st) {
+k_stencil_d1(const T* __restrict__ S, long long pitch, int R, const float* __restrict__ cov,
+             int rule, int H, int W, int row0, int rows, float scale_f, double scale_d,
+             Out* __restrict__ out, long long ldo, DevStatus* st) {
+  // pixel (x, row0 + y) of an H x W image; rows [row0, row0 + rows) are
+  // filtered from running sums whose padded row 0 is image row row0 - R
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= W || y >= H) return;
-  const ushort4 L4 = Lf[(long long)y * W + x];
-  const long long L1 = L4.x, L2 = L4.y, L3 = L4.z, L4w = L4.w;
+  if (x >= W || y >= rows) return;
+  const long long HW = (long long)H * W, i = (long long)(row0 + y) * W + x;
+  int L[4], flags, reach;
+  const bool in_reach = bsf_solve::pixel_steps(cov[i], cov[HW + i], cov[2 * HW + i], NF, rule, R,
+                                               L, flags, reach);
+  {  // rare-event counters, aggregated per warp
+    const unsigned act = __activemask();
+    const unsigned mc = __ballot_sync(act, flags & 1), mb = __ballot_sync(act, flags & 2),
+                   mr = __ballot_sync(act, !in_reach);
+    if ((mc | mb | mr) && (threadIdx.x & 31) == __ffs(act) - 1) {
+      if (mc) atomicAdd(&st->clamp_count, (unsigned)__popc(mc));
+      if (mb) { atomicAdd(&st->bad_count, (unsigned)__popc(mb)); bsf_set_error(st, BSF_ECOV); }
+      if (mr) { atomicAdd(&st->range_count, (unsigned)__popc(mr)); bsf_set_error(st, BSF_ERANGE); }
+    }
+  }
+  const int L1 = L[0], L2 = L[1], L3 = L[2], L4w = L[3];
   // element strides of d1 = (1,0), d2 = (1,1), d3 = (0,1), d4 = (-1,1)
-  const long long e1 = 1, e2 = pitch + 1, e3 = pitch, e4 = pitch - 1;
-  const long long c1 = NF * (L1 - 1) / 2, c2 = NF * (L2 - 1) / 2, c3 = NF * (L3 - 1) / 2,
-                  c4 = NF * (L4w - 1) / 2;
-  const T* base = S + (long long)(y + R) * pitch + (x + R) + c1 * e1 + c2 * e2 + c3 * e3 + c4 * e4;
-  const long long s[4] = {L1 * e1, L2 * e2, L3 * e3, L4w * e4};
-  const T acc = comb<T, NF, 4>(base, s);
+  const int p32 = (int)pitch;
+  const int e1 = 1, e2 = p32 + 1, e3 = p32, e4 = p32 - 1;
+  const int c1 = NF * (L1 - 1) / 2, c2 = NF * (L2 - 1) / 2, c3 = NF * (L3 - 1) / 2,
+            c4 = NF * (L4w - 1) / 2;
+  const int base = (y + R) * p32 + (x + R) + c1 * e1 + c2 * e2 + c3 * e3 + c4 * e4;
+  const int s[4] = {L1 * e1, L2 * e2, L3 * e3, L4w * e4};
+  const T acc = comb<T, NF, 4>(S, base, s);
 
   // D = prod_k L_k^n (exact) and the bound max|Q| * D < 2^(b-1) that makes
   // the modular accumulator equal the true one (checked in float32 with a
   // margin far above its rounding: |acc| <= D max|Q| and max|Q| <= bound + 1/2)
   T D = 1;
-  const T D1 = (T)(L1 * L2) * (T)(L3 * L4w);
+  const T D1 = (T)(unsigned)(L1 * L2) * (T)(unsigned)(L3 * L4w);
   const float Df1 = (float)(L1 * L2) * (float)(L3 * L4w);
   float Df = Df1;
 #pragma unroll
@@ -130,16 +133,19 @@ k_stencil_d1(const T* __restrict__ S, long long pitch, int R, const ushort4* __r
 }
 
 template <typename T, int NF>
-cudaError_t launch_t(const T* S, long long pitch, int R, const ushort4* Lf, int H, int W, int q,
-                     void* out, int out_dtype, long long ldo, DevStatus* st, cudaStream_t s) {
+cudaError_t launch_t(const T* S, long long pitch, int R, const float* cov, int rule, int H, int W,
+                     int row0, int rows, int q, void* out, int out_dtype, long long ldo,
+                     DevStatus* st, cudaStream_t s) {
   dim3 block(32, 8);
-  dim3 grid((W + 31) / 32, (H + 7) / 8);
+  dim3 grid((W + 31) / 32, (rows + 7) / 8);
   const float sf = ldexpf(1.f, -q);
   const double sd = ldexp(1.0, -q);
   if (out_dtype == BSF_F32)
-    k_stencil_d1<T, NF, float><<<grid, block, 0, s>>>(S, pitch, R, Lf, H, W, sf, sd, (float*)out, ldo, st);
+    k_stencil_d1<T, NF, float><<<grid, block, 0, s>>>(S, pitch, R, cov, rule, H, W, row0, rows,
+                                                      sf, sd, (float*)out, ldo, st);
   else if (out_dtype == BSF_F64)
-    k_stencil_d1<T, NF, double><<<grid, block, 0, s>>>(S, pitch, R, Lf, H, W, sf, sd, (double*)out, ldo, st);
+    k_stencil_d1<T, NF, double><<<grid, block, 0, s>>>(S, pitch, R, cov, rule, H, W, row0, rows,
+                                                       sf, sd, (double*)out, ldo, st);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
@@ -148,9 +154,12 @@ cudaError_t launch_t(const T* S, long long pitch, int R, const ushort4* Lf, int 
 }  // namespace
 
 cudaError_t bsf_launch_stencil_d1(int elem_bytes, int n, const void* S, long long pitch, int R,
-                                  const ushort4* Lf, int H, int W, int q, void* out,
-                                  int out_dtype, long long ldo, DevStatus* st, cudaStream_t s) {
-#define BSF_ST(T, NF) return launch_t<T, NF>((const T*)S, pitch, R, Lf, H, W, q, out, out_dtype, ldo, st, s)
+                                  const float* cov, int rule, int H, int W, int row0, int rows,
+                                  int q, void* out, int out_dtype, long long ldo, DevStatus* st,
+                                  cudaStream_t s) {
+#define BSF_ST(T, NF)                                                                          \
+  return launch_t<T, NF>((const T*)S, pitch, R, cov, rule, H, W, row0, rows, q, out, out_dtype, \
+                         ldo, st, s)
   if (elem_bytes == 8) {
     if (n == 1) BSF_ST(uint64_t, 1);
     if (n == 2) BSF_ST(uint64_t, 2);

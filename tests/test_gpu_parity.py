@@ -184,3 +184,74 @@ def test_auto_q_on_large_kernels_does_not_overflow():
     assert g["info"].max_mass > 2.0 ** 30
     o = run_oracle(img, cov, n, 2, g["q"], g["R"])
     np.testing.assert_array_equal(g["out"], o["out"])
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_scan_modes_agree_bit_exact(prec):
+    # single-pass look-back and three-phase scans give the same running sums
+    torch = pytest.importorskip("torch")
+    from paper_1109_5114_gb300 import bsf
+    H, W, n = 157, 203, 3
+    img = wl.random_integer_image(H, W, seed=12, lo=-999, hi=999).astype(np.float32)
+    cov = _cov(H, W, seed=13, smax=8.0)
+    outs = []
+    for mode in (bsf.BSF_SCAN_LOOKBACK, bsf.BSF_SCAN_THREE_PHASE):
+        f = bsf.BoxSplineFilter(H, W, n, "symmetric", precision=prec, frac_bits=4)
+        f.set_option(bsf.BSF_OPT_SCAN_MODE, mode)
+        out = f.filter(torch.from_numpy(img).cuda(), torch.from_numpy(cov).cuda())
+        raw, _ = f.preintegrated()
+        torch.cuda.synchronize()
+        assert f.status() == 0
+        outs.append((out.cpu().numpy(), raw.cpu().numpy()))
+        f.close()
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+
+
+def test_bounded_wait_times_out_and_context_stays_usable():
+    # failure injection: the first chunk of every look-back scan never marks
+    # its state ready, so every wait on it runs out after the wait limit; the
+    # kernel must report BSF_ETIMEOUT and return (no hang, no fault), and the
+    # same context must work normally afterwards
+    torch = pytest.importorskip("torch")
+    from paper_1109_5114_gb300 import bsf
+    H, W, n = 120, 90, 2
+    img = wl.blob_image(H, W, seed=2, n_blobs=5).astype(np.float32)
+    cov = _cov(H, W, seed=3)
+    f = bsf.BoxSplineFilter(H, W, n, "symmetric", frac_bits=20)
+    ti, tc = torch.from_numpy(img).cuda(), torch.from_numpy(cov).cuda()
+    f.set_option(bsf.BSF_OPT_SCAN_MODE, bsf.BSF_SCAN_LOOKBACK)
+    f.set_option(bsf.BSF_OPT_WAIT_LIMIT, 2000)
+    f.set_option(bsf.BSF_OPT_TEST_UNPUBLISHED, 1)
+    f.filter(ti, tc)
+    torch.cuda.synchronize()
+    assert f.status() == bsf.BSF_ETIMEOUT
+    f.set_option(bsf.BSF_OPT_TEST_UNPUBLISHED, 0)
+    f.set_option(bsf.BSF_OPT_WAIT_LIMIT, 1 << 20)
+    out = f.filter(ti, tc)
+    torch.cuda.synchronize()
+    assert f.status() == 0
+    R = f.info().R
+    f.close()
+    o = run_oracle(img, cov, n, 2, 20, R)
+    np.testing.assert_array_equal(out.cpu().numpy(), o["out"])
+
+
+@pytest.mark.parametrize("n,boundary", [(1, 2), (2, 0), (2, 2), (3, 1)])
+def test_row_bands_equal_whole_image_bit_exact(n, boundary):
+    # row-band decomposition (one image over several devices, tested here as
+    # bands on one device): each band's running sums restart R rows above it
+    torch = pytest.importorskip("torch")
+    from paper_1109_5114_gb300 import bsf
+    H, W = 150, 97
+    img = torch.from_numpy(wl.blob_image(H, W, seed=n, n_blobs=8)).cuda()
+    cov = torch.from_numpy(_cov(H, W, seed=30 + n, smax=5.0)).cuda()
+    f = bsf.BoxSplineFilter(H, W, n, boundary, frac_bits=24)
+    f.plan(cov)
+    whole = f.filter(img, cov).clone()
+    bands = [(0, 37), (37, 38), (38, 101), (101, 150)]
+    parts = [f.filter_rows(img, cov, a, b).clone() for a, b in bands]
+    torch.cuda.synchronize()
+    assert f.status() == 0
+    f.close()
+    torch.testing.assert_close(torch.cat(parts, 0), whole, rtol=0, atol=0)
