@@ -9,12 +9,13 @@
 //       step and 0, +1 or -1 column across.  In skewed coordinates
 //       u = x - skew * y every line is a column, so one thread owns one line
 //       and a warp reads 32 consecutive x of a row (coalesced).  Rows are cut
-//       into chunks of kScanChunk rows, scanned in three phases:
+//       into chunks of kScanChunk rows, scanned in phases:
 //         agg   -- per (line, chunk): the n-fold state at the chunk's end
 //                  with zero carry-in;
-//         carry -- per line: combine the chunk states in order; the state
+//         carry -- combine the earlier chunks' states in order; the state
 //                  after a chunk of m rows is
-//                  s'_f = sum_{j<=f} C(m-1+j, j) s_{f-j} + agg_f;
+//                  s'_f = sum_{j<=f} C(m-1+j, j) s_{f-j} + agg_f
+//                  (folded at the start of the apply kernel);
 //         apply -- per (line, chunk): rescan with the carried-in state and
 //                  write the result in place.
 //       No block waits on another block.  (The single-pass look-back variant
@@ -155,38 +156,29 @@ k_vscan_agg(const T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, 
   for (int f = 0; f < NF; ++f) agg[((long long)c * NF + f) * Nu + ui] = s[f];
 }
 
+// zero-carry combine of the three-phase scan: state after prefix state s
+// followed by m rows whose zero-carry state is a
 template <typename T, int NF>
-__global__ void __launch_bounds__(128)
-k_vscan_carry(const T* __restrict__ agg, T* __restrict__ carry, int nchunks, int Hp, int Nu,
-              int ch) {
-  const int ui = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ui >= Nu) return;
-  T s[NF];
+__device__ __forceinline__ void tp_combine(T* s, const T* a, T m) {
+  T ns[NF];
+  ns[0] = s[0] + a[0];
+  if constexpr (NF >= 2) ns[1] = s[1] + m * s[0] + a[1];
+  if constexpr (NF >= 3) ns[2] = s[2] + m * s[1] + ((m * (m + 1)) >> 1) * s[0] + a[2];
 #pragma unroll
-  for (int f = 0; f < NF; ++f) s[f] = 0;
-#pragma unroll 8
-  for (int c = 0; c < nchunks; ++c) {
-    T a[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      carry[((long long)c * NF + f) * Nu + ui] = s[f];
-      a[f] = agg[((long long)c * NF + f) * Nu + ui];
-    }
-    const T m = (T)min(ch, Hp - c * ch);
-    // state after m zero-input steps plus the chunk's own contribution
-    T ns[NF];
-    ns[0] = s[0] + a[0];
-    if constexpr (NF >= 2) ns[1] = s[1] + m * s[0] + a[1];
-    if constexpr (NF >= 3) ns[2] = s[2] + m * s[1] + ((m * (m + 1)) >> 1) * s[0] + a[2];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) s[f] = ns[f];
-  }
+  for (int f = 0; f < NF; ++f) s[f] = ns[f];
 }
+
+// Rescan of one (line, chunk): the carried-in state is folded here from the
+// zero-carry states of the earlier chunks of the same line (independent loads
+// from L2, so no separate carry pass and no serial chain between launches),
+// then the chunk is rescanned in batches of kApplyBatch rows whose loads are
+// all issued before any store.
+constexpr int kApplyBatch = 16;
 
 template <typename T, int NF, int SKEW, bool REV>
 __global__ void __launch_bounds__(128)
 k_vscan_apply(T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, int Nu, int ch,
-              const T* __restrict__ carry) {
+              const T* __restrict__ agg) {
   const int ui = blockIdx.x * blockDim.x + threadIdx.x;
   if (ui >= Nu) return;
   const int u = umin + ui;
@@ -198,19 +190,34 @@ k_vscan_apply(T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, int 
   if (max(xa, xb) < 0 || min(xa, xb) >= Wp) return;
   T s[NF];
 #pragma unroll
-  for (int f = 0; f < NF; ++f) s[f] = carry[((long long)c * NF + f) * Nu + ui];
-#pragma unroll 8
-  for (int yl = y0; yl < y1; ++yl) {
-    const int y = REV ? Hp - 1 - yl : yl;
-    const int x = u + SKEW * y;
-    const bool in = x >= 0 && x < Wp;
-    T* p = S + (long long)y * pitch + x;
-    T v = 0;
-    if (in) v = *p;
-    s[0] += v;
+  for (int f = 0; f < NF; ++f) s[f] = 0;
+#pragma unroll 4
+  for (int j = 0; j < c; ++j) {
+    T a[NF];
 #pragma unroll
-    for (int f = 1; f < NF; ++f) s[f] += s[f - 1];
-    if (in) *p = s[NF - 1];
+    for (int f = 0; f < NF; ++f) a[f] = agg[((long long)j * NF + f) * Nu + ui];
+    tp_combine<T, NF>(s, a, (T)ch);  // every earlier chunk is full
+  }
+  const int p32 = (int)pitch;
+  for (int yb0 = y0; yb0 < y1; yb0 += kApplyBatch) {
+    T v[kApplyBatch];
+    int idx[kApplyBatch];
+#pragma unroll
+    for (int r = 0; r < kApplyBatch; ++r) {
+      const int yl = yb0 + r;
+      const int y = REV ? Hp - 1 - yl : yl;
+      const int x = u + SKEW * y;
+      const bool in = yl < y1 && x >= 0 && x < Wp;
+      idx[r] = in ? y * p32 + x : -1;
+      v[r] = in ? S[idx[r]] : (T)0;
+    }
+#pragma unroll
+    for (int r = 0; r < kApplyBatch; ++r) {
+      s[0] += v[r];
+#pragma unroll
+      for (int f = 1; f < NF; ++f) s[f] += s[f - 1];
+      if (idx[r] >= 0) S[idx[r]] = s[NF - 1];
+    }
   }
 }
 
@@ -461,11 +468,10 @@ k_suffix_rows(T* __restrict__ S, long long pitch, int Wp) {
   }
 }
 
-template <typename T, int NF>
-cudaError_t launch_rows_t(const void* img, int dtype, long long ld, int H, int W, int R, int row0,
+template <typename T, int NF, int V>
+cudaError_t launch_rows_v(const void* img, int dtype, long long ld, int H, int W, int R, int row0,
                           int boundary, int q, T* S, long long pitch, int Hp, int Wp,
                           DevStatus* st, cudaStream_t s) {
-  constexpr int V = sizeof(T) == 8 ? 4 : 2;
   const float scale = ldexpf(1.f, q);  // q <= 100: a normal float32
   switch (dtype) {
     case BSF_U8:
@@ -485,6 +491,16 @@ cudaError_t launch_rows_t(const void* img, int dtype, long long ld, int H, int W
   return cudaGetLastError();
 }
 
+// V consecutive elements per thread (measured: longer per-thread runs lengthen
+// the serial dependence of the local scans more than they save in barriers)
+template <typename T, int NF>
+cudaError_t launch_rows_t(const void* img, int dtype, long long ld, int H, int W, int R, int row0,
+                          int boundary, int q, T* S, long long pitch, int Hp, int Wp,
+                          DevStatus* st, cudaStream_t s) {
+  constexpr int V0 = sizeof(T) == 8 ? 4 : 2;
+  return launch_rows_v<T, NF, V0>(img, dtype, ld, H, W, R, row0, boundary, q, S, pitch, Hp, Wp, st, s);
+}
+
 template <typename T, int NF, int SKEW, bool REV>
 cudaError_t launch_v_t(T* S, long long pitch, int Hp, int Wp, int ch, T* agg, T* carry,
                        cudaStream_t s) {
@@ -494,9 +510,9 @@ cudaError_t launch_v_t(T* S, long long pitch, int Hp, int Wp, int ch, T* agg, T*
   const int nchunks = (Hp + ch - 1) / ch;
   const int threads = 128;
   dim3 grid((Nu + threads - 1) / threads, nchunks);
+  (void)carry;
   k_vscan_agg<T, NF, SKEW, REV><<<grid, threads, 0, s>>>(S, pitch, Hp, Wp, umin, Nu, ch, agg);
-  k_vscan_carry<T, NF><<<(Nu + threads - 1) / threads, threads, 0, s>>>(agg, carry, nchunks, Hp, Nu, ch);
-  k_vscan_apply<T, NF, SKEW, REV><<<grid, threads, 0, s>>>(S, pitch, Hp, Wp, umin, Nu, ch, carry);
+  k_vscan_apply<T, NF, SKEW, REV><<<grid, threads, 0, s>>>(S, pitch, Hp, Wp, umin, Nu, ch, agg);
   return cudaGetLastError();
 }
 
