@@ -76,6 +76,10 @@ extern "C" {
 /* precision of the running sums */
 #define BSF_FIX64   1       /* uint64 modular fixed point (8 B per element) */
 #define BSF_FIX128  2       /* uint128 modular fixed point (16 B per element) */
+#define BSF_F64ACC  3       /* precision study: float64 running sums (8 B) */
+#define BSF_F32KAHAN 4      /* precision study: compensated float32 running sums, each
+                               element an unevaluated sum hi + lo of two float32 added
+                               with error-free transformations (8 B) */
 
 /* covariance field encodings */
 #define BSF_COV_C   0       /* (C11, C12, C22) in px^2 */
@@ -148,8 +152,11 @@ void bsf_destroy(bsf_t h);
 /* Issue all later work on this cudaStream_t (NULL = the legacy default stream). */
 int bsf_set_stream(bsf_t h, void* stream);
 
-/* Choose the running-sum modulus and the number q of fractional bits of the
- * fixed-point input.  frac_bits in [0, 62] (BSF_FIX64) or [0, 100] (BSF_FIX128)
+/* Choose the arithmetic of the running sums and the number q of fractional
+ * bits of the fixed-point input.  BSF_F64ACC / BSF_F32KAHAN keep the image
+ * values as they are (q is ignored) and are not exact: the n-fold sums grow
+ * like prod_k (extent^n / n!) and their rounding is not cancelled by the
+ * differences (forward only).  frac_bits in [0, 62] (BSF_FIX64) or [0, 100] (BSF_FIX128)
  * fixes q; -1 chooses the largest q (at most b - 28) with
  * (max|f| 2^q) * max prod L^n < 2^(b-2), from the value bound (see
  * bsf_set_value_bound; uint8 images use 255; float images without a declared

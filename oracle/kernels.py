@@ -140,9 +140,10 @@ def correlate_exact(fq: np.ndarray, Lfield: np.ndarray, n: int, boundary: int,
 def correlate_f64(f: np.ndarray, Lfield: np.ndarray, n: int, boundary: int, pixels=None):
     """Float64 direct filter out(p) = sum_j K_p(j) f~(p+j) / mass, no quantisation.
 
-    Uses math.fsum per pixel (correctly rounded sum of exactly-rounded
-    products, the products being exact for the integer weights that fit in
-    53 bits).  Returns a float64 array, or a dict when ``pixels`` is given.
+    Each product K(j) f(p+j) is rounded once to float64 and the products are
+    summed with math.fsum (correctly rounded), so the result is within a few
+    units in the last place of the exact value.  Returns a float64 array, or
+    a dict when ``pixels`` is given.
     """
     import math
     H, W = f.shape
@@ -160,4 +161,50 @@ def correlate_f64(f: np.ndarray, Lfield: np.ndarray, n: int, boundary: int, pixe
         terms = (Kf * patch)[mask & (K != 0)]
         val = math.fsum(terms.tolist()) / float(kernel_mass(Lt, n))
         out[(y, x)] = val
+    return out
+
+
+def kernel_d1_int64(L: tuple, n: int):
+    """kernel_d1 built with int64 arithmetic (scipy.signal.convolve2d of the
+    four line kernels); exact while the mass prod L^n stays below 2^62.
+    Returns (K, ox, oy) like kernel_d1.  Pinned by tests against kernel_d1."""
+    from scipy.signal import convolve2d
+    if kernel_mass(L, n) >= (1 << 62):
+        raise OverflowError("kernel mass too large for int64")
+    K = np.ones((1, 1), dtype=np.int64)
+    for k, (dx, dy) in enumerate(DIRS):
+        h = np.array(box_power_1d(int(L[k]), n), dtype=np.int64)
+        m = len(h)
+        if (dx, dy) == (1, 0):
+            line = h.reshape(1, m)
+        elif (dx, dy) == (0, 1):
+            line = h.reshape(m, 1)
+        elif (dx, dy) == (1, 1):
+            line = np.diag(h)
+        else:  # (-1, 1): x decreases as y increases
+            line = np.fliplr(np.diag(h))
+        K = convolve2d(K, line)
+    oy, ox = (K.shape[0] - 1) // 2, (K.shape[1] - 1) // 2
+    return K, ox, oy
+
+
+def correlate_exact_sampled(fq: np.ndarray, Lfield: np.ndarray, n: int, boundary: int, pixels):
+    """Exact accumulators at sampled pixels for small-valued integer images
+    (|fq| < 2^24), with int64 kernels split into 31-bit limbs so every dot
+    product is exact in int64.  Returns {(y, x): Python int}."""
+    H, W = fq.shape
+    f64 = fq.astype(np.int64)
+    cache = {}
+    out = {}
+    for (y, x) in pixels:
+        Lt = tuple(int(Lfield[k, y, x]) for k in range(4))
+        if Lt not in cache:
+            K, ox, oy = kernel_d1_int64(Lt, n)
+            cache[Lt] = (K >> 31, K & ((1 << 31) - 1), ox, oy)
+        Khi, Klo, ox, oy = cache[Lt]
+        kh, kw = Khi.shape
+        yi, yv = extend_index(np.arange(y - oy, y - oy + kh), H, boundary)
+        xi, xv = extend_index(np.arange(x - ox, x - ox + kw), W, boundary)
+        patch = np.where(np.outer(yv, xv), f64[np.ix_(yi, xi)], 0)
+        out[(y, x)] = (int((Khi * patch).sum()) << 31) + int((Klo * patch).sum())
     return out

@@ -87,6 +87,7 @@ int cuda_fail(bsf_t h, cudaError_t e, const char* where) {
   } while (0)
 
 size_t elem_bytes_of(int precision) { return precision == BSF_FIX128 ? 16 : 8; }
+bool is_fixed(int precision) { return precision == BSF_FIX64 || precision == BSF_FIX128; }
 
 void free_workspace(bsf_t h) {
   if (h->S) cudaFree(h->S);
@@ -225,6 +226,10 @@ int run_steps(bsf_t h, const float* cov, int cov_kind, bool sync_plan) {
 // Choose q for this pre-integration.
 int resolve_q(bsf_t h, const void* img, int dtype, long long ld) {
   const int b = h->precision == BSF_FIX128 ? 128 : 64;
+  if (!is_fixed(h->precision)) {  // floating-point sums hold the values themselves
+    h->q = 0;
+    return BSF_OK;
+  }
   if (h->frac_req >= 0) {
     h->q = h->frac_req;
     return BSF_OK;
@@ -272,8 +277,8 @@ int preintegrate_impl(bsf_t h, const void* img, int dtype, long long ld, int row
   cudaError_t e;
   {
     PhaseTimer t(h, BSF_PHASE_ROWS);
-    e = bsf_launch_scan_rows(h->elem, h->n, img, dtype, ld, h->H, h->W, h->R, row0, h->boundary,
-                             h->q, h->S, h->pitch, Hb, h->Wp, h->st, h->stream);
+    e = bsf_launch_scan_rows(h->precision, h->n, img, dtype, ld, h->H, h->W, h->R, row0,
+                             h->boundary, h->q, h->S, h->pitch, Hb, h->Wp, h->st, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "row scan");
   // d3, d2, d4
@@ -281,12 +286,12 @@ int preintegrate_impl(bsf_t h, const void* img, int dtype, long long ld, int row
   const int phases[3] = {BSF_PHASE_D3, BSF_PHASE_D2, BSF_PHASE_D4};
   for (int i = 0; i < 3; ++i) {
     PhaseTimer t(h, phases[i]);
-    if (h->scan_mode == BSF_SCAN_LOOKBACK)
-      e = bsf_launch_vscan_lb(h->elem, h->n, skews[i], false, h->short_tiles != 0, h->S, h->pitch,
+    if (h->scan_mode == BSF_SCAN_LOOKBACK && is_fixed(h->precision))
+      e = bsf_launch_vscan_lb(h->precision, h->n, skews[i], false, h->short_tiles != 0, h->S, h->pitch,
                               Hb, h->Wp, h->agg, h->carry, h->sync_words, h->wait_limit,
                               h->test_unpublished, h->st, h->stream);
     else
-      e = bsf_launch_vscan(h->elem, h->n, skews[i], false, h->S, h->pitch, Hb, h->Wp,
+      e = bsf_launch_vscan(h->precision, h->n, skews[i], false, h->S, h->pitch, Hb, h->Wp,
                            h->scan_chunk, h->agg, h->carry, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "vertical scan");
   }
@@ -353,7 +358,8 @@ int bsf_set_stream(bsf_t h, void* stream) {
 
 int bsf_set_precision(bsf_t h, int mode, int frac_bits) {
   if (!h) return BSF_EINVAL;
-  if (mode != BSF_FIX64 && mode != BSF_FIX128) return fail(h, BSF_EINVAL, "bad precision mode %d", mode);
+  if (mode != BSF_FIX64 && mode != BSF_FIX128 && mode != BSF_F64ACC && mode != BSF_F32KAHAN)
+    return fail(h, BSF_EINVAL, "bad precision mode %d", mode);
   const int qmax = mode == BSF_FIX64 ? 62 : 100;
   if (frac_bits < -1 || frac_bits > qmax)
     return fail(h, BSF_EINVAL, "frac_bits %d outside [-1, %d]", frac_bits, qmax);
@@ -441,8 +447,8 @@ static int filter_impl(bsf_t h, const void* img, int dtype, long long ld, const 
   cudaError_t e;
   {
     PhaseTimer t(h, BSF_PHASE_STENCIL);
-    e = bsf_launch_stencil_d1(h->elem, h->n, h->S, h->pitch, h->R, cov, h->step_rule, h->H, h->W,
-                              row0, rows, h->S_q, out, out_dtype, ldo, h->st, h->stream);
+    e = bsf_launch_stencil_d1(h->precision, h->n, h->S, h->pitch, h->R, cov, h->step_rule, h->H,
+                              h->W, row0, rows, h->S_q, out, out_dtype, ldo, h->st, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "stencil");
   if (h->last_cov != cov) h->steps_current = false;
@@ -502,11 +508,11 @@ int bsf_filter_backward(bsf_t h, const float* gout, long long ldg, const float* 
     const int skews[3] = {-1, 1, 0};  // transposes in reverse order: d4, d2, d3
     for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
       if (h->scan_mode == BSF_SCAN_LOOKBACK)
-        e = bsf_launch_vscan_lb(8, h->n, skews[i], true, h->short_tiles != 0, h->G, h->pitch,
+        e = bsf_launch_vscan_lb(BSF_FIX64, h->n, skews[i], true, h->short_tiles != 0, h->G, h->pitch,
                                 h->Hp, h->Wp, h->agg, h->carry, h->sync_words, h->wait_limit, 0,
                                 h->st, h->stream);
       else
-        e = bsf_launch_vscan(8, h->n, skews[i], true, h->G, h->pitch, h->Hp, h->Wp, h->scan_chunk,
+        e = bsf_launch_vscan(BSF_FIX64, h->n, skews[i], true, h->G, h->pitch, h->Hp, h->Wp, h->scan_chunk,
                              h->agg, h->carry, h->stream);
     }
     if (e == cudaSuccess) e = bsf_launch_suffix_rows(8, h->n, h->G, h->pitch, h->Hp, h->Wp, h->stream);

@@ -39,13 +39,61 @@ __device__ __forceinline__ int bsf_map_index(int i, int N, int boundary, bool& v
 }
 
 // ----------------------------------------------------------------------------
-// Element traits of the running sums
+// Element types of the running sums.  The fixed-point types wrap modulo 2^b;
+// the floating-point precision variants are float64 and a double-float
+// (an unevaluated sum hi + lo of two float32, added with error-free
+// transformations: the compensated float32 running sums).
 // ----------------------------------------------------------------------------
+struct f32x2 {
+  float hi, lo;
+  __host__ __device__ f32x2() : hi(0.f), lo(0.f) {}
+  __host__ __device__ f32x2(int v) : hi((float)v), lo(0.f) {}
+  __host__ __device__ f32x2(float h, float l) : hi(h), lo(l) {}
+};
+
+// Knuth's TwoSum (s + e == a + b exactly) and the renormalisation of a
+// double-float, both written out with IEEE round-to-nearest float32 steps.
+__device__ __forceinline__ f32x2 ddf_renorm(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return f32x2(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ f32x2 ddf_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return f32x2(s, e);
+}
+__device__ __forceinline__ f32x2 operator+(f32x2 a, f32x2 b) {
+  const f32x2 t = ddf_two_sum(a.hi, b.hi);
+  return ddf_renorm(t.hi, __fadd_rn(t.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ f32x2 operator-(f32x2 a) { return f32x2(-a.hi, -a.lo); }
+__device__ __forceinline__ f32x2 operator-(f32x2 a, f32x2 b) { return a + (-b); }
+__device__ __forceinline__ f32x2& operator+=(f32x2& a, f32x2 b) { a = a + b; return a; }
+
 template <typename T> struct ElemBits;
 template <> struct ElemBits<uint64_t> { static constexpr int value = 64; };
 template <> struct ElemBits<u128> { static constexpr int value = 128; };
 
+template <typename T> struct IsFixed { static constexpr bool value = false; };
+template <> struct IsFixed<uint64_t> { static constexpr bool value = true; };
+template <> struct IsFixed<u128> { static constexpr bool value = true; };
+
+// v * m for a small non-negative integer m
+template <typename T> __device__ __forceinline__ T bsf_mul_int(T v, long long m) { return v * (T)m; }
+template <> __device__ __forceinline__ f32x2 bsf_mul_int<f32x2>(f32x2 v, long long m) {
+  const float mf = (float)m;  // exact: m < 2^24
+  const float p = __fmul_rn(v.hi, mf);
+  const float e = __fmaf_rn(v.hi, mf, -p);  // exact error of the product
+  return ddf_renorm(p, __fadd_rn(e, __fmul_rn(v.lo, mf)));
+}
+
 template <typename T> __device__ __forceinline__ T bsf_load(const T* p);
+template <> __device__ __forceinline__ double bsf_load<double>(const double* p) { return __ldg(p); }
+template <> __device__ __forceinline__ f32x2 bsf_load<f32x2>(const f32x2* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return f32x2(v.x, v.y);
+}
 template <> __device__ __forceinline__ uint64_t bsf_load<uint64_t>(const uint64_t* p) {
   return __ldg(reinterpret_cast<const unsigned long long*>(p));
 }
@@ -55,6 +103,12 @@ template <> __device__ __forceinline__ u128 bsf_load<u128>(const u128* p) {
 }
 
 template <typename T> __device__ __forceinline__ T bsf_shfl_up(T v, int d);
+template <> __device__ __forceinline__ double bsf_shfl_up<double>(double v, int d) {
+  return __shfl_up_sync(0xffffffffu, v, d);
+}
+template <> __device__ __forceinline__ f32x2 bsf_shfl_up<f32x2>(f32x2 v, int d) {
+  return f32x2(__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d));
+}
 template <> __device__ __forceinline__ uint64_t bsf_shfl_up<uint64_t>(uint64_t v, int d) {
   return __shfl_up_sync(0xffffffffu, (unsigned long long)v, d);
 }
@@ -65,6 +119,12 @@ template <> __device__ __forceinline__ u128 bsf_shfl_up<u128>(u128 v, int d) {
   return ((u128)hi << 64) | (u128)lo;
 }
 template <typename T> __device__ __forceinline__ T bsf_shfl_idx(T v, int src);
+template <> __device__ __forceinline__ double bsf_shfl_idx<double>(double v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+template <> __device__ __forceinline__ f32x2 bsf_shfl_idx<f32x2>(f32x2 v, int src) {
+  return f32x2(__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src));
+}
 template <> __device__ __forceinline__ uint64_t bsf_shfl_idx<uint64_t>(uint64_t v, int src) {
   return __shfl_sync(0xffffffffu, (unsigned long long)v, src);
 }

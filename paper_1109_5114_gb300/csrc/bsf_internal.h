@@ -34,23 +34,25 @@ cudaError_t bsf_launch_steps(const float* cov, int cov_kind, int H, int W, int n
 cudaError_t bsf_launch_absmax(const void* img, int dtype, long long ld, int H, int W,
                               DevStatus* st, cudaStream_t s);
 
+// prec: BSF_FIX64 (uint64), BSF_FIX128 (uint128), BSF_F64ACC (float64) or
+// BSF_F32KAHAN (double-float) element type of the running sums.
 // Row running sums of image rows row0 - R .. row0 - R + Hp - 1 (extended).
-cudaError_t bsf_launch_scan_rows(int elem_bytes, int n, const void* img, int dtype, long long ld,
+cudaError_t bsf_launch_scan_rows(int prec, int n, const void* img, int dtype, long long ld,
                                  int H, int W, int R, int row0, int boundary, int q, void* S,
                                  long long pitch, int Hp, int Wp, DevStatus* st, cudaStream_t s);
 
 // Vertical running sums along d3 (skew 0), d2 (skew +1), d4 (skew -1), in place
 // on S.  agg and carry each hold nchunks * n * Nu elements, Nu = Wp + Hp - 1.
-cudaError_t bsf_launch_vscan(int elem_bytes, int n, int skew, bool reverse, void* S, long long pitch,
+cudaError_t bsf_launch_vscan(int prec, int n, int skew, bool reverse, void* S, long long pitch,
                              int Hp, int Wp, int chunk, void* agg, void* carry, cudaStream_t s);
 
 // Single-pass vertical running sums (decoupled look-back).  aggs and incls
 // each hold bsf_vscan_lb_bytes() bytes; sync_words holds *sync_bytes (zeroed
 // by the launcher).  Waits poll at most spin_limit times.
 size_t bsf_vscan_lb_bytes(int elem_bytes, int n, int Hp, int Wp, size_t* sync_bytes);
-// reverse: suffix sums (the transpose).  test_unpublished != 0 leaves the
-// first chunk's flags unset (failure injection).
-cudaError_t bsf_launch_vscan_lb(int elem_bytes, int n, int skew, bool reverse, bool short_tiles,
+// Fixed-point types only.  reverse: suffix sums (the transpose).
+// test_unpublished != 0 leaves the first chunk's flags unset (failure injection).
+cudaError_t bsf_launch_vscan_lb(int prec, int n, int skew, bool reverse, bool short_tiles,
                                 void* S, long long pitch, int Hp, int Wp, void* aggs, void* incls,
                                 unsigned* sync_words, int spin_limit, int test_unpublished,
                                 DevStatus* st, cudaStream_t s);
@@ -72,7 +74,7 @@ cudaError_t bsf_launch_fold(const void* G, long long pitch, int Hp, int H, int W
 
 // Finite differences with the per-pixel step solve fused in (cov: [3][H][W]).
 // Output rows row0 .. row0 + rows - 1 of an H x W image (S holds that band).
-cudaError_t bsf_launch_stencil_d1(int elem_bytes, int n, const void* S, long long pitch, int R,
+cudaError_t bsf_launch_stencil_d1(int prec, int n, const void* S, long long pitch, int R,
                                   const float* cov, int rule, int H, int W, int row0, int rows,
                                   int q, void* out, int out_dtype, long long ldo, DevStatus* st,
                                   cudaStream_t s);

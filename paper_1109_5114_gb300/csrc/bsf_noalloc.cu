@@ -89,15 +89,15 @@ extern "C" int bsf_filter_noalloc(const void* img, int dtype, long long ld, int 
   // the status word must start from zero; everything else is fully written
   // before it is read
   if (cudaMemsetAsync(st, 0, sizeof(DevStatus), s) != cudaSuccess) return BSF_ECUDA;
-  if (bsf_launch_scan_rows(8, n, img, dtype, ld, H, W, reach, 0, boundary, frac_bits, S, pitch,
+  if (bsf_launch_scan_rows(BSF_FIX64, n, img, dtype, ld, H, W, reach, 0, boundary, frac_bits, S, pitch,
                            (int)Hp, (int)Wp, st, s) != cudaSuccess)
     return BSF_ECUDA;
   const int skews[3] = {0, 1, -1};
   for (int i = 0; i < 3; ++i)
-    if (bsf_launch_vscan(8, n, skews[i], false, S, pitch, (int)Hp, (int)Wp, kScanChunk, agg, carry, s) !=
+    if (bsf_launch_vscan(BSF_FIX64, n, skews[i], false, S, pitch, (int)Hp, (int)Wp, kScanChunk, agg, carry, s) !=
         cudaSuccess)
       return BSF_ECUDA;
-  if (bsf_launch_stencil_d1(8, n, S, pitch, reach, cov, BSF_STEP_D1, H, W, 0, H, frac_bits, out,
+  if (bsf_launch_stencil_d1(BSF_FIX64, n, S, pitch, reach, cov, BSF_STEP_D1, H, W, 0, H, frac_bits, out,
                             out_dtype, ldo, st, s) != cudaSuccess)
     return BSF_ECUDA;
 

@@ -23,6 +23,8 @@
 //
 // Arithmetic wraps modulo 2^64 or 2^128 (the element type), which the final
 // finite differences cancel exactly.
+#include <type_traits>
+
 #include "bsf_device.cuh"
 
 namespace {
@@ -37,7 +39,18 @@ constexpr int kRowThreads = 256;
 
 template <typename T, typename In>
 __device__ __forceinline__ T quantize_one(In fv, int q, float scale_f, bool& ok, float& ax) {
-  if constexpr (sizeof(In) == 1) {
+  if constexpr (!IsFixed<T>::value) {  // floating-point variants: the values themselves
+    ok = true;
+    ax = 0.f;
+    if constexpr (std::is_same<T, double>::value) {
+      return (double)fv;
+    } else if constexpr (sizeof(In) <= 4) {
+      return f32x2((float)fv, 0.f);
+    } else {  // float64 input: hi + lo carries its 48 leading bits
+      const float h = __double2float_rn(fv);
+      return f32x2(h, __double2float_rn(fv - (double)h));
+    }
+  } else if constexpr (sizeof(In) == 1) {
     ok = true;
     ax = (float)fv * scale_f;
     return (T)fv << q;
@@ -159,11 +172,11 @@ k_vscan_agg(const T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, 
 // zero-carry combine of the three-phase scan: state after prefix state s
 // followed by m rows whose zero-carry state is a
 template <typename T, int NF>
-__device__ __forceinline__ void tp_combine(T* s, const T* a, T m) {
+__device__ __forceinline__ void tp_combine(T* s, const T* a, long long m) {
   T ns[NF];
   ns[0] = s[0] + a[0];
-  if constexpr (NF >= 2) ns[1] = s[1] + m * s[0] + a[1];
-  if constexpr (NF >= 3) ns[2] = s[2] + m * s[1] + ((m * (m + 1)) >> 1) * s[0] + a[2];
+  if constexpr (NF >= 2) ns[1] = s[1] + bsf_mul_int(s[0], m) + a[1];
+  if constexpr (NF >= 3) ns[2] = s[2] + bsf_mul_int(s[1], m) + bsf_mul_int(s[0], m * (m + 1) / 2) + a[2];
 #pragma unroll
   for (int f = 0; f < NF; ++f) s[f] = ns[f];
 }
@@ -196,7 +209,7 @@ k_vscan_apply(T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, int 
     T a[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) a[f] = agg[((long long)j * NF + f) * Nu + ui];
-    tp_combine<T, NF>(s, a, (T)ch);  // every earlier chunk is full
+    tp_combine<T, NF>(s, a, ch);  // every earlier chunk is full
   }
   const int p32 = (int)pitch;
   for (int yb0 = y0; yb0 < y1; yb0 += kApplyBatch) {
@@ -247,10 +260,9 @@ template <typename T, bool SHORT> struct LbRows {
 // zero-carry state is X:  r_f = sum_{i<=f} C(m-1+i, i) P_{f-i} + X_f
 template <typename T, int NF>
 __device__ __forceinline__ void lb_combine(const T* P, const T* X, long long m, T* r) {
-  const T tm = (T)m;
   r[0] = P[0] + X[0];
-  if constexpr (NF >= 2) r[1] = P[1] + tm * P[0] + X[1];
-  if constexpr (NF >= 3) r[2] = P[2] + tm * P[1] + ((tm * (tm + 1)) >> 1) * P[0] + X[2];
+  if constexpr (NF >= 2) r[1] = P[1] + bsf_mul_int(P[0], m) + X[1];
+  if constexpr (NF >= 3) r[2] = P[2] + bsf_mul_int(P[1], m) + bsf_mul_int(P[0], m * (m + 1) / 2) + X[2];
 }
 
 __device__ __forceinline__ unsigned lb_load_acquire(const unsigned* p) {
@@ -529,22 +541,27 @@ cudaError_t launch_v_skew(int skew, T* S, long long pitch, int Hp, int Wp, int c
 
 }  // namespace
 
-cudaError_t bsf_launch_scan_rows(int elem_bytes, int n, const void* img, int dtype, long long ld,
+cudaError_t bsf_launch_scan_rows(int prec, int n, const void* img, int dtype, long long ld,
                                  int H, int W, int R, int row0, int boundary, int q, void* S,
                                  long long pitch, int Hp, int Wp, DevStatus* st, cudaStream_t s) {
 #define BSF_ROWS(T, NF) \
   return launch_rows_t<T, NF>(img, dtype, ld, H, W, R, row0, boundary, q, (T*)S, pitch, Hp, Wp, st, s)
-  if (elem_bytes == 8) {
-    if (n == 1) BSF_ROWS(uint64_t, 1);
-    if (n == 2) BSF_ROWS(uint64_t, 2);
-    if (n == 3) BSF_ROWS(uint64_t, 3);
-  } else if (elem_bytes == 16) {
-    if (n == 1) BSF_ROWS(u128, 1);
-    if (n == 2) BSF_ROWS(u128, 2);
-    if (n == 3) BSF_ROWS(u128, 3);
+  switch (prec * 10 + n) {
+    case 11: BSF_ROWS(uint64_t, 1);
+    case 12: BSF_ROWS(uint64_t, 2);
+    case 13: BSF_ROWS(uint64_t, 3);
+    case 21: BSF_ROWS(u128, 1);
+    case 22: BSF_ROWS(u128, 2);
+    case 23: BSF_ROWS(u128, 3);
+    case 31: BSF_ROWS(double, 1);
+    case 32: BSF_ROWS(double, 2);
+    case 33: BSF_ROWS(double, 3);
+    case 41: BSF_ROWS(f32x2, 1);
+    case 42: BSF_ROWS(f32x2, 2);
+    case 43: BSF_ROWS(f32x2, 3);
+    default: return cudaErrorInvalidValue;
   }
 #undef BSF_ROWS
-  return cudaErrorInvalidValue;
 }
 
 cudaError_t bsf_launch_suffix_rows(int elem_bytes, int n, void* S, long long pitch, int Hp, int Wp,
@@ -598,10 +615,12 @@ cudaError_t launch_lb_any(int skew, bool reverse, bool short_tiles, void* S, lon
 
 }  // namespace
 
-cudaError_t bsf_launch_vscan_lb(int elem_bytes, int n, int skew, bool reverse, bool short_tiles,
+cudaError_t bsf_launch_vscan_lb(int prec, int n, int skew, bool reverse, bool short_tiles,
                                 void* S, long long pitch, int Hp, int Wp, void* aggs, void* incls,
                                 unsigned* sync_words, int spin_limit, int test_unpublished,
                                 DevStatus* st, cudaStream_t s) {
+  const int elem_bytes = prec == 2 ? 16 : 8;
+  if (prec != 1 && prec != 2) return cudaErrorInvalidValue;  // fixed point only
   switch (elem_bytes * 10 + n) {
     case 81: return launch_lb_any<uint64_t, 1>(skew, reverse, short_tiles, S, pitch, Hp, Wp, aggs, incls, sync_words, spin_limit, test_unpublished, st, s);
     case 82: return launch_lb_any<uint64_t, 2>(skew, reverse, short_tiles, S, pitch, Hp, Wp, aggs, incls, sync_words, spin_limit, test_unpublished, st, s);
@@ -613,22 +632,27 @@ cudaError_t bsf_launch_vscan_lb(int elem_bytes, int n, int skew, bool reverse, b
   }
 }
 
-cudaError_t bsf_launch_vscan(int elem_bytes, int n, int skew, bool reverse, void* S, long long pitch,
+cudaError_t bsf_launch_vscan(int prec, int n, int skew, bool reverse, void* S, long long pitch,
                              int Hp, int Wp, int chunk, void* agg, void* carry, cudaStream_t s) {
 #define BSF_V(T, NF)                                                                              \
   return reverse ? launch_v_skew<T, NF, true>(skew, (T*)S, pitch, Hp, Wp, chunk, (T*)agg,        \
                                               (T*)carry, s)                                      \
                  : launch_v_skew<T, NF, false>(skew, (T*)S, pitch, Hp, Wp, chunk, (T*)agg,       \
                                                (T*)carry, s)
-  if (elem_bytes == 8) {
-    if (n == 1) BSF_V(uint64_t, 1);
-    if (n == 2) BSF_V(uint64_t, 2);
-    if (n == 3) BSF_V(uint64_t, 3);
-  } else if (elem_bytes == 16) {
-    if (n == 1) BSF_V(u128, 1);
-    if (n == 2) BSF_V(u128, 2);
-    if (n == 3) BSF_V(u128, 3);
+  switch (prec * 10 + n) {
+    case 11: BSF_V(uint64_t, 1);
+    case 12: BSF_V(uint64_t, 2);
+    case 13: BSF_V(uint64_t, 3);
+    case 21: BSF_V(u128, 1);
+    case 22: BSF_V(u128, 2);
+    case 23: BSF_V(u128, 3);
+    case 31: BSF_V(double, 1);
+    case 32: BSF_V(double, 2);
+    case 33: BSF_V(double, 3);
+    case 41: BSF_V(f32x2, 1);
+    case 42: BSF_V(f32x2, 2);
+    case 43: BSF_V(f32x2, 3);
+    default: return cudaErrorInvalidValue;
   }
 #undef BSF_V
-  return cudaErrorInvalidValue;
 }

@@ -12,6 +12,8 @@
 // One thread per output pixel; a warp covers 32 consecutive pixels of a row,
 // so each tap is a coalesced row segment of S whenever neighbouring pixels
 // share their steps (the covariance field is smooth).
+#include <type_traits>
+
 #include "bsf_solve.cuh"
 
 namespace {
@@ -32,12 +34,12 @@ __device__ __forceinline__ T comb(const T* __restrict__ S, int idx, const int* s
       return v0 - v1;
     } else if constexpr (NF == 2) {
       const T v2 = comb<T, NF, LVL - 1>(S, idx - 2 * sk, s);
-      return (v0 + v2) - (v1 << 1);
+      return (v0 + v2) - (v1 + v1);
     } else {
       const T v2 = comb<T, NF, LVL - 1>(S, idx - 2 * sk, s);
       const T v3 = comb<T, NF, LVL - 1>(S, idx - 3 * sk, s);
       const T a = v1 - v2;
-      return (v0 - v3) - ((a << 1) + a);
+      return (v0 - v3) - (a + a + a);
     }
   }
 }
@@ -106,29 +108,43 @@ k_stencil_d1(const T* __restrict__ S, long long pitch, int R, const float* __res
   const int s[4] = {L1 * e1, L2 * e2, L3 * e3, L4w * e4};
   const T acc = comb<T, NF, 4>(S, base, s);
 
-  // D = prod_k L_k^n (exact) and the bound max|Q| * D < 2^(b-1) that makes
-  // the modular accumulator equal the true one (checked in float32 with a
-  // margin far above its rounding: |acc| <= D max|Q| and max|Q| <= bound + 1/2)
-  T D = 1;
-  const T D1 = (T)(unsigned)(L1 * L2) * (T)(unsigned)(L3 * L4w);
-  const float Df1 = (float)(L1 * L2) * (float)(L3 * L4w);
-  float Df = Df1;
+  if constexpr (IsFixed<T>::value) {
+    // D = prod_k L_k^n (exact) and the bound max|Q| * D < 2^(b-1) that makes
+    // the modular accumulator equal the true one (checked in float32 with a
+    // margin far above its rounding: |acc| <= D max|Q| and max|Q| <= bound + 1/2)
+    T D = 1;
+    const T D1 = (T)(unsigned)(L1 * L2) * (T)(unsigned)(L3 * L4w);
+    const float Df1 = (float)(L1 * L2) * (float)(L3 * L4w);
+    float Df = Df1;
 #pragma unroll
-  for (int j = 0; j < NF; ++j) D *= D1;
+    for (int j = 0; j < NF; ++j) D *= D1;
 #pragma unroll
-  for (int j = 1; j < NF; ++j) Df *= Df1;
-  const float maxq = __uint_as_float(st->max_absq_bits) + 1.f;
-  const float lim = bsf_pow2_f32(ElemBits<T>::value - 1);
-  if (maxq * Df * 1.0001f >= lim) {
-    atomicAdd(&st->overflow_count, 1u);
-    bsf_set_error(st, BSF_EOVERFLOW);
-  }
-  if constexpr (sizeof(Out) == 4) {
-    const float xa = __fmul_rn(to_f32<T>(acc, D), scale_f);
-    out[(long long)y * ldo + x] = __fdiv_rn(xa, mass_f32<T>(D));
+    for (int j = 1; j < NF; ++j) Df *= Df1;
+    const float maxq = __uint_as_float(st->max_absq_bits) + 1.f;
+    const float lim = bsf_pow2_f32(ElemBits<T>::value - 1);
+    if (maxq * Df * 1.0001f >= lim) {
+      atomicAdd(&st->overflow_count, 1u);
+      bsf_set_error(st, BSF_EOVERFLOW);
+    }
+    if constexpr (sizeof(Out) == 4) {
+      const float xa = __fmul_rn(to_f32<T>(acc, D), scale_f);
+      out[(long long)(y) * ldo + x] = __fdiv_rn(xa, mass_f32<T>(D));
+    } else {
+      const double xa = __dmul_rn(to_f64<T>(acc), scale_d);
+      out[(long long)(y) * ldo + x] = __ddiv_rn(xa, mass_f64<T>(D));
+    }
   } else {
-    const double xa = __dmul_rn(to_f64<T>(acc), scale_d);
-    out[(long long)y * ldo + x] = __ddiv_rn(xa, mass_f64<T>(D));
+    // floating-point precision variants: acc / prod L^n
+    double Dd = 1.0;
+    const double D1 = (double)(L1 * L2) * (double)(L3 * L4w);
+#pragma unroll
+    for (int j = 0; j < NF; ++j) Dd *= D1;
+    double a;
+    if constexpr (std::is_same<T, double>::value) a = acc;
+    else a = (double)acc.hi + (double)acc.lo;
+    const double v = a / Dd;
+    if constexpr (sizeof(Out) == 4) out[(long long)(y) * ldo + x] = __double2float_rn(v);
+    else out[(long long)(y) * ldo + x] = v;
   }
 }
 
@@ -153,21 +169,27 @@ cudaError_t launch_t(const T* S, long long pitch, int R, const float* cov, int r
 
 }  // namespace
 
-cudaError_t bsf_launch_stencil_d1(int elem_bytes, int n, const void* S, long long pitch, int R,
+cudaError_t bsf_launch_stencil_d1(int prec, int n, const void* S, long long pitch, int R,
                                   const float* cov, int rule, int H, int W, int row0, int rows,
                                   int q, void* out, int out_dtype, long long ldo, DevStatus* st,
                                   cudaStream_t s) {
 #define BSF_ST(T, NF)                                                                          \
   return launch_t<T, NF>((const T*)S, pitch, R, cov, rule, H, W, row0, rows, q, out, out_dtype, \
                          ldo, st, s)
-  if (elem_bytes == 8) {
-    if (n == 1) BSF_ST(uint64_t, 1);
-    if (n == 2) BSF_ST(uint64_t, 2);
-    if (n == 3) BSF_ST(uint64_t, 3);
-  } else if (elem_bytes == 16) {
-    if (n == 1) BSF_ST(u128, 1);
-    if (n == 2) BSF_ST(u128, 2);
-    if (n == 3) BSF_ST(u128, 3);
+  switch (prec * 10 + n) {
+    case 11: BSF_ST(uint64_t, 1);
+    case 12: BSF_ST(uint64_t, 2);
+    case 13: BSF_ST(uint64_t, 3);
+    case 21: BSF_ST(u128, 1);
+    case 22: BSF_ST(u128, 2);
+    case 23: BSF_ST(u128, 3);
+    case 31: BSF_ST(double, 1);
+    case 32: BSF_ST(double, 2);
+    case 33: BSF_ST(double, 3);
+    case 41: BSF_ST(f32x2, 1);
+    case 42: BSF_ST(f32x2, 2);
+    case 43: BSF_ST(f32x2, 3);
+    default: break;
   }
 #undef BSF_ST
   return cudaErrorInvalidValue;

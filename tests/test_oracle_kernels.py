@@ -186,3 +186,29 @@ def test_finalize_small_exact():
     D = np.array([[3, 3, 7]], dtype=np.int64)
     np.testing.assert_array_equal(finalize(acc, D, 1, np.float64), [[1.0, -1.5, 0.0]])
     np.testing.assert_array_equal(finalize(acc, D, 1, np.float32), np.float32([[1.0, -1.5, 0.0]]))
+
+
+def test_int64_kernel_equals_exact_kernel():
+    rng = np.random.default_rng(11)
+    for n in (1, 2, 3):
+        for _ in range(5):
+            L = tuple(int(v) for v in rng.integers(1, 9, size=4))
+            if n % 2 == 1:
+                L = tuple(2 * (v // 2) + 1 for v in L)
+            K, ox, oy = kernels.kernel_d1(L, n)
+            K2, ox2, oy2 = kernels.kernel_d1_int64(L, n)
+            assert (ox, oy) == (ox2, oy2)
+            np.testing.assert_array_equal(K.astype(np.int64), K2)
+
+
+def test_sampled_exact_correlation_matches_full():
+    H, W, n = 12, 15, 3
+    f = wl.random_integer_image(H, W, seed=4, lo=0, hi=256)
+    cov = wl.random_cov_field(H, W, seed=6, sigma_range=(0.5, 3), rho_range=(1, 3))
+    L, _ = params.integer_steps(cov[0], cov[1], cov[2], n)
+    fq = quantize(f, 0)
+    full = kernels.correlate_exact(fq, L, n, 2)
+    pix = [(0, 0), (5, 7), (11, 14), (3, 12)]
+    samp = kernels.correlate_exact_sampled(fq, L, n, 2, pix)
+    for p in pix:
+        assert samp[p] == full[p]
