@@ -386,6 +386,79 @@ def run_reference(args):
     }
 
 
+BATCH_WORKLOAD = ("batch: 64 fp32 blob images, sides log-uniform in [128, 2048] (H and W "
+                  "independent, seed 1), each with its own smooth random covariance field "
+                  "(sigma 1-24 px, rho 1-3, random orientation), N=4, n=2, uint64 running sums")
+
+
+def run_batch(args):
+    """Batched form: one launch per phase over 64 images, replayed from a CUDA
+    graph, against the same kernels launched image by image."""
+    import torch
+    import workloads as wl
+    from paper_1109_5114_gb300 import bsf
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    sizes = wl.batch_sizes_loguniform(64, seed=1, lo=128, hi=2048)
+    imgs, covs = [], []
+    for i, (h, w) in enumerate(sizes):
+        imgs.append(torch.from_numpy(wl.blob_image(h, w, seed=1000 + i)).cuda())
+        covs.append(torch.from_numpy(wl.random_cov_field(h, w, seed=2000 + 3 * i,
+                                                         sigma_range=(1.0, 24.0),
+                                                         rho_range=(1.0, 3.0))).cuda())
+    outs = [torch.empty_like(im) for im in imgs]
+    vmax = max(float(im.abs().max()) for im in imgs)
+    px = sum(h * w for h, w in sizes)
+    bf = bsf.BatchFilter(ORDER, "symmetric", frac_bits=-1, value_bound=vmax)
+    torch.cuda.synchronize()
+    info = bf.plan(imgs, covs, outs, autotune=True)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    bstream = bf.stream()
+    results = {}
+    for name, flags in [("per_image", bsf.BSF_BATCH_PER_IMAGE), ("batched", 0),
+                        ("graph", bsf.BSF_BATCH_GRAPH)]:
+        for _ in range(args.warmup):
+            bf.run(flags)
+        assert bf.status() == 0
+        total = 0.0
+        for _ in range(args.steps):
+            with torch.cuda.stream(bstream):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(bstream)
+            bf.run(flags)
+            with torch.cuda.stream(bstream):
+                e1.record(bstream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        assert bf.status() == 0
+        total = max_over_ranks(total, world)
+        results[name] = {"ms_per_step": round(total / args.steps, 4),
+                         "value": round(world * px * args.steps / (total * 1e-3) / 1e6, 2)}
+    bf.close()
+    if rank != 0:
+        return None
+    g = results["graph"]
+    return {
+        "metric": METRIC, "value": g["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": g["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "images": len(sizes), "pixels": px, "n": ORDER,
+                   "frac_bits": info.frac_bits, "scan_chunk_by_class": list(info.scan_chunk),
+                   "arena_bytes": info.arena_bytes,
+                   "l2": "flushed before every timed step (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "modes": results,
+        "gpu_launches_per_step": {"per_image": 8 * len(sizes), "batched": 8, "graph": 1},
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -397,10 +470,17 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=256,
                     help="rows of the workload each --impl reference step filters")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="spacevariant2048", choices=["spacevariant2048", "batch64"],
+                    help="spacevariant2048: the benchmark line; batch64: the batched form")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "bsf":
         args.warmup = 3
-    line = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if args.impl == "reference":
+        line = run_reference(args)
+    elif args.workload == "batch64":
+        line = run_batch(args)
+    else:
+        line = run_gpu(args)
     if line is not None:
         print(json.dumps(line), flush=True)
 

@@ -305,6 +305,90 @@ int bsf_filter_noalloc(const void* img, int dtype, long long ld, int H, int W, i
                        int boundary, int reach, int frac_bits, const float* cov,
                        void* out, int out_dtype, long long ldo, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batches: many images of uneven sizes, each with its own covariance field
+ * (the paper filters one image at a time; batching is this library's
+ * serving form).  One batch object owns one device arena laid out for a
+ * given list of images; every image keeps its own padding R and scan chunk
+ * height, and all share one q.
+ * ------------------------------------------------------------------------ */
+typedef struct bsf_batch* bsf_batch_t;
+
+/* One image of a batch (device pointers; the caller owns them). */
+typedef struct {
+  int H, W;              /* image size */
+  const void* img;       /* [H][ld] of dtype */
+  int dtype;             /* BSF_U8 / BSF_F32 / BSF_F64; the same for every image */
+  long long ld;
+  const float* cov;      /* [3][H][W] float32 (C11, C12, C22) */
+  void* out;             /* [H][ldo] of out_dtype */
+  int out_dtype;         /* BSF_F32 / BSF_F64; the same for every image */
+  long long ldo;
+} bsf_image_desc;
+
+typedef struct {
+  int B;                 /* images in the plan */
+  int frac_bits;         /* common q */
+  long long arena_bytes; /* running sums + scan states of all images */
+  int scan_chunk[4];     /* scan chunk rows per padded-height class (<=384, <=768, <=1536, more) */
+  int blocks[5];         /* blocks of the five batched phases (rows, d3, d2, d4, stencil) */
+  long long pixels;      /* output pixels of the batch */
+  int graph_ready;       /* a CUDA graph of the batched launches is instantiated */
+} bsf_batch_info_t;
+
+#define BSF_BATCH_GRAPH      1  /* record the batched launches once in a CUDA graph, replay it */
+#define BSF_BATCH_PER_IMAGE  2  /* baseline: the per-image kernels, image after image */
+#define BSF_BATCH_AUTOTUNE   4  /* bsf_batch_plan: time scan chunk heights per size class */
+
+/* Create a batch object for order n (1..3) and a boundary rule.  It uses
+ * uint64 running sums and its own non-blocking stream.  Errors: BSF_EINVAL,
+ * BSF_ENOMEM, BSF_ECUDA. */
+int bsf_batch_create(bsf_batch_t* out, int n, int boundary);
+
+/* Free the batch (synchronises its stream).  NULL is a no-op. */
+void bsf_batch_destroy(bsf_batch_t b);
+
+/* Use this cudaStream_t (must not be the legacy default stream: graph
+ * capture needs a real stream).  Drops a recorded graph. */
+int bsf_batch_set_stream(bsf_batch_t b, void* stream);
+
+/* The batch's stream (its own unless set). */
+void* bsf_batch_stream(bsf_batch_t b);
+
+/* q for the batch: frac_bits in [0, 62], or -1 for automatic (the smallest
+ * per-image choice from value_bound (max |f| over the batch; uint8 uses 255)
+ * and each image's largest kernel mass). */
+int bsf_batch_set_precision(bsf_batch_t b, int frac_bits, double value_bound);
+
+/* Text file in which autotuned chunk heights are kept (read now, appended
+ * after tuning); lines "gpu class n rows". */
+int bsf_batch_set_tune_cache(bsf_batch_t b, const char* path);
+
+/* Plan a batch of B images (host array of descriptors): solve each image's
+ * steps to find its R (synchronous), choose q, allocate one arena, build the
+ * per-phase block offsets; with BSF_BATCH_AUTOTUNE also time scan chunk
+ * heights of 32, 64 and 128 rows on the largest image of each height class
+ * (running the filter on it) and keep the fastest.
+ * Errors: BSF_EINVAL, BSF_ENOMEM, BSF_ECUDA. */
+int bsf_batch_plan(bsf_batch_t b, int B, const bsf_image_desc* descs, int flags);
+
+/* Filter every image of the planned batch (descs must equal the plan's).
+ * Default: one launch per phase for the whole batch (row sums, the two
+ * kernels of each vertical direction, finite differences: 8 launches);
+ * BSF_BATCH_GRAPH records them in a CUDA graph on the first call and replays
+ * it; BSF_BATCH_PER_IMAGE runs the single-image kernels image by image
+ * (8 launches per image).  Asynchronous on the batch's stream.
+ * Errors: BSF_EINVAL, BSF_ESTATE, BSF_ECUDA; device-side problems go to
+ * bsf_batch_status. */
+int bsf_filter_batched(bsf_batch_t b, int B, const bsf_image_desc* descs, int flags);
+
+/* Synchronise and return the first device-side error since the last call
+ * (as bsf_status), then clear it. */
+int bsf_batch_status(bsf_batch_t b);
+
+int bsf_batch_get_info(bsf_batch_t b, bsf_batch_info_t* info);
+const char* bsf_batch_last_error(bsf_batch_t b);
+
 #ifdef __cplusplus
 }
 #endif

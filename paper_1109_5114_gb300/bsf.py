@@ -80,6 +80,30 @@ bsf_filter_backward = _fn("bsf_filter_backward", c_int, bsf_t, c_void_p, c_ll, c
                           c_void_p, c_ll, c_void_p)
 bsf_read_profile = _fn("bsf_read_profile", c_int, bsf_t, ctypes.POINTER(c_double), ctypes.POINTER(c_int))
 
+class bsf_image_desc(ctypes.Structure):
+    _fields_ = [("H", c_int), ("W", c_int), ("img", c_void_p), ("dtype", c_int), ("ld", c_ll),
+                ("cov", c_void_p), ("out", c_void_p), ("out_dtype", c_int), ("ldo", c_ll)]
+
+
+class bsf_batch_info_t(ctypes.Structure):
+    _fields_ = [("B", c_int), ("frac_bits", c_int), ("arena_bytes", c_ll),
+                ("scan_chunk", c_int * 4), ("blocks", c_int * 5), ("pixels", c_ll),
+                ("graph_ready", c_int)]
+
+
+bsf_batch_t = ctypes.c_void_p
+bsf_batch_create = _fn("bsf_batch_create", c_int, ctypes.POINTER(bsf_batch_t), c_int, c_int)
+bsf_batch_destroy = _fn("bsf_batch_destroy", None, bsf_batch_t)
+bsf_batch_set_stream = _fn("bsf_batch_set_stream", c_int, bsf_batch_t, c_void_p)
+bsf_batch_stream = _fn("bsf_batch_stream", c_void_p, bsf_batch_t)
+bsf_batch_set_precision = _fn("bsf_batch_set_precision", c_int, bsf_batch_t, c_int, c_double)
+bsf_batch_set_tune_cache = _fn("bsf_batch_set_tune_cache", c_int, bsf_batch_t, ctypes.c_char_p)
+bsf_batch_plan = _fn("bsf_batch_plan", c_int, bsf_batch_t, c_int, ctypes.POINTER(bsf_image_desc), c_int)
+bsf_filter_batched = _fn("bsf_filter_batched", c_int, bsf_batch_t, c_int, ctypes.POINTER(bsf_image_desc), c_int)
+bsf_batch_status = _fn("bsf_batch_status", c_int, bsf_batch_t)
+bsf_batch_get_info = _fn("bsf_batch_get_info", c_int, bsf_batch_t, ctypes.POINTER(bsf_batch_info_t))
+bsf_batch_last_error = _fn("bsf_batch_last_error", ctypes.c_char_p, bsf_batch_t)
+
 ERROR_NAMES = {v: k for k, v in _C.items() if k.startswith("BSF_E")}
 
 
@@ -295,3 +319,70 @@ def box_spline_filter(img, cov, filt: "BoxSplineFilter"):
     except NameError:
         fn = _AUTOGRAD = _make_autograd()
     return fn.apply(img, cov, filt)
+
+
+class BatchFilter:
+    """A batch of images of uneven sizes on one device arena (bsf_batch_*).
+
+    imgs / covs / outs are lists of CUDA tensors ([H][W], [3][H][W] float32,
+    [H][W]).  The batch runs on its own stream; ``stream()`` gives it as a
+    torch external stream for ordering with torch work.
+    """
+
+    def __init__(self, n: int, boundary="symmetric", frac_bits: int = -1, value_bound: float = 0.0):
+        if isinstance(boundary, str):
+            boundary = _BOUNDARY[boundary]
+        b = bsf_batch_t()
+        rc = bsf_batch_create(ctypes.byref(b), n, boundary)
+        if rc != 0:
+            raise BsfError(rc, "bsf_batch_create")
+        self._b = b
+        self._chk(bsf_batch_set_precision(b, frac_bits, float(value_bound)))
+
+    def _chk(self, rc):
+        if rc != 0:
+            raise BsfError(rc, bsf_batch_last_error(self._b).decode())
+
+    def close(self):
+        if getattr(self, "_b", None):
+            bsf_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tune_cache(self, path: str):
+        self._chk(bsf_batch_set_tune_cache(self._b, path.encode()))
+
+    def plan(self, imgs, covs, outs, autotune: bool = False):
+        B = len(imgs)
+        arr = (bsf_image_desc * B)()
+        for i, (im, cv, ot) in enumerate(zip(imgs, covs, outs)):
+            H, W = im.shape
+            assert im.is_cuda and im.stride(1) == 1 and ot.is_cuda and ot.shape == (H, W) and ot.stride(1) == 1
+            assert cv.is_cuda and cv.dtype.itemsize == 4 and cv.shape == (3, H, W) and cv.is_contiguous()
+            arr[i] = bsf_image_desc(H, W, im.data_ptr(), _dtype_code(im), im.stride(0), cv.data_ptr(),
+                                    ot.data_ptr(), BSF_F32 if ot.dtype.itemsize == 4 else BSF_F64,  # noqa: F821
+                                    ot.stride(0))
+        self._descs = arr
+        self._B = B
+        self._chk(bsf_batch_plan(self._b, B, arr, BSF_BATCH_AUTOTUNE if autotune else 0))  # noqa: F821
+        return self.info()
+
+    def run(self, flags: int = 0):
+        self._chk(bsf_filter_batched(self._b, self._B, self._descs, flags))
+
+    def status(self) -> int:
+        return bsf_batch_status(self._b)
+
+    def info(self) -> bsf_batch_info_t:
+        inf = bsf_batch_info_t()
+        self._chk(bsf_batch_get_info(self._b, ctypes.byref(inf)))
+        return inf
+
+    def stream(self):
+        import torch
+        return torch.cuda.ExternalStream(bsf_batch_stream(self._b))

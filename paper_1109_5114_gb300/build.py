@@ -27,7 +27,7 @@ COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
 EXTRA = {"bsf_steps.cu": ["-fmad=false"]}
 
 SOURCES = ["bsf_api.cu", "bsf_steps.cu", "bsf_scan.cu", "bsf_stencil.cu", "bsf_backward.cu",
-           "bsf_noalloc.cu"]
+           "bsf_batch.cu", "bsf_noalloc.cu"]
 
 
 def nvcc() -> str:

@@ -72,6 +72,32 @@ cudaError_t bsf_launch_fold(const void* G, long long pitch, int Hp, int H, int W
                             int boundary, void* Gx, float* gimg, long long ldo, const DevStatus* st,
                             cudaStream_t s);
 
+// ---- batched form: one launch per phase over every image of a batch --------
+// Per-image parameters of a batch (device array).  S and agg point into the
+// batch's arena; q is common to the batch.
+struct BatchImage {
+  const void* img;
+  long long ld;
+  const float* cov;
+  void* out;
+  long long ldo;
+  void* S;
+  void* agg;
+  long long pitch;
+  int H, W, R, Hp, Wp, ch;
+};
+// Phases with their own block ranges: starts[phase * (B + 1) + i] is the first
+// block of image i (starts[... + B] = total blocks).
+enum { kBatchRows = 0, kBatchV0 = 1, kBatchVp = 2, kBatchVm = 3, kBatchStencil = 4, kBatchPhases = 5 };
+
+cudaError_t bsf_launch_batch_rows(int n, int dtype, const BatchImage* imgs, const int* starts, int B,
+                                  int total, int boundary, int q, DevStatus* st, cudaStream_t s);
+cudaError_t bsf_launch_batch_vscan(int n, int skew, const BatchImage* imgs, const int* starts, int B,
+                                   int total, cudaStream_t s);
+cudaError_t bsf_launch_batch_stencil(int n, int out_dtype, const BatchImage* imgs, const int* starts,
+                                     int B, int total, int rule, int q, DevStatus* st,
+                                     cudaStream_t s);
+
 // Finite differences with the per-pixel step solve fused in (cov: [3][H][W]).
 // Output rows row0 .. row0 + rows - 1 of an H x W image (S holds that band).
 cudaError_t bsf_launch_stencil_d1(int prec, int n, const void* S, long long pitch, int R,

@@ -65,13 +65,12 @@ __device__ __forceinline__ T quantize_one(In fv, int q, float scale_f, bool& ok,
 }
 
 template <typename T, int NF, typename In, int V>
-__global__ void __launch_bounds__(kRowThreads)
-k_scan_rows(const In* __restrict__ img, long long ld, int H, int W, int R, int row0, int boundary,
-            float scale_f, int q, T* __restrict__ S, long long pitch, int Hp, int Wp,
-            DevStatus* st) {
+__device__ __forceinline__ void scan_rows_body(const In* __restrict__ img, long long ld, int H,
+                                               int W, int R, int row0, int boundary, float scale_f,
+                                               int q, T* __restrict__ S, long long pitch, int Hp,
+                                               int Wp, DevStatus* st, int yp) {
   constexpr int NW = kRowThreads / 32;
   __shared__ T s_warp[NF][NW];
-  const int yp = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   bool yvalid;
   const int ys = bsf_map_index(row0 + yp - R, H, boundary, yvalid);  // row0: first row of a band
@@ -140,17 +139,25 @@ k_scan_rows(const In* __restrict__ img, long long ld, int H, int W, int R, int r
   }
 }
 
+template <typename T, int NF, typename In, int V>
+__global__ void __launch_bounds__(kRowThreads)
+k_scan_rows(const In* __restrict__ img, long long ld, int H, int W, int R, int row0, int boundary,
+            float scale_f, int q, T* __restrict__ S, long long pitch, int Hp, int Wp,
+            DevStatus* st) {
+  scan_rows_body<T, NF, In, V>(img, ld, H, W, R, row0, boundary, scale_f, q, S, pitch, Hp, Wp, st,
+                               blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // d3 / d2 / d4 in skewed coordinates
 // ---------------------------------------------------------------------------
 template <typename T, int NF, int SKEW, bool REV>
-__global__ void __launch_bounds__(128)
-k_vscan_agg(const T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, int Nu, int ch,
-            T* __restrict__ agg) {
-  const int ui = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void vscan_agg_body(const T* __restrict__ S, long long pitch, int Hp,
+                                               int Wp, int umin, int Nu, int ch,
+                                               T* __restrict__ agg, int bx, int c) {
+  const int ui = bx * 128 + threadIdx.x;
   if (ui >= Nu) return;
   const int u = umin + ui;
-  const int c = blockIdx.y;
   const int y0 = c * ch, y1 = min(y0 + ch, Hp);
   T s[NF];
 #pragma unroll
@@ -167,6 +174,13 @@ k_vscan_agg(const T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, 
   }
 #pragma unroll
   for (int f = 0; f < NF; ++f) agg[((long long)c * NF + f) * Nu + ui] = s[f];
+}
+
+template <typename T, int NF, int SKEW, bool REV>
+__global__ void __launch_bounds__(128)
+k_vscan_agg(const T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, int Nu, int ch,
+            T* __restrict__ agg) {
+  vscan_agg_body<T, NF, SKEW, REV>(S, pitch, Hp, Wp, umin, Nu, ch, agg, blockIdx.x, blockIdx.y);
 }
 
 // zero-carry combine of the three-phase scan: state after prefix state s
@@ -189,13 +203,12 @@ __device__ __forceinline__ void tp_combine(T* s, const T* a, long long m) {
 constexpr int kApplyBatch = 16;
 
 template <typename T, int NF, int SKEW, bool REV>
-__global__ void __launch_bounds__(128)
-k_vscan_apply(T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, int Nu, int ch,
-              const T* __restrict__ agg) {
-  const int ui = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void vscan_apply_body(T* __restrict__ S, long long pitch, int Hp, int Wp,
+                                                 int umin, int Nu, int ch, const T* __restrict__ agg,
+                                                 int bx, int c) {
+  const int ui = bx * 128 + threadIdx.x;
   if (ui >= Nu) return;
   const int u = umin + ui;
-  const int c = blockIdx.y;
   const int y0 = c * ch, y1 = min(y0 + ch, Hp);
   // skip lines that do not cross this chunk
   const int ya = REV ? Hp - 1 - y0 : y0, yb = REV ? Hp - y1 : y1 - 1;
@@ -232,6 +245,13 @@ k_vscan_apply(T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, int 
       if (idx[r] >= 0) S[idx[r]] = s[NF - 1];
     }
   }
+}
+
+template <typename T, int NF, int SKEW, bool REV>
+__global__ void __launch_bounds__(128)
+k_vscan_apply(T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, int Nu, int ch,
+              const T* __restrict__ agg) {
+  vscan_apply_body<T, NF, SKEW, REV>(S, pitch, Hp, Wp, umin, Nu, ch, agg, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -655,4 +675,90 @@ cudaError_t bsf_launch_vscan(int prec, int n, int skew, bool reverse, void* S, l
     default: return cudaErrorInvalidValue;
   }
 #undef BSF_V
+}
+
+// ---------------------------------------------------------------------------
+// Batched kernels: a block finds its image by binary search over the block
+// offsets of the phase, then runs the single-image body on it.
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ int batch_find(const int* __restrict__ starts, int B, int blk) {
+  int lo = 0, hi = B - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (starts[mid] <= blk) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T, int NF, typename In>
+__global__ void __launch_bounds__(kRowThreads)
+k_batch_rows(const BatchImage* __restrict__ imgs, const int* __restrict__ starts, int B,
+             int boundary, int q, DevStatus* st) {
+  const int i = batch_find(starts, B, blockIdx.x);
+  const BatchImage& im = imgs[i];
+  scan_rows_body<T, NF, In, 4>((const In*)im.img, im.ld, im.H, im.W, im.R, 0, boundary,
+                               bsf_pow2_f32(q), q, (T*)im.S, im.pitch, im.Hp, im.Wp, st,
+                               blockIdx.x - starts[i]);
+}
+
+template <typename T, int NF, int SKEW, bool APPLY>
+__global__ void __launch_bounds__(128)
+k_batch_vscan(const BatchImage* __restrict__ imgs, const int* __restrict__ starts, int B) {
+  const int i = batch_find(starts, B, blockIdx.x);
+  const BatchImage& im = imgs[i];
+  const int local = blockIdx.x - starts[i];
+  const int Nu = SKEW == 0 ? im.Wp : im.Wp + im.Hp - 1;
+  const int umin = SKEW == 1 ? -(im.Hp - 1) : 0;
+  const int gx = (Nu + 127) / 128;
+  const int bx = local % gx, c = local / gx;
+  if (APPLY)
+    vscan_apply_body<T, NF, SKEW, false>((T*)im.S, im.pitch, im.Hp, im.Wp, umin, Nu, im.ch,
+                                         (const T*)im.agg, bx, c);
+  else
+    vscan_agg_body<T, NF, SKEW, false>((const T*)im.S, im.pitch, im.Hp, im.Wp, umin, Nu, im.ch,
+                                       (T*)im.agg, bx, c);
+}
+
+}  // namespace
+
+cudaError_t bsf_launch_batch_rows(int n, int dtype, const BatchImage* imgs, const int* starts, int B,
+                                  int total, int boundary, int q, DevStatus* st, cudaStream_t s) {
+#define BSF_BR(NF, In) k_batch_rows<uint64_t, NF, In><<<total, kRowThreads, 0, s>>>(imgs, starts, B, boundary, q, st)
+  if (dtype == BSF_F32) {
+    if (n == 1) BSF_BR(1, float); else if (n == 2) BSF_BR(2, float); else BSF_BR(3, float);
+  } else if (dtype == BSF_U8) {
+    if (n == 1) BSF_BR(1, uint8_t); else if (n == 2) BSF_BR(2, uint8_t); else BSF_BR(3, uint8_t);
+  } else if (dtype == BSF_F64) {
+    if (n == 1) BSF_BR(1, double); else if (n == 2) BSF_BR(2, double); else BSF_BR(3, double);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+#undef BSF_BR
+  return cudaGetLastError();
+}
+
+namespace {
+template <int NF, int SKEW>
+void batch_vscan_t(const BatchImage* imgs, const int* starts, int B, int total, cudaStream_t s) {
+  k_batch_vscan<uint64_t, NF, SKEW, false><<<total, 128, 0, s>>>(imgs, starts, B);
+  k_batch_vscan<uint64_t, NF, SKEW, true><<<total, 128, 0, s>>>(imgs, starts, B);
+}
+template <int NF>
+void batch_vscan_n(int skew, const BatchImage* imgs, const int* starts, int B, int total,
+                   cudaStream_t s) {
+  if (skew == 0) batch_vscan_t<NF, 0>(imgs, starts, B, total, s);
+  else if (skew == 1) batch_vscan_t<NF, 1>(imgs, starts, B, total, s);
+  else batch_vscan_t<NF, -1>(imgs, starts, B, total, s);
+}
+}  // namespace
+
+cudaError_t bsf_launch_batch_vscan(int n, int skew, const BatchImage* imgs, const int* starts, int B,
+                                   int total, cudaStream_t s) {
+  if (n == 1) batch_vscan_n<1>(skew, imgs, starts, B, total, s);
+  else if (n == 2) batch_vscan_n<2>(skew, imgs, starts, B, total, s);
+  else if (n == 3) batch_vscan_n<3>(skew, imgs, starts, B, total, s);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
 }

@@ -75,14 +75,15 @@ template <typename T, int NF> struct StencilOcc {
 // The step solve of bsf_solve.cuh runs here, per pixel, so its arithmetic
 // overlaps the gathers of other warps and no step field goes through HBM.
 template <typename T, int NF, typename Out>
-__global__ void __launch_bounds__(256, (StencilOcc<T, NF>::value))
-k_stencil_d1(const T* __restrict__ S, long long pitch, int R, const float* __restrict__ cov,
-             int rule, int H, int W, int row0, int rows, float scale_f, double scale_d,
-             Out* __restrict__ out, long long ldo, DevStatus* st) {
+__device__ __forceinline__ void stencil_d1_body(const T* __restrict__ S, long long pitch, int R,
+                                                const float* __restrict__ cov, int rule, int H,
+                                                int W, int row0, int rows, float scale_f,
+                                                double scale_d, Out* __restrict__ out,
+                                                long long ldo, DevStatus* st, int bx, int by) {
   // pixel (x, row0 + y) of an H x W image; rows [row0, row0 + rows) are
   // filtered from running sums whose padded row 0 is image row row0 - R
-  const int x = blockIdx.x * 32 + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int x = bx * 32 + threadIdx.x;
+  const int y = by * blockDim.y + threadIdx.y;
   if (x >= W || y >= rows) return;
   const long long HW = (long long)H * W, i = (long long)(row0 + y) * W + x;
   int L[4], flags, reach;
@@ -148,6 +149,15 @@ k_stencil_d1(const T* __restrict__ S, long long pitch, int R, const float* __res
   }
 }
 
+template <typename T, int NF, typename Out>
+__global__ void __launch_bounds__(256, (StencilOcc<T, NF>::value))
+k_stencil_d1(const T* __restrict__ S, long long pitch, int R, const float* __restrict__ cov,
+             int rule, int H, int W, int row0, int rows, float scale_f, double scale_d,
+             Out* __restrict__ out, long long ldo, DevStatus* st) {
+  stencil_d1_body<T, NF, Out>(S, pitch, R, cov, rule, H, W, row0, rows, scale_f, scale_d, out, ldo,
+                              st, blockIdx.x, blockIdx.y);
+}
+
 template <typename T, int NF>
 cudaError_t launch_t(const T* S, long long pitch, int R, const float* cov, int rule, int H, int W,
                      int row0, int rows, int q, void* out, int out_dtype, long long ldo,
@@ -193,4 +203,48 @@ cudaError_t bsf_launch_stencil_d1(int prec, int n, const void* S, long long pitc
   }
 #undef BSF_ST
   return cudaErrorInvalidValue;
+}
+
+namespace {
+
+__device__ __forceinline__ int batch_find_st(const int* __restrict__ starts, int B, int blk) {
+  int lo = 0, hi = B - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (starts[mid] <= blk) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int NF, typename Out>
+__global__ void __launch_bounds__(256, (StencilOcc<uint64_t, NF>::value))
+k_batch_stencil(const BatchImage* __restrict__ imgs, const int* __restrict__ starts, int B, int rule,
+                float scale_f, double scale_d, DevStatus* st) {
+  const int i = batch_find_st(starts, B, blockIdx.x);
+  const BatchImage& im = imgs[i];
+  const int local = blockIdx.x - starts[i];
+  const int gx = (im.W + 31) / 32;
+  stencil_d1_body<uint64_t, NF, Out>((const uint64_t*)im.S, im.pitch, im.R, im.cov, rule, im.H,
+                                     im.W, 0, im.H, scale_f, scale_d, (Out*)im.out, im.ldo, st,
+                                     local % gx, local / gx);
+}
+
+}  // namespace
+
+cudaError_t bsf_launch_batch_stencil(int n, int out_dtype, const BatchImage* imgs, const int* starts,
+                                     int B, int total, int rule, int q, DevStatus* st,
+                                     cudaStream_t s) {
+  const dim3 block(32, 8);
+  const float sf = ldexpf(1.f, -q);
+  const double sd = ldexp(1.0, -q);
+#define BSF_BS(NF, O) k_batch_stencil<NF, O><<<total, block, 0, s>>>(imgs, starts, B, rule, sf, sd, st)
+  if (out_dtype == BSF_F32) {
+    if (n == 1) BSF_BS(1, float); else if (n == 2) BSF_BS(2, float); else BSF_BS(3, float);
+  } else if (out_dtype == BSF_F64) {
+    if (n == 1) BSF_BS(1, double); else if (n == 2) BSF_BS(2, double); else BSF_BS(3, double);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+#undef BSF_BS
+  return cudaGetLastError();
 }

@@ -89,7 +89,7 @@ def covariance_from_axes(sigma, rho, theta) -> np.ndarray:
     c11 = k * (rho * c * c + s * s)
     c22 = k * (rho * s * s + c * c)
     c12 = k * (rho - 1.0) * s * c
-    return np.stack([c11, c12, c22]).astype(np.float32)
+    return np.ascontiguousarray(np.stack([c11, c12, c22]), dtype=np.float32)
 
 
 def constant_cov_field(H: int, W: int, c11: float, c12: float, c22: float) -> np.ndarray:
@@ -116,16 +116,19 @@ def diagonal_ramp_cov_field(H: int, W: int, sigma_lo: float = 1.0, sigma_hi: flo
 
 
 def _bilinear_upsample(g: np.ndarray, H: int, W: int) -> np.ndarray:
+    """Bilinear interpolation of g onto an H x W grid spanning the same extent."""
     h, w = g.shape
     ys = np.linspace(0.0, h - 1.0, H)
     xs = np.linspace(0.0, w - 1.0, W)
-    rows = np.empty((h, W))
-    for i in range(h):
-        rows[i] = np.interp(xs, np.arange(w), g[i])
-    out = np.empty((H, W))
-    for j in range(W):
-        out[:, j] = np.interp(ys, np.arange(h), rows[:, j])
-    return out
+    y0 = np.minimum(np.floor(ys).astype(np.int64), h - 2) if h > 1 else np.zeros(H, np.int64)
+    x0 = np.minimum(np.floor(xs).astype(np.int64), w - 2) if w > 1 else np.zeros(W, np.int64)
+    wy = (ys - y0)[:, None]
+    wx = (xs - x0)[None, :]
+    y1 = np.minimum(y0 + 1, h - 1)
+    x1 = np.minimum(x0 + 1, w - 1)
+    top = g[y0][:, x0] * (1 - wx) + g[y0][:, x1] * wx
+    bot = g[y1][:, x0] * (1 - wx) + g[y1][:, x1] * wx
+    return np.ascontiguousarray(top * (1 - wy) + bot * wy)
 
 
 def smooth_field(H: int, W: int, seed: int, lo: float, hi: float,
@@ -165,7 +168,7 @@ def param_fields_logsig_theta_logrho(H: int, W: int, seed: int,
     a = smooth_field(H, W, seed, logsig_range[0], logsig_range[1])
     b = smooth_field(H, W, seed + 1, 0.0, math.pi)
     c = smooth_field(H, W, seed + 2, logrho_range[0], logrho_range[1])
-    return np.stack([a, b, c]).astype(np.float32)
+    return np.ascontiguousarray(np.stack([a, b, c]), dtype=np.float32)
 
 
 def batch_sizes_loguniform(B: int, seed: int = 1, lo: int = 128, hi: int = 2048):
