@@ -16,8 +16,11 @@ modular   the paper's pipeline -- running sums, then finite differences --
           in exact two's-complement modular arithmetic.
 gaussian  Gaussian-approximation errors of continuous box splines (Theorem 1,
           Table 2) by Parseval.
+backward  the adjoint of the integer-step filter with respect to the image.
+continuous  the continuous-step filter (interpolated taps, Section 2.3) and
+          the derivative of its output with respect to the covariance field.
 
 Parity status of each function is stated in its docstring; "parity unpinned"
 marks a function with no independent pin.
 """
-from . import params, kernels, modular, gaussian, backward  # noqa: F401
+from . import params, kernels, modular, gaussian, backward, continuous  # noqa: F401
