@@ -32,7 +32,8 @@
  *   - Pointers named "device" must point to device memory of the current
  *     device; the caller owns them.  Images are row-major [H][ld] (ld >= W
  *     elements).  Covariance fields are three contiguous float32 planes
- *     [3][H][W]: (C11, C12, C22) for BSF_COV_C.
+ *     [3][H][W]: (C11, C12, C22) for BSF_COV_C, (log sigma, theta, log rho)
+ *     for BSF_COV_LOGSIG_THETA_LOGRHO.
  *   - The context owns its workspace (running sums S, step field, scan
  *     carries, status word) and allocates it in bsf_create / bsf_plan only.
  *   - Every call is asynchronous on the context's stream unless stated;
@@ -83,10 +84,21 @@ extern "C" {
 
 /* covariance field encodings */
 #define BSF_COV_C   0       /* (C11, C12, C22) in px^2 */
+#define BSF_COV_LOGSIG_THETA_LOGRHO 1
+                            /* (log sigma, theta, log rho): C has trace 2 sigma^2,
+                               eigenvalue ratio rho (>= 1 for log rho >= 0) and its
+                               major axis at angle theta from +x; built per pixel in
+                               float64 (exp, sin, cos of the plane values, fixed
+                               operation order) and rounded once to float32:
+                               k = 2 e^(2 ls) / (1 + rho),
+                               C11 = k (rho cos^2 + sin^2), C22 = k (rho sin^2 + cos^2),
+                               C12 = k (rho - 1) sin cos */
 
 /* step rules */
 #define BSF_STEP_D1        0  /* L = admissible integer nearest sqrt(1 + a^2/|d|^2) */
 #define BSF_STEP_D1_PAPER  1  /* L = admissible integer nearest a/|d| (paper's step scaling) */
+#define BSF_STEP_D2        2  /* continuous steps with interpolated taps (n = 1, 2; fixed
+                                 point only): see bsf_filter_jacobian */
 
 /* phases timed by bsf_set_profiling / bsf_read_profile */
 #define BSF_PHASE_STEPS    0  /* per-pixel step solve */
@@ -167,7 +179,8 @@ int bsf_set_precision(bsf_t h, int mode, int frac_bits);
 /* Declare max |f| of the images to come (used by automatic q; no sync). */
 int bsf_set_value_bound(bsf_t h, double max_abs);
 
-/* BSF_STEP_D1 (default) or BSF_STEP_D1_PAPER. */
+/* BSF_STEP_D1 (default), BSF_STEP_D1_PAPER or BSF_STEP_D2 (n <= 2 only).
+ * Errors: BSF_EINVAL. */
 int bsf_set_step_rule(bsf_t h, int rule);
 
 /* Set an execution option (BSF_OPT_*); it affects how, not what, the filter
@@ -231,9 +244,56 @@ int bsf_filter_rows(bsf_t h, const void* img, int dtype, long long ld, const flo
  *         almost everywhere and is written as zeros.
  * Requires a known R (plan or max_reach) and BSF_FIX64.  The first call
  * allocates the backward workspace (synchronous).
+ * With step rule BSF_STEP_D2 only the covariance gradient is available
+ * (gimg must be NULL, gcov non-NULL): gcov = gout * d out / d plane, from
+ * the held running sums of the forward's image (see bsf_filter_jacobian).
  * Errors: BSF_EINVAL, BSF_ESTATE, BSF_ENOMEM, BSF_ECUDA. */
 int bsf_filter_backward(bsf_t h, const float* gout, long long ldg, const float* cov, int cov_kind,
                         float* gimg, long long ldgi, float* gcov);
+
+/* Continuous-step filter (step rule BSF_STEP_D2) and its Jacobian with
+ * respect to the covariance field.
+ *
+ * The paper samples the running sums at off-grid taps by interpolation
+ * (Section 2.3, eq. "interpolation").  Here each direction's step
+ * lambda_k = sqrt(1 + a_k^2/|d_k|^2) is kept continuous, quantised to 2^-9 of
+ * a grid step (Hq = RNE(512 lambda), lambda~ = Hq/512), and every tap
+ * q_t = c - t lambda~ (c = n (lambda~ - 1)/2, t = 0..n) along d_k is the
+ * linear interpolation of the running sum between its two neighbouring grid
+ * points, with integer weights (multiples of 2^-10).  Per direction the 1-D
+ * kernel is then exactly the triangle max(0, lambda~ - |j|) sampled at the
+ * integers (n = 2) or the overlap of the unit cell at j with the box of
+ * width lambda~ (n = 1), and the output is normalised by the exact mass
+ * prod_k M_k of the four kernels (integers, times 2^40):
+ *    out = RN(RN(acc) 2^-q) / RN(prod_k M_k)   (as in the header comment).
+ * For lambda~ an admissible integer it equals BSF_STEP_D1.  The samples are
+ * 5^4 = 625 per pixel for n = 2 (4^4 = 256 for n = 1).  The running sums
+ * carry 40 more bits than with D1; BSF_FIX128 is the usual choice.
+ *
+ * jac (NULL, or device float32 [3][H][ldj]) receives d out(p) / d plane_c(p)
+ * for the three planes of cov_kind (covariance entries or log sigma, theta,
+ * log rho): the derivative of the interpolation weights at fixed brackets
+ * (the right derivative in lambda), through the quantisation as the
+ * identity, the scale solve (implicit derivative of its stationarity cubic)
+ * and the covariance encoding.  Computed from exact integer derivative sums
+ * (float64 combination, float32 chain).  Pixels out of reach (identity
+ * steps) get zero.  Whole image only; requires BSF_STEP_D2, n <= 2 and a
+ * fixed-point precision; automatic q keeps two more guard bits for the
+ * derivative sums.  img / dtype / ld / cov / out / ldo as in bsf_filter;
+ * out_dtype must be BSF_F32 here.  Errors: BSF_EINVAL, BSF_ESTATE, BSF_ECUDA. */
+int bsf_filter_jacobian(bsf_t h, const void* img, int dtype, long long ld, const float* cov,
+                        int cov_kind, void* out, int out_dtype, long long ldo, float* jac,
+                        long long ldj);
+
+/* Vector-Jacobian product of the continuous-step filter: gcov[c][p] =
+ * gout[p] * jac[c][p] for the Jacobian planes of bsf_filter_jacobian.
+ * gout device [H][ldg], jac device [3][H][ldj], gcov device [3][H][W]
+ * (float32).  With step rule BSF_STEP_D2, bsf_filter_backward(gimg = NULL,
+ * gcov) computes the same product without a stored Jacobian, from the
+ * running sums of the last pre-integration (which must be the forward's).
+ * Errors: BSF_EINVAL. */
+int bsf_jacobian_vjp(bsf_t h, const float* gout, long long ldg, const float* jac, long long ldj,
+                     float* gcov);
 
 /* Synchronise the stream and return the first device-side error recorded
  * since the last call (BSF_ERANGE, BSF_EOVERFLOW, BSF_ECOV) or BSF_OK, then

@@ -204,11 +204,12 @@ def line_data(Hh: int, n: int):
 # 2-D kernels and the direct filter
 # ---------------------------------------------------------------------------
 
-def assemble(lines):
-    """Convolution of four 1-D kernels [(g, j0)] placed on Z d_k.
+def assemble(lines, dtype=object):
+    """Convolution of four 1-D kernels [(g, j0)] placed on Z d_k (exact
+    integers with dtype=object, float64 with dtype=np.float64).
 
     Returns (K, ox, oy): K[oy + dy, ox + dx] is the weight at offset (dx, dy)."""
-    K = np.ones((1, 1), dtype=object)
+    K = np.ones((1, 1), dtype=dtype)
     ox = oy = 0
     for k, (dx, dy) in enumerate(params.DIRS):
         g, j0 = lines[k]
@@ -216,7 +217,7 @@ def assemble(lines):
         sx, sy = offs * dx, offs * dy
         nx0, nx1 = -ox + sx.min(), K.shape[1] - 1 - ox + sx.max()
         ny0, ny1 = -oy + sy.min(), K.shape[0] - 1 - oy + sy.max()
-        Kn = np.zeros((ny1 - ny0 + 1, nx1 - nx0 + 1), dtype=object)
+        Kn = np.zeros((ny1 - ny0 + 1, nx1 - nx0 + 1), dtype=dtype)
         nox, noy = -nx0, -ny0
         for w, ddx, ddy in zip(g, sx, sy):
             if w == 0:
@@ -488,8 +489,7 @@ def filter_d2_f64_at(f: np.ndarray, p, kind: int, n: int, boundary: int, y: int,
     """Continuous-step filter at one pixel with real (unquantised) steps from
     the float64 solve, in float64."""
     lams = [float(np.real(v)) for v in steps_f64([float(v) for v in p], kind, n)]
-    K, ox, oy = assemble([line_kernel_real(l, n) for l in lams])
-    K = K.astype(np.float64)
+    K, ox, oy = assemble([line_kernel_real(l, n) for l in lams], dtype=np.float64)
     Hh, Ww = f.shape
     kh, kw = K.shape
     yi, yv = extend_index(np.arange(y - oy, y - oy + kh), Hh, boundary)

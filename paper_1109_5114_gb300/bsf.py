@@ -79,6 +79,9 @@ bsf_filter_rows = _fn("bsf_filter_rows", c_int, bsf_t, c_void_p, c_int, c_ll, c_
 bsf_filter_backward = _fn("bsf_filter_backward", c_int, bsf_t, c_void_p, c_ll, c_void_p, c_int,
                           c_void_p, c_ll, c_void_p)
 bsf_read_profile = _fn("bsf_read_profile", c_int, bsf_t, ctypes.POINTER(c_double), ctypes.POINTER(c_int))
+bsf_filter_jacobian = _fn("bsf_filter_jacobian", c_int, bsf_t, c_void_p, c_int, c_ll, c_void_p, c_int,
+                          c_void_p, c_int, c_ll, c_void_p, c_ll)
+bsf_jacobian_vjp = _fn("bsf_jacobian_vjp", c_int, bsf_t, c_void_p, c_ll, c_void_p, c_ll, c_void_p)
 
 class bsf_image_desc(ctypes.Structure):
     _fields_ = [("H", c_int), ("W", c_int), ("img", c_void_p), ("dtype", c_int), ("ld", c_ll),
@@ -151,14 +154,19 @@ class BoxSplineFilter:
     filter(img, cov, out_dtype) runs the whole forward pass on torch's current
     stream: step solve, extension + quantisation + running sums, finite
     differences.  img: [H][W] uint8/float32/float64 CUDA tensor; cov: [3][H][W]
-    float32 CUDA tensor (C11, C12, C22).
+    float32 CUDA tensor of cov_kind (0: C11, C12, C22; 1: log sigma, theta,
+    log rho).  step_rule 2 (BSF_STEP_D2) selects the continuous-step filter,
+    whose derivative with respect to cov comes from filter_jacobian.
     """
 
     def __init__(self, H: int, W: int, n: int, boundary="symmetric", max_reach: int = -1,
-                 precision: int = 1, frac_bits: int = -1, value_bound=None, step_rule: int = 0):
+                 precision: int = 1, frac_bits: int = -1, value_bound=None, step_rule: int = 0,
+                 cov_kind: int = 0):
         if isinstance(boundary, str):
             boundary = _BOUNDARY[boundary]
         self.H, self.W, self.n = H, W, n
+        self.cov_kind = cov_kind
+        self.step_rule = step_rule
         h = bsf_t()
         rc = bsf_create(ctypes.byref(h), H, W, 4, n, boundary, max_reach)
         if rc != 0:
@@ -191,7 +199,7 @@ class BoxSplineFilter:
     def plan(self, cov):
         self._stream()
         assert cov.is_cuda and cov.dtype.is_floating_point and cov.is_contiguous()
-        check(self._h, bsf_plan(self._h, ctypes.c_void_p(cov.data_ptr()), 0))
+        check(self._h, bsf_plan(self._h, ctypes.c_void_p(cov.data_ptr()), self.cov_kind))
         return self.info()
 
     def filter(self, img, cov, out=None, out_dtype=None):
@@ -204,14 +212,47 @@ class BoxSplineFilter:
             out = torch.empty((H, W), dtype=out_dtype or torch.float32, device=cov.device)
         oc = BSF_F32 if out.dtype == torch.float32 else BSF_F64  # noqa: F821
         if img is None:
-            rc = bsf_filter(self._h, None, 0, W, ctypes.c_void_p(cov.data_ptr()), 0,
+            rc = bsf_filter(self._h, None, 0, W, ctypes.c_void_p(cov.data_ptr()), self.cov_kind,
                             ctypes.c_void_p(out.data_ptr()), oc, out.stride(0))
         else:
             rc = bsf_filter(self._h, ctypes.c_void_p(img.data_ptr()), _dtype_code(img), img.stride(0),
-                            ctypes.c_void_p(cov.data_ptr()), 0, ctypes.c_void_p(out.data_ptr()), oc,
-                            out.stride(0))
+                            ctypes.c_void_p(cov.data_ptr()), self.cov_kind,
+                            ctypes.c_void_p(out.data_ptr()), oc, out.stride(0))
         check(self._h, rc)
         return out
+
+    def filter_jacobian(self, img, cov, out=None, jac=None):
+        """Continuous-step forward and d out / d cov-plane: (out float32 [H][W], jac [3][H][W])."""
+        import torch
+        self._stream()
+        H, W = self.H, self.W
+        assert img.is_cuda and img.shape == (H, W) and img.stride(1) == 1
+        assert cov.is_cuda and cov.dtype == torch.float32 and cov.shape == (3, H, W) and cov.is_contiguous()
+        if out is None:
+            out = torch.empty((H, W), dtype=torch.float32, device=cov.device)
+        if jac is None:
+            jac = torch.empty((3, H, W), dtype=torch.float32, device=cov.device)
+        assert jac.is_contiguous() and out.dtype == torch.float32
+        rc = bsf_filter_jacobian(self._h, ctypes.c_void_p(img.data_ptr()), _dtype_code(img),
+                                 img.stride(0), ctypes.c_void_p(cov.data_ptr()), self.cov_kind,
+                                 ctypes.c_void_p(out.data_ptr()), BSF_F32, out.stride(0),  # noqa: F821
+                                 ctypes.c_void_p(jac.data_ptr()), W)
+        check(self._h, rc)
+        return out, jac
+
+    def jacobian_vjp(self, gout, jac, gcov=None):
+        """gcov[c] = gout * jac[c] (library kernel)."""
+        import torch
+        self._stream()
+        H, W = self.H, self.W
+        assert gout.is_cuda and gout.dtype == torch.float32 and gout.shape == (H, W) and gout.stride(1) == 1
+        assert jac.is_contiguous() and jac.shape == (3, H, W)
+        if gcov is None:
+            gcov = torch.empty((3, H, W), dtype=torch.float32, device=gout.device)
+        check(self._h, bsf_jacobian_vjp(self._h, ctypes.c_void_p(gout.data_ptr()), gout.stride(0),
+                                        ctypes.c_void_p(jac.data_ptr()), W,
+                                        ctypes.c_void_p(gcov.data_ptr())))
+        return gcov
 
     def filter_rows(self, img, cov, y0: int, y1: int, out=None):
         """Rows [y0, y1) of the filtered image (float32), from the band's own running sums."""
@@ -220,23 +261,27 @@ class BoxSplineFilter:
         if out is None:
             out = torch.empty((y1 - y0, self.W), dtype=torch.float32, device=cov.device)
         rc = bsf_filter_rows(self._h, ctypes.c_void_p(img.data_ptr()), _dtype_code(img), img.stride(0),
-                             ctypes.c_void_p(cov.data_ptr()), 0, ctypes.c_void_p(out.data_ptr()),
+                             ctypes.c_void_p(cov.data_ptr()), self.cov_kind, ctypes.c_void_p(out.data_ptr()),
                              BSF_F32 if out.dtype == torch.float32 else BSF_F64, out.stride(0), y0, y1)  # noqa: F821
         check(self._h, rc)
         return out
 
-    def backward(self, gout, cov, gimg=None, want_gcov=False):
-        """Image gradient (and zero covariance gradient) of the last filter."""
+    def backward(self, gout, cov, gimg=None, want_gcov=False, want_gimg=True):
+        """Gradients of the last filter: image gradient (D1; the covariance
+        gradient of D1 is zero) or, for continuous steps, the covariance
+        gradient only (recomputed from the held running sums)."""
         import torch
         self._stream()
         H, W = self.H, self.W
         assert gout.is_cuda and gout.dtype == torch.float32 and gout.shape == (H, W) and gout.stride(1) == 1
-        if gimg is None:
+        if want_gimg and gimg is None:
             gimg = torch.empty((H, W), dtype=torch.float32, device=gout.device)
         gcov = torch.empty((3, H, W), dtype=torch.float32, device=gout.device) if want_gcov else None
         rc = bsf_filter_backward(self._h, ctypes.c_void_p(gout.data_ptr()), gout.stride(0),
-                                 ctypes.c_void_p(cov.data_ptr()), 0, ctypes.c_void_p(gimg.data_ptr()),
-                                 gimg.stride(0), ctypes.c_void_p(gcov.data_ptr()) if want_gcov else None)
+                                 ctypes.c_void_p(cov.data_ptr()), self.cov_kind,
+                                 ctypes.c_void_p(gimg.data_ptr()) if want_gimg else None,
+                                 gimg.stride(0) if want_gimg else W,
+                                 ctypes.c_void_p(gcov.data_ptr()) if want_gcov else None)
         check(self._h, rc)
         return gimg, gcov
 
@@ -291,18 +336,37 @@ def _make_autograd():
     import torch
 
     class BoxSplineFilterFunction(torch.autograd.Function):
-        """out = filter(img, cov); backward gives d/dimg through the library's
-        adjoint kernels (the D1 steps are piecewise constant, so d/dcov = 0)."""
+        """out = filter(img, cov).  Integer steps (D1): backward gives d/dimg
+        through the library's adjoint kernels (the steps are piecewise
+        constant, so d/dcov = 0).  Continuous steps (D2): the forward also
+        writes d out / d cov-plane when cov requires grad, and the backward
+        multiplies it by the incoming gradient (library kernel); the image
+        gradient of D2 is not available."""
 
         @staticmethod
         def forward(ctx, img, cov, filt):
-            out = filt.filter(img.contiguous(), cov.contiguous())
             ctx.filt = filt
+            ctx.d2 = filt.step_rule == BSF_STEP_D2  # noqa: F821
+            if ctx.d2:
+                if img.requires_grad:
+                    raise NotImplementedError("continuous steps: no image gradient")
+                if cov.requires_grad:
+                    out, jac = filt.filter_jacobian(img.contiguous(), cov.contiguous())
+                    ctx.save_for_backward(jac)
+                    return out
+                ctx.save_for_backward()
+                return filt.filter(img.contiguous(), cov.contiguous())
+            out = filt.filter(img.contiguous(), cov.contiguous())
             ctx.save_for_backward(cov)
             return out
 
         @staticmethod
         def backward(ctx, gout):
+            if ctx.d2:
+                if not ctx.needs_input_grad[1]:
+                    return None, None, None
+                (jac,) = ctx.saved_tensors
+                return None, ctx.filt.jacobian_vjp(gout.contiguous().float(), jac), None
             (cov,) = ctx.saved_tensors
             gimg, gcov = ctx.filt.backward(gout.contiguous().float(), cov,
                                            want_gcov=ctx.needs_input_grad[1])

@@ -22,12 +22,16 @@ LIB = os.path.join(LIBDIR, "libbsf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                  "-I", INCLUDE, "-I", CSRC]
-# The step solve is reproduced bit for bit by IEEE float32 code elsewhere: no
-# contraction of multiplies and adds into fused multiply-adds in that unit.
-EXTRA = {"bsf_steps.cu": ["-fmad=false"]}
+# The step solve (and the float64 covariance of log parameters) must give the
+# same bits in every unit that runs it: no contraction of multiplies and adds
+# into fused multiply-adds there.
+_NOFMA = ["-fmad=false"]
+EXTRA = {"bsf_steps.cu": _NOFMA, "bsf_continuous.cu": _NOFMA, "bsf_continuous64.cu": _NOFMA,
+         "bsf_continuous128.cu": _NOFMA, "bsf_stencil.cu": _NOFMA, "bsf_backward.cu": _NOFMA}
 
 SOURCES = ["bsf_api.cu", "bsf_steps.cu", "bsf_scan.cu", "bsf_stencil.cu", "bsf_backward.cu",
-           "bsf_batch.cu", "bsf_noalloc.cu"]
+           "bsf_batch.cu", "bsf_noalloc.cu", "bsf_continuous.cu", "bsf_continuous64.cu",
+           "bsf_continuous128.cu"]
 
 
 def nvcc() -> str:

@@ -48,6 +48,7 @@ struct bsf_ctx {
   double plan_mass = 1.0;    // largest prod L^n of the plan
   int plan_reach = -1;       // largest tap reach of the plan
   const float* last_cov = nullptr;  // covariance of the last filter call (bsf_copy_steps)
+  int last_kind = BSF_COV_C;
   bool steps_current = false;       // Lf holds the steps of last_cov
   bool have_S = false;       // S holds a pre-integration made with (R, elem, q)
   int S_R = -1, S_elem = 0, S_q = -1;
@@ -187,7 +188,21 @@ struct PhaseTimer {
 };
 
 int check_cov_kind(bsf_t h, int cov_kind) {
-  if (cov_kind != BSF_COV_C) return fail(h, BSF_EINVAL, "unsupported cov_kind %d", cov_kind);
+  if (cov_kind != BSF_COV_C && cov_kind != BSF_COV_LOGSIG_THETA_LOGRHO)
+    return fail(h, BSF_EINVAL, "unsupported cov_kind %d", cov_kind);
+  return BSF_OK;
+}
+
+// Smallest padding of the continuous-step taps (identity steps): samples at
+// -3..1 (n = 2) or -2..1 (n = 1) along every direction.
+int d2_min_reach(int n) { return n == 2 ? 9 : 6; }
+
+int check_d2(bsf_t h) {
+  if (h->n > 2) return fail(h, BSF_EINVAL, "continuous steps need n <= 2");
+  if (!is_fixed(h->precision)) return fail(h, BSF_EINVAL, "continuous steps need fixed point");
+  if (h->R >= 0 && h->R < d2_min_reach(h->n))
+    return fail(h, BSF_EINVAL, "padding R = %d below %d, the reach of continuous identity steps",
+                h->R, d2_min_reach(h->n));
   return BSF_OK;
 }
 
@@ -208,6 +223,7 @@ int run_steps(bsf_t h, const float* cov, int cov_kind, bool sync_plan) {
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "steps kernel");
   h->last_cov = cov;
+  h->last_kind = cov_kind;
   h->steps_current = true;
   if (sync_plan) {
     if ((rc = read_status(h))) return rc;
@@ -216,6 +232,7 @@ int run_steps(bsf_t h, const float* cov, int cov_kind, bool sync_plan) {
     if (!h->R_fixed) {
       // the solve ran unbounded: every tap of this field fits this R
       h->R = h->host_st.max_reach > 3 * h->n ? h->host_st.max_reach : 3 * h->n;
+      if (h->step_rule == BSF_STEP_D2 && h->R < d2_min_reach(h->n)) h->R = d2_min_reach(h->n);
     }
     h->planned = true;
     if ((rc = ensure_workspace(h))) return rc;
@@ -255,6 +272,7 @@ int resolve_q(bsf_t h, const void* img, int dtype, long long ld) {
   const double lv = std::log2(vmax > 1e-300 ? vmax : 1e-300);
   const double lm = std::log2(mass);
   int q = (int)std::floor((b - 2) - lv - lm) - 1;
+  if (h->step_rule == BSF_STEP_D2) q -= 2;  // derivative sums reach 3 max|Q| mass
   if (q > b - 28) q = b - 28;
   if (q < 0) q = 0;
   h->q = q;
@@ -379,7 +397,10 @@ int bsf_set_value_bound(bsf_t h, double max_abs) {
 
 int bsf_set_step_rule(bsf_t h, int rule) {
   if (!h) return BSF_EINVAL;
-  if (rule != BSF_STEP_D1 && rule != BSF_STEP_D1_PAPER) return fail(h, BSF_EINVAL, "bad step rule %d", rule);
+  if (rule != BSF_STEP_D1 && rule != BSF_STEP_D1_PAPER && rule != BSF_STEP_D2)
+    return fail(h, BSF_EINVAL, "bad step rule %d", rule);
+  if (rule == BSF_STEP_D2 && h->n > 2) return fail(h, BSF_EINVAL, "continuous steps need n <= 2");
+  if (rule != h->step_rule) h->planned = false;  // the mass bound differs between rules
   h->step_rule = rule;
   return BSF_OK;
 }
@@ -422,9 +443,14 @@ int bsf_preintegrate(bsf_t h, const void* img, int dtype, long long ld) {
 }
 
 static int filter_impl(bsf_t h, const void* img, int dtype, long long ld, const float* cov,
-                       int cov_kind, void* out, int out_dtype, long long ldo, int row0, int rows) {
+                       int cov_kind, void* out, int out_dtype, long long ldo, int row0, int rows,
+                       float* jac = nullptr, long long ldj = 0) {
   if (!h) return BSF_EINVAL;
   if (!out) return fail(h, BSF_EINVAL, "out is NULL");
+  if (h->step_rule == BSF_STEP_D2) {
+    const int rc = check_d2(h);
+    if (rc) return rc;
+  }
   if (out_dtype != BSF_F32 && out_dtype != BSF_F64) return fail(h, BSF_EINVAL, "bad out dtype %d", out_dtype);
   if (ldo < h->W) return fail(h, BSF_EINVAL, "ldo %lld < W %d", ldo, h->W);
   if (row0 < 0 || rows <= 0 || row0 + rows > h->H) return fail(h, BSF_EINVAL, "bad row band");
@@ -447,12 +473,19 @@ static int filter_impl(bsf_t h, const void* img, int dtype, long long ld, const 
   cudaError_t e;
   {
     PhaseTimer t(h, BSF_PHASE_STENCIL);
-    e = bsf_launch_stencil_d1(h->precision, h->n, h->S, h->pitch, h->R, cov, h->step_rule, h->H,
-                              h->W, row0, rows, h->S_q, out, out_dtype, ldo, h->st, h->stream);
+    if (h->step_rule == BSF_STEP_D2)
+      e = bsf_launch_stencil_d2(h->precision, h->n, jac ? 1 : 0, h->S, h->pitch, h->R, cov, cov_kind,
+                                h->H, h->W, row0, rows, h->S_q, out, out_dtype, ldo, jac, ldj,
+                                (long long)rows * ldj, nullptr, 0, h->st, h->stream);
+    else
+      e = bsf_launch_stencil_d1(h->precision, h->n, h->S, h->pitch, h->R, cov, cov_kind,
+                                h->step_rule, h->H, h->W, row0, rows, h->S_q, out, out_dtype, ldo,
+                                h->st, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "stencil");
-  if (h->last_cov != cov) h->steps_current = false;
+  if (h->last_cov != cov || h->last_kind != cov_kind) h->steps_current = false;
   h->last_cov = cov;
+  h->last_kind = cov_kind;
   return BSF_OK;
 }
 
@@ -469,11 +502,55 @@ int bsf_filter_rows(bsf_t h, const void* img, int dtype, long long ld, const flo
   return filter_impl(h, img, dtype, ld, cov, cov_kind, out, out_dtype, ldo, y0, y1 - y0);
 }
 
+int bsf_filter_jacobian(bsf_t h, const void* img, int dtype, long long ld, const float* cov,
+                        int cov_kind, void* out, int out_dtype, long long ldo, float* jac,
+                        long long ldj) {
+  if (!h) return BSF_EINVAL;
+  if (h->step_rule != BSF_STEP_D2) return fail(h, BSF_EINVAL, "the Jacobian needs BSF_STEP_D2");
+  if (!jac) return fail(h, BSF_EINVAL, "jac is NULL");
+  if (ldj < h->W) return fail(h, BSF_EINVAL, "ldj %lld < W %d", ldj, h->W);
+  if (out_dtype != BSF_F32) return fail(h, BSF_EINVAL, "the Jacobian comes with float32 output");
+  return filter_impl(h, img, dtype, ld, cov, cov_kind, out, out_dtype, ldo, 0, h->H, jac, ldj);
+}
+
+int bsf_jacobian_vjp(bsf_t h, const float* gout, long long ldg, const float* jac, long long ldj,
+                     float* gcov) {
+  if (!h) return BSF_EINVAL;
+  if (!gout || !jac || !gcov) return fail(h, BSF_EINVAL, "NULL gout, jac or gcov");
+  if (ldg < h->W || ldj < h->W) return fail(h, BSF_EINVAL, "leading dimension < W");
+  PhaseTimer t(h, BSF_PHASE_BWD_SCATTER);
+  cudaError_t e = bsf_launch_jacobian_vjp(gout, ldg, jac, ldj, gcov, h->H, h->W, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "jacobian vjp");
+  return BSF_OK;
+}
+
+static int backward_d2(bsf_t h, const float* gout, long long ldg, const float* cov, int cov_kind,
+                       float* gcov) {
+  int rc = check_d2(h);
+  if (rc) return rc;
+  if (!gcov) return fail(h, BSF_EINVAL, "continuous steps: gcov is NULL");
+  if (!h->have_S || h->S_R != h->R || h->S_elem != h->elem || h->S_row0 != 0 || h->S_rows != h->H)
+    return fail(h, BSF_ESTATE, "no whole-image pre-integration is held");
+  if ((rc = reset_counters(h, true, false))) return rc;
+  PhaseTimer t(h, BSF_PHASE_BWD_SCATTER);
+  cudaError_t e = bsf_launch_stencil_d2(h->precision, h->n, 2, h->S, h->pitch, h->R, cov, cov_kind,
+                                        h->H, h->W, 0, h->H, h->S_q, nullptr, BSF_F32, h->W, gcov,
+                                        h->W, (long long)h->H * h->W, gout, ldg, h->st, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "continuous-step vjp");
+  return BSF_OK;
+}
+
 int bsf_filter_backward(bsf_t h, const float* gout, long long ldg, const float* cov, int cov_kind,
                         float* gimg, long long ldgi, float* gcov) {
   if (!h) return BSF_EINVAL;
   int rc = check_cov_kind(h, cov_kind);
   if (rc) return rc;
+  if (h->step_rule == BSF_STEP_D2) {
+    if (gimg) return fail(h, BSF_EINVAL, "continuous steps: the image gradient is not available");
+    if (!gout || !cov) return fail(h, BSF_EINVAL, "NULL gout or cov");
+    if (ldg < h->W) return fail(h, BSF_EINVAL, "leading dimension < W");
+    return backward_d2(h, gout, ldg, cov, cov_kind, gcov);
+  }
   if (!gout || !cov || !gimg) return fail(h, BSF_EINVAL, "NULL gout, cov or gimg");
   if (ldg < h->W || ldgi < h->W) return fail(h, BSF_EINVAL, "leading dimension < W");
   if (h->precision != BSF_FIX64) return fail(h, BSF_EINVAL, "backward needs BSF_FIX64");
@@ -499,7 +576,7 @@ int bsf_filter_backward(bsf_t h, const float* gout, long long ldg, const float* 
     BSF_CUDA(h, cudaMemsetAsync(h->G, 0, G_bytes, h->stream));
     e = bsf_launch_gabsmax(gout, ldg, h->H, h->W, h->st, h->stream);
     if (e == cudaSuccess)
-      e = bsf_launch_scatter_d1(h->n, h->G, h->pitch, h->R, cov, h->step_rule, gout, ldg, h->H,
+      e = bsf_launch_scatter_d1(h->n, h->G, h->pitch, h->R, cov, cov_kind, h->step_rule, gout, ldg, h->H,
                                 h->W, h->st, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "backward scatter");
@@ -573,7 +650,7 @@ int bsf_copy_steps(bsf_t h, uint16_t* dst) {
   if (!h->steps_current) {  // solve the last field again (it must still be valid)
     const bool planned = h->planned;
     h->planned = true;  // bounded by the current R, no plan
-    int rc = run_steps(h, h->last_cov, BSF_COV_C, false);
+    int rc = run_steps(h, h->last_cov, h->last_kind, false);
     h->planned = planned;
     if (rc) return rc;
   }

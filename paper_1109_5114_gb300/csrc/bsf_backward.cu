@@ -63,14 +63,16 @@ __device__ __forceinline__ void scatter(unsigned long long* p, const long long* 
 template <int NF>
 __global__ void __launch_bounds__(256)
 k_scatter_d1(unsigned long long* __restrict__ G, long long pitch, int R,
-             const float* __restrict__ cov, int rule, const float* __restrict__ gout,
+             const float* __restrict__ cov, int kind, int rule, const float* __restrict__ gout,
              long long ldg, int H, int W, DevStatus* st) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= W || y >= H) return;
   const long long HW = (long long)H * W, i = (long long)y * W + x;
   int L[4], flags, reach;
-  bsf_solve::pixel_steps(cov[i], cov[HW + i], cov[2 * HW + i], NF, rule, R, L, flags, reach);
+  float C11, C12, C22;
+  bsf_solve::load_cov(cov, kind, HW, i, C11, C12, C22);
+  bsf_solve::pixel_steps(C11, C12, C22, NF, rule, R, L, flags, reach);
   const int qg = grad_q(st->max_absg_bits);
   unsigned long long D = (unsigned long long)(L[0] * L[1]) * (unsigned long long)(L[2] * L[3]);
   const unsigned long long D1 = D;
@@ -151,13 +153,14 @@ cudaError_t bsf_launch_gabsmax(const float* gout, long long ldg, int H, int W, D
 }
 
 cudaError_t bsf_launch_scatter_d1(int n, void* G, long long pitch, int R, const float* cov,
-                                  int rule, const float* gout, long long ldg, int H, int W,
-                                  DevStatus* st, cudaStream_t s) {
+                                  int cov_kind, int rule, const float* gout, long long ldg, int H,
+                                  int W, DevStatus* st, cudaStream_t s) {
   dim3 block(32, 8), grid((W + 31) / 32, (H + 7) / 8);
   auto* g = (unsigned long long*)G;
-  if (n == 1) k_scatter_d1<1><<<grid, block, 0, s>>>(g, pitch, R, cov, rule, gout, ldg, H, W, st);
-  else if (n == 2) k_scatter_d1<2><<<grid, block, 0, s>>>(g, pitch, R, cov, rule, gout, ldg, H, W, st);
-  else if (n == 3) k_scatter_d1<3><<<grid, block, 0, s>>>(g, pitch, R, cov, rule, gout, ldg, H, W, st);
+  const int k = cov_kind;
+  if (n == 1) k_scatter_d1<1><<<grid, block, 0, s>>>(g, pitch, R, cov, k, rule, gout, ldg, H, W, st);
+  else if (n == 2) k_scatter_d1<2><<<grid, block, 0, s>>>(g, pitch, R, cov, k, rule, gout, ldg, H, W, st);
+  else if (n == 3) k_scatter_d1<3><<<grid, block, 0, s>>>(g, pitch, R, cov, k, rule, gout, ldg, H, W, st);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

@@ -143,7 +143,7 @@ int run_one(bsf_batch_t b, const BatchImage& im) {
     e = bsf_launch_vscan(BSF_FIX64, b->n, skews[k], false, im.S, im.pitch, im.Hp, im.Wp, im.ch,
                          im.agg, nullptr, b->stream);
   if (e == cudaSuccess)
-    e = bsf_launch_stencil_d1(BSF_FIX64, b->n, im.S, im.pitch, im.R, im.cov, b->step_rule, im.H,
+    e = bsf_launch_stencil_d1(BSF_FIX64, b->n, im.S, im.pitch, im.R, im.cov, BSF_COV_C, b->step_rule, im.H,
                               im.W, 0, im.H, b->q, im.out, b->out_dtype, im.ldo, b->st, b->stream);
   if (e != cudaSuccess) return bfail(b, BSF_ECUDA, "per-image launch: %s", cudaGetErrorString(e));
   return BSF_OK;

@@ -66,7 +66,7 @@ cudaError_t bsf_launch_suffix_rows(int elem_bytes, int n, void* S, long long pit
 cudaError_t bsf_launch_gabsmax(const float* gout, long long ldg, int H, int W, DevStatus* st,
                                cudaStream_t s);
 cudaError_t bsf_launch_scatter_d1(int n, void* G, long long pitch, int R, const float* cov,
-                                  int rule, const float* gout, long long ldg, int H, int W,
+                                  int cov_kind, int rule, const float* gout, long long ldg, int H, int W,
                                   DevStatus* st, cudaStream_t s);
 cudaError_t bsf_launch_fold(const void* G, long long pitch, int Hp, int H, int W, int R,
                             int boundary, void* Gx, float* gimg, long long ldo, const DevStatus* st,
@@ -101,6 +101,19 @@ cudaError_t bsf_launch_batch_stencil(int n, int out_dtype, const BatchImage* img
 // Finite differences with the per-pixel step solve fused in (cov: [3][H][W]).
 // Output rows row0 .. row0 + rows - 1 of an H x W image (S holds that band).
 cudaError_t bsf_launch_stencil_d1(int prec, int n, const void* S, long long pitch, int R,
-                                  const float* cov, int rule, int H, int W, int row0, int rows,
-                                  int q, void* out, int out_dtype, long long ldo, DevStatus* st,
-                                  cudaStream_t s);
+                                  const float* cov, int cov_kind, int rule, int H, int W, int row0,
+                                  int rows, int q, void* out, int out_dtype, long long ldo,
+                                  DevStatus* st, cudaStream_t s);
+
+// Continuous-step stencil (BSF_STEP_D2, n = 1, 2; BSF_FIX64 / BSF_FIX128).
+// mode 0: out only; 1: out and the Jacobian planes jac[c * jac_plane + y * ldj + x]
+// (d out / d plane c of cov_kind); 2: gout(p) times the Jacobian into the same
+// layout (no out).  Rows row0 .. row0 + rows - 1; S holds that band.
+cudaError_t bsf_launch_stencil_d2(int prec, int n, int mode, const void* S, long long pitch, int R,
+                                  const float* cov, int cov_kind, int H, int W, int row0, int rows,
+                                  int q, void* out, int out_dtype, long long ldo, float* jac,
+                                  long long ldj, long long jac_plane, const float* gout,
+                                  long long ldg, DevStatus* st, cudaStream_t s);
+// gcov[c][y][x] = gout[y][x] * jac[c][y][x] (jac planes H * ldj apart; gcov [3][H][W]).
+cudaError_t bsf_launch_jacobian_vjp(const float* gout, long long ldg, const float* jac,
+                                    long long ldj, float* gcov, int H, int W, cudaStream_t s);

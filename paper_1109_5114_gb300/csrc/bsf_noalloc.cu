@@ -97,7 +97,7 @@ extern "C" int bsf_filter_noalloc(const void* img, int dtype, long long ld, int 
     if (bsf_launch_vscan(BSF_FIX64, n, skews[i], false, S, pitch, (int)Hp, (int)Wp, kScanChunk, agg, carry, s) !=
         cudaSuccess)
       return BSF_ECUDA;
-  if (bsf_launch_stencil_d1(BSF_FIX64, n, S, pitch, reach, cov, BSF_STEP_D1, H, W, 0, H, frac_bits, out,
+  if (bsf_launch_stencil_d1(BSF_FIX64, n, S, pitch, reach, cov, BSF_COV_C, BSF_STEP_D1, H, W, 0, H, frac_bits, out,
                             out_dtype, ldo, st, s) != cudaSuccess)
     return BSF_ECUDA;
 

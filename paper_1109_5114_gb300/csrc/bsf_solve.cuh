@@ -112,4 +112,182 @@ __device__ __forceinline__ bool pixel_steps(float C11, float C12, float C22, int
   return true;
 }
 
+// ---------------------------------------------------------------------------
+// Covariance of one pixel from a field of kind BSF_COV_C (planes C11, C12,
+// C22) or BSF_COV_LOGSIG_THETA_LOGRHO (planes log sigma, theta, log rho).  The
+// latter is evaluated in float64 in one fixed order, every operation rounded
+// once (explicit intrinsics, no contraction), then rounded to float32:
+//   s2 = exp(2 ls), rho = exp(lr), k = (2 s2) / (1 + rho),
+//   C11 = k (rho c^2 + s^2), C22 = k (rho s^2 + c^2), C12 = k ((rho - 1) s c).
+// (trace 2 sigma^2, eigenvalue ratio rho, major axis at theta).
+// ---------------------------------------------------------------------------
+struct LogCov {  // float64 intermediates kept for the chain rule
+  double k, rho, c, s, C11, C12, C22;
+};
+
+__device__ __forceinline__ LogCov cov_of_log_params(float ls, float th, float lr) {
+  LogCov r;
+  const double s2 = exp(__dmul_rn(2.0, (double)ls));
+  r.rho = exp((double)lr);
+  r.k = __ddiv_rn(__dmul_rn(2.0, s2), __dadd_rn(1.0, r.rho));
+  sincos((double)th, &r.s, &r.c);
+  const double cc = __dmul_rn(r.c, r.c), ss = __dmul_rn(r.s, r.s), sc = __dmul_rn(r.s, r.c);
+  r.C11 = __dmul_rn(r.k, __dadd_rn(__dmul_rn(r.rho, cc), ss));
+  r.C22 = __dmul_rn(r.k, __dadd_rn(__dmul_rn(r.rho, ss), cc));
+  r.C12 = __dmul_rn(r.k, __dmul_rn(__dsub_rn(r.rho, 1.0), sc));
+  return r;
+}
+
+__device__ __forceinline__ void load_cov(const float* __restrict__ cov, int kind, long long HW,
+                                         long long i, float& C11, float& C12, float& C22) {
+  const float a = cov[i], b = cov[HW + i], c = cov[2 * HW + i];
+  if (kind == BSF_COV_LOGSIG_THETA_LOGRHO) {
+    const LogCov r = cov_of_log_params(a, b, c);
+    C11 = __double2float_rn(r.C11);
+    C12 = __double2float_rn(r.C12);
+    C22 = __double2float_rn(r.C22);
+  } else {
+    C11 = a; C12 = b; C22 = c;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Continuous steps (BSF_STEP_D2).  lambda_k = sqrt(1 + A_k / |d_k|^2) is
+// quantised to 2^-9 of a grid step: Hq_k = RNE(512 lambda_k), so that every
+// interpolation fraction of the taps is a multiple of 2^-10.
+// ---------------------------------------------------------------------------
+constexpr int kHalf = 512;              // 2^(QW-1), QW = 10 fraction bits
+constexpr int kHMax = 512 * 32767;
+
+// Along d_k the samples lie at offsets a0, a0 + 1 (tap t = 0) and their
+// mirror images (t = n), plus -1 for the middle tap of n = 2:
+//   n = 2: a0 = (2 Hq - 1024) >> 10, offsets -a0-3 .. a0+1
+//   n = 1: a0 = (Hq - 512) >> 10,    offsets -a0-2 .. a0+1
+__device__ __forceinline__ int d2_a0(int Hq, int n) {
+  return n == 2 ? (2 * Hq - 1024) >> 10 : (Hq - 512) >> 10;
+}
+__device__ __forceinline__ int d2_reach(const int Hq[4], int n) {
+  int lo[4], hi[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int a0 = d2_a0(Hq[k], n);
+    lo[k] = -a0 - (n == 2 ? 3 : 2);
+    hi[k] = a0 + 1;
+  }
+  const int xr = max(-(lo[0] + lo[1] - hi[3]), hi[0] + hi[1] - lo[3]);
+  const int yr = max(-(lo[1] + lo[2] + lo[3]), hi[1] + hi[2] + hi[3]);
+  return max(xr, yr);
+}
+// Exact mass (times 2^10) of one direction's 1-D kernel and its right
+// derivative with respect to lambda (times 2^10, times 2 for n = 1):
+//   n = 2: sum_j max(0, 2 Hq - 1024 |j|) = 2 Hq (2m + 1) - 1024 m (m + 1),
+//          m = (2 Hq - 1) >> 10;  derivative 1024 (2 floor(lambda~) + 1)
+//   n = 1: 2 Hq (box of width lambda~);  derivative 2 * 1024
+__device__ __forceinline__ unsigned long long d2_mass(int Hq, int n) {
+  if (n == 1) return 2ull * (unsigned)Hq;
+  const unsigned long long m = (unsigned long long)((2 * Hq - 1) >> 10);
+  return 2ull * (unsigned)Hq * (2ull * m + 1ull) - 1024ull * m * (m + 1ull);
+}
+__device__ __forceinline__ unsigned long long d2_dmass(int Hq, int n) {
+  if (n == 1) return 2048ull;
+  return 1024ull * (2ull * (unsigned long long)(Hq >> 9) + 1ull);
+}
+
+// Steps of one pixel for the continuous path; false (identity steps,
+// Hq = 512) when a sample would leave the padding R.
+__device__ __forceinline__ bool pixel_steps_d2(float C11, float C12, float C22, int n, int R,
+                                               int Hq[4], float lam[4], int& flags, int& reach) {
+  const Solved sv = solve_scales(C11, C12, C22, scale_of_order(n));
+  flags = sv.flags;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float a = (k & 1) ? __fmul_rn(sv.A[k], 0.5f) : sv.A[k];
+    lam[k] = __fsqrt_rn(__fadd_rn(1.f, a));
+    Hq[k] = min(__float2int_rn(__fmul_rn(lam[k], (float)kHalf)), kHMax);
+  }
+  reach = d2_reach(Hq, n);
+  if (R >= 0 && reach > R) {
+    Hq[0] = Hq[1] = Hq[2] = Hq[3] = kHalf;
+    reach = d2_reach(Hq, n);
+    return false;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of the scale solve: given gA_k = d out / d A_k, the derivative with
+// respect to (C11, C12, C22).  The forward steps are repeated; the Newton root
+// v of v^3 + p v + q = 0 is differentiated implicitly,
+//   dv = -(v dp + dq) / (3 v^2 + p),
+// with p = (2.5 d^2 + 2 c1 c3 + 8 b^2)/8, q = s (b^2 - d^2/4)/8; where u is
+// clamped, it follows the active bound; the C12 clamp and the floors at zero
+// route the derivative the same way.  float32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void solve_scales_vjp(float C11, float C12, float C22, float B,
+                                                 const float gA[4], float gC[3]) {
+  gC[0] = gC[1] = gC[2] = 0.f;
+  if (!(isfinite(C11) && isfinite(C12) && isfinite(C22))) return;
+  const float c11 = fmaxf(C11, 0.f), c22 = fmaxf(C22, 0.f);
+  const float m = fminf(c11, c22);
+  const bool clamp12 = fabsf(C12) > m;
+  const float c12 = clamp12 ? copysignf(m, C12) : C12;
+  const float c1 = __fmul_rn(B, c11), c3 = __fmul_rn(B, c22), b = __fmul_rn(B, c12);
+  const float s = __fadd_rn(c1, c3), d = __fsub_rn(c1, c3);
+  const float bb = __fmul_rn(b, b), dd = __fmul_rn(d, d);
+  const float p = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(2.5f, dd), __fmul_rn(2.f, __fmul_rn(c1, c3))),
+                                      __fmul_rn(8.f, bb)), 0.125f);
+  const float q = __fmul_rn(__fmul_rn(s, __fsub_rn(bb, __fmul_rn(0.25f, dd))), 0.125f);
+  float v = (p > 0.f) ? __fdiv_rn(-q, p) : 0.f;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const float v2 = __fmul_rn(v, v);
+    const float h = __fadd_rn(__fmul_rn(__fadd_rn(v2, p), v), q);
+    const float dh = __fadd_rn(__fmul_rn(3.f, v2), p);
+    if (dh > 0.f) v = __fsub_rn(v, __fdiv_rn(h, dh));
+  }
+  const float u0 = __fadd_rn(__fmul_rn(0.25f, s), v);
+  const float lo = fabsf(b), hi = fminf(c1, c3);
+  // A1 = c1 - u, A2 = u + b, A3 = c3 - u, A4 = u - b
+  const float gu = gA[1] + gA[3] - gA[0] - gA[2];
+  float gc1 = gA[0], gc3 = gA[2], gb = gA[1] - gA[3];
+  if (u0 < lo) {  // u = |b|
+    gb += b < 0.f ? -gu : gu;
+  } else if (u0 > hi) {
+    if (c1 <= c3) gc1 += gu; else gc3 += gu;
+  } else {
+    const float den = 3.f * v * v + p;
+    if (den > 0.f) {
+      const float gq = -gu / den;
+      const float gp = gq * v;
+      const float w = bb - 0.25f * dd;
+      gc1 += 0.25f * gu + gp * (0.125f * (5.f * d + 2.f * c3)) + gq * (0.125f * (w - 0.5f * s * d));
+      gc3 += 0.25f * gu + gp * (0.125f * (2.f * c1 - 5.f * d)) + gq * (0.125f * (w + 0.5f * s * d));
+      gb += gp * (2.f * b) + gq * (0.25f * s * b);
+    } else {
+      gc1 += 0.25f * gu;
+      gc3 += 0.25f * gu;
+    }
+  }
+  float g11 = B * gc1, g22 = B * gc3, g12 = B * gb;
+  if (clamp12) {  // c12 = sign(C12) min(c11, c22)
+    const float gm = C12 < 0.f ? -g12 : g12;
+    g12 = 0.f;
+    if (c11 <= c22) g11 += gm; else g22 += gm;
+  }
+  gC[0] = C11 > 0.f ? g11 : 0.f;
+  gC[1] = g12;
+  gC[2] = C22 > 0.f ? g22 : 0.f;
+}
+
+// Chain from (C11, C12, C22) to (log sigma, theta, log rho) (float64).
+__device__ __forceinline__ void log_params_vjp(const LogCov& r, const float gC[3], float gP[3]) {
+  const double g11 = gC[0], g12 = gC[1], g22 = gC[2];
+  const double sc = r.s * r.c, cs2 = r.c * r.c - r.s * r.s, kd = r.k * (r.rho - 1.0);
+  const double inv = 1.0 / (1.0 + r.rho);
+  gP[0] = (float)(2.0 * (r.C11 * g11 + r.C12 * g12 + r.C22 * g22));
+  gP[1] = (float)(-2.0 * kd * sc * g11 + kd * cs2 * g12 + 2.0 * kd * sc * g22);
+  gP[2] = (float)(r.rho * ((r.k * r.c * r.c - r.C11 * inv) * g11 + (r.k * sc - r.C12 * inv) * g12 +
+                           (r.k * r.s * r.s - r.C22 * inv) * g22));
+}
+
 }  // namespace bsf_solve

@@ -76,7 +76,7 @@ template <typename T, int NF> struct StencilOcc {
 // overlaps the gathers of other warps and no step field goes through HBM.
 template <typename T, int NF, typename Out>
 __device__ __forceinline__ void stencil_d1_body(const T* __restrict__ S, long long pitch, int R,
-                                                const float* __restrict__ cov, int rule, int H,
+                                                const float* __restrict__ cov, int kind, int rule, int H,
                                                 int W, int row0, int rows, float scale_f,
                                                 double scale_d, Out* __restrict__ out,
                                                 long long ldo, DevStatus* st, int bx, int by) {
@@ -87,8 +87,9 @@ __device__ __forceinline__ void stencil_d1_body(const T* __restrict__ S, long lo
   if (x >= W || y >= rows) return;
   const long long HW = (long long)H * W, i = (long long)(row0 + y) * W + x;
   int L[4], flags, reach;
-  const bool in_reach = bsf_solve::pixel_steps(cov[i], cov[HW + i], cov[2 * HW + i], NF, rule, R,
-                                               L, flags, reach);
+  float C11, C12, C22;
+  bsf_solve::load_cov(cov, kind, HW, i, C11, C12, C22);
+  const bool in_reach = bsf_solve::pixel_steps(C11, C12, C22, NF, rule, R, L, flags, reach);
   {  // rare-event counters, aggregated per warp
     const unsigned act = __activemask();
     const unsigned mc = __ballot_sync(act, flags & 1), mb = __ballot_sync(act, flags & 2),
@@ -152,14 +153,14 @@ __device__ __forceinline__ void stencil_d1_body(const T* __restrict__ S, long lo
 template <typename T, int NF, typename Out>
 __global__ void __launch_bounds__(256, (StencilOcc<T, NF>::value))
 k_stencil_d1(const T* __restrict__ S, long long pitch, int R, const float* __restrict__ cov,
-             int rule, int H, int W, int row0, int rows, float scale_f, double scale_d,
+             int kind, int rule, int H, int W, int row0, int rows, float scale_f, double scale_d,
              Out* __restrict__ out, long long ldo, DevStatus* st) {
-  stencil_d1_body<T, NF, Out>(S, pitch, R, cov, rule, H, W, row0, rows, scale_f, scale_d, out, ldo,
-                              st, blockIdx.x, blockIdx.y);
+  stencil_d1_body<T, NF, Out>(S, pitch, R, cov, kind, rule, H, W, row0, rows, scale_f, scale_d, out,
+                              ldo, st, blockIdx.x, blockIdx.y);
 }
 
 template <typename T, int NF>
-cudaError_t launch_t(const T* S, long long pitch, int R, const float* cov, int rule, int H, int W,
+cudaError_t launch_t(const T* S, long long pitch, int R, const float* cov, int kind, int rule, int H, int W,
                      int row0, int rows, int q, void* out, int out_dtype, long long ldo,
                      DevStatus* st, cudaStream_t s) {
   dim3 block(32, 8);
@@ -167,10 +168,10 @@ cudaError_t launch_t(const T* S, long long pitch, int R, const float* cov, int r
   const float sf = ldexpf(1.f, -q);
   const double sd = ldexp(1.0, -q);
   if (out_dtype == BSF_F32)
-    k_stencil_d1<T, NF, float><<<grid, block, 0, s>>>(S, pitch, R, cov, rule, H, W, row0, rows,
+    k_stencil_d1<T, NF, float><<<grid, block, 0, s>>>(S, pitch, R, cov, kind, rule, H, W, row0, rows,
                                                       sf, sd, (float*)out, ldo, st);
   else if (out_dtype == BSF_F64)
-    k_stencil_d1<T, NF, double><<<grid, block, 0, s>>>(S, pitch, R, cov, rule, H, W, row0, rows,
+    k_stencil_d1<T, NF, double><<<grid, block, 0, s>>>(S, pitch, R, cov, kind, rule, H, W, row0, rows,
                                                        sf, sd, (double*)out, ldo, st);
   else
     return cudaErrorInvalidValue;
@@ -180,11 +181,11 @@ cudaError_t launch_t(const T* S, long long pitch, int R, const float* cov, int r
 }  // namespace
 
 cudaError_t bsf_launch_stencil_d1(int prec, int n, const void* S, long long pitch, int R,
-                                  const float* cov, int rule, int H, int W, int row0, int rows,
+                                  const float* cov, int cov_kind, int rule, int H, int W, int row0, int rows,
                                   int q, void* out, int out_dtype, long long ldo, DevStatus* st,
                                   cudaStream_t s) {
 #define BSF_ST(T, NF)                                                                          \
-  return launch_t<T, NF>((const T*)S, pitch, R, cov, rule, H, W, row0, rows, q, out, out_dtype, \
+  return launch_t<T, NF>((const T*)S, pitch, R, cov, cov_kind, rule, H, W, row0, rows, q, out, out_dtype, \
                          ldo, st, s)
   switch (prec * 10 + n) {
     case 11: BSF_ST(uint64_t, 1);
@@ -224,7 +225,7 @@ k_batch_stencil(const BatchImage* __restrict__ imgs, const int* __restrict__ sta
   const BatchImage& im = imgs[i];
   const int local = blockIdx.x - starts[i];
   const int gx = (im.W + 31) / 32;
-  stencil_d1_body<uint64_t, NF, Out>((const uint64_t*)im.S, im.pitch, im.R, im.cov, rule, im.H,
+  stencil_d1_body<uint64_t, NF, Out>((const uint64_t*)im.S, im.pitch, im.R, im.cov, BSF_COV_C, rule, im.H,
                                      im.W, 0, im.H, scale_f, scale_d, (Out*)im.out, im.ldo, st,
                                      local % gx, local / gx);
 }

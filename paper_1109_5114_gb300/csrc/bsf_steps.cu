@@ -6,8 +6,10 @@ namespace {
 
 using namespace bsf_solve;
 
-__global__ void k_steps(const float* __restrict__ cov, int H, int W, int n, int rule, int R,
-                        ushort4* __restrict__ Lf, DevStatus* st) {
+// rule BSF_STEP_D2: Lf holds floor(lambda~) (capped at 65535) and the mass is
+// that of the interpolated kernels (prod_k M_k, times 2^40).
+__global__ void k_steps(const float* __restrict__ cov, int kind, int H, int W, int n, int rule,
+                        int R, ushort4* __restrict__ Lf, DevStatus* st) {
   const long long HW = (long long)H * W;
   int my_reach = 0;
   float my_mass = 1.f;
@@ -15,11 +17,24 @@ __global__ void k_steps(const float* __restrict__ cov, int H, int W, int n, int 
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HW;
        i += (long long)gridDim.x * blockDim.x) {
     int L[4], flags, reach;
-    if (!pixel_steps(cov[i], cov[HW + i], cov[2 * HW + i], n, rule, R, L, flags, reach)) ++my_range;
-    // prod L^n in float32 (a bound for the choice of q; the stencil checks exactly)
-    const float m1 = (float)(L[0] * L[1]) * (float)(L[2] * L[3]);
-    float mass = m1;
-    for (int j = 1; j < n; ++j) mass *= m1;
+    float C11, C12, C22, mass;
+    load_cov(cov, kind, HW, i, C11, C12, C22);
+    if (rule == BSF_STEP_D2) {
+      int Hq[4];
+      float lam[4];
+      if (!pixel_steps_d2(C11, C12, C22, n, R, Hq, lam, flags, reach)) ++my_range;
+      mass = 1.f;
+      for (int k = 0; k < 4; ++k) {
+        mass *= (float)d2_mass(Hq[k], n);
+        L[k] = min(Hq[k] >> 9, 65535);
+      }
+    } else {
+      if (!pixel_steps(C11, C12, C22, n, rule, R, L, flags, reach)) ++my_range;
+      // prod L^n in float32 (a bound for the choice of q; the stencil checks exactly)
+      const float m1 = (float)(L[0] * L[1]) * (float)(L[2] * L[3]);
+      mass = m1;
+      for (int j = 1; j < n; ++j) mass *= m1;
+    }
     my_reach = max(my_reach, reach);
     my_mass = fmaxf(my_mass, mass);
     my_clamp += (flags & 1) ? 1u : 0u;
@@ -83,9 +98,11 @@ int grid_for(long long work, int threads) {
 
 cudaError_t bsf_launch_steps(const float* cov, int cov_kind, int H, int W, int n, int rule,
                              int R, ushort4* Lf, DevStatus* st, cudaStream_t s) {
-  if (cov_kind != BSF_COV_C) return cudaErrorInvalidValue;
+  if (cov_kind != BSF_COV_C && cov_kind != BSF_COV_LOGSIG_THETA_LOGRHO) return cudaErrorInvalidValue;
+  if (rule == BSF_STEP_D2 && n > 2) return cudaErrorInvalidValue;
   const int threads = 256;
-  k_steps<<<grid_for((long long)H * W, threads), threads, 0, s>>>(cov, H, W, n, rule, R, Lf, st);
+  k_steps<<<grid_for((long long)H * W, threads), threads, 0, s>>>(cov, cov_kind, H, W, n, rule, R,
+                                                                  Lf, st);
   return cudaGetLastError();
 }
 
