@@ -64,29 +64,39 @@ def make_inputs():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples (every 20 ms, timestamped) of the SM clock and the
+    throttle reasons; summary() keeps the samples taken inside the timed
+    regions recorded with mark(), or, when a region is shorter than the
+    sampling interval, the samples within 0.5 s around them."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.regions = []
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.5)  # let the sampler start before the first timed region
         except OSError:
             self.proc = None
         return self
 
+    def mark(self, t0: float, t1: float):
+        """Record a timed region (host wall-clock seconds)."""
+        self.regions.append((t0, t1))
+
     def __exit__(self, *a):
         self.lines = []
         if self.proc is not None:
+            time.sleep(0.1)
             self.proc.terminate()
             try:
                 out, _ = self.proc.communicate(timeout=5)
@@ -96,22 +106,32 @@ class ClockSampler:
             self.lines = [l for l in out.splitlines() if l.strip()]
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
+        import datetime
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for l in getattr(self, "lines", []):
             parts = [p.strip() for p in l.split(",")]
-            if len(parts) < 8:
+            if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[0]))
-                mx = float(parts[1])
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[1]), float(parts[2]),
+                             {nm for nm, v in zip(names, parts[5:9]) if v.lower().startswith("active")}))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[4:8]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+
+        def pick(slack):
+            return [r for r in rows if any(t0 - slack <= r[0] <= t1 + slack for t0, t1 in self.regions)]
+
+        sel, window = pick(0.0), "inside the timed regions"
+        if len(sel) < 3:
+            sel, window = pick(0.5), "within 0.5 s of the timed regions"
+        reasons = set()
+        for r in sel:
+            reasons |= r[3]
+        return {"sm_mhz": statistics.median(r[1] for r in sel) if sel else None,
+                "sm_max_mhz": sel[-1][2] if sel else None, "reasons": sorted(reasons),
+                "samples": len(sel), "window": window}
 
 
 def dist_env():
@@ -172,19 +192,21 @@ def run_gpu(args):
     info = f.info()
 
     # ---- device-resident timed region -------------------------------------
+    clk = ClockSampler(local).__enter__()
     f.set_profiling(True)
     f.read_profile()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier(world)
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            flush.zero_()
-            starts[i].record(stream)
-            step()
-            ends[i].record(stream)
-        torch.cuda.synchronize()
+    t0 = time.time()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    clk.mark(t0, time.time())
     barrier(world)
     prof = f.read_profile()
     f.set_profiling(False)
@@ -208,6 +230,7 @@ def run_gpu(args):
     bs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     be = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier(world)
+    t0 = time.time()
     for i in range(args.steps):
         flush.zero_()
         bs[i].record(stream)
@@ -215,6 +238,7 @@ def run_gpu(args):
         f.backward(d_gout, d_cov, gimg=d_gimg)
         be[i].record(stream)
     torch.cuda.synchronize()
+    clk.mark(t0, time.time())
     barrier(world)
     prof_fb = f.read_profile()
     f.set_profiling(False)
@@ -244,12 +268,15 @@ def run_gpu(args):
     es = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ee = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier(world)
+    t0 = time.time()
     for i in range(args.steps):
         flush.zero_()
         es[i].record(stream)
         e2e_step()
         ee[i].record(stream)
     torch.cuda.synchronize()
+    clk.mark(t0, time.time())
+    clk.__exit__(None, None, None)
     barrier(world)
     e2e_ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(es, ee)), world)
     h2d = img.nbytes + cov.nbytes
@@ -294,7 +321,7 @@ def run_gpu(args):
         with open(tfile) as fh:
             tj = json.load(fh)
         ent = tj.get(dominant)
-        if ent and ent.get("kernel_rev") == kernel_revision():
+        if ent and dominant in KERNEL_SOURCES and ent.get("kernel_rev") == kernel_revision(dominant):
             traffic = ent.get("bytes_per_launch")
 
     clocks = clk.summary()
@@ -318,8 +345,7 @@ def run_gpu(args):
                      "frac": round(achieved / hbm_peak, 4), "traffic": traffic,
                      "algorithmic_bytes_per_launch": alg[dominant]},
         "phases_ms": {k: round(v[0], 5) for k, v in per_phase.items()},
-        "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
-                   "reasons": clocks["reasons"]},
+        "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(img, cov, info.R, info.frac_bits, rows=args.cpu_rows)
@@ -329,14 +355,22 @@ def run_gpu(args):
     return line
 
 
-def kernel_revision() -> str:
-    """Hash of the CUDA sources, to tell whether stored ncu traffic still applies."""
+KERNEL_SOURCES = {
+    "stencil": ["bsf_stencil.cu", "bsf_solve.cuh", "bsf_device.cuh", "bsf_internal.h"],
+    "stencil_d2": ["bsf_continuous.cuh", "bsf_continuous128.cu", "bsf_solve.cuh", "bsf_device.cuh",
+                   "bsf_internal.h"],
+}
+
+
+def kernel_revision(kernel: str = "stencil") -> str:
+    """Hash of the sources that build one kernel (and the build flags), to
+    tell whether stored ncu traffic still applies to it."""
     import hashlib
     hsh = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_1109_5114_gb300", "csrc")
-    for fn in sorted(os.listdir(cs)):
+    for fn in KERNEL_SOURCES[kernel] + ["../build.py", "../../include/bsf.h"]:
         with open(os.path.join(cs, fn), "rb") as fh:
-            hsh.update(fn.encode() + fh.read())
+            hsh.update(os.path.basename(fn).encode() + fh.read())
     return hsh.hexdigest()[:16]
 
 
@@ -459,6 +493,131 @@ def run_batch(args):
     }
 
 
+DIFF_WORKLOAD = ("differentiation: 8 fp32 blob images of 1024x1024 (seeds 0-7), smooth fields "
+                 "log sigma in [0, 3], theta in [0, pi), log rho in [0, 1.1] per image (fp32, "
+                 "requiring grad); target = filter(img, fields + smooth perturbation of amplitude "
+                 "0.1 per field, seed 1); loss = 1/2 ||out - target||^2; continuous steps (D2), "
+                 "n=2, 625 samples per pixel, uint128 running sums, symmetric extension")
+
+
+def diff_inputs(B=8, side=1024):
+    import workloads as wl
+    imgs, fields, targets_fields = [], [], []
+    for i in range(B):
+        imgs.append(wl.blob_image(side, side, seed=i))
+        fl = wl.param_fields_logsig_theta_logrho(side, side, seed=100 + 3 * i,
+                                                 logsig_range=(0.0, 3.0), logrho_range=(0.0, 1.1))
+        pert = np.stack([wl.smooth_field(side, side, seed=1 + 10 * i + j, lo=-0.1, hi=0.1)
+                         for j in range(3)]).astype(np.float32)
+        fields.append(fl)
+        targets_fields.append(np.ascontiguousarray(fl + pert, dtype=np.float32))
+    return imgs, fields, targets_fields
+
+
+def run_diff(args):
+    """Forward with the covariance Jacobian and the parameter gradient of an L2
+    loss (continuous steps), image by image through one context."""
+    import torch
+    from paper_1109_5114_gb300 import bsf
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    side = 1024
+    imgs, fields, tfields = diff_inputs(8, side)
+    vmax = max(float(np.abs(im).max()) for im in imgs)
+    d_imgs = [torch.from_numpy(im).cuda() for im in imgs]
+    d_fields = [torch.from_numpy(fl).cuda() for fl in fields]
+    f = bsf.BoxSplineFilter(side, side, ORDER, "symmetric", precision=bsf.BSF_FIX128, frac_bits=-1,
+                            value_bound=vmax, step_rule=bsf.BSF_STEP_D2,
+                            cov_kind=bsf.BSF_COV_LOGSIG_THETA_LOGRHO)
+    f.set_option(bsf.BSF_OPT_PLAN_UNION, 1)
+    d_tfields = [torch.from_numpy(fl).cuda() for fl in tfields]
+    for fl in d_fields + d_tfields:
+        f.plan(fl)
+    # targets: the filter at the perturbed fields (input preparation, untimed)
+    targets = [f.filter(im, tf).clone() for im, tf in zip(d_imgs, d_tfields)]
+    del d_tfields
+    outs = [torch.empty((side, side), dtype=torch.float32, device="cuda") for _ in range(8)]
+    jacs = [torch.empty((3, side, side), dtype=torch.float32, device="cuda") for _ in range(8)]
+    grads = [torch.empty((3, side, side), dtype=torch.float32, device="cuda") for _ in range(8)]
+    gouts = [torch.empty((side, side), dtype=torch.float32, device="cuda") for _ in range(8)]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def fwd_bwd():
+        for i in range(8):
+            f.filter_jacobian(d_imgs[i], d_fields[i], out=outs[i], jac=jacs[i])
+            torch.sub(outs[i], targets[i], out=gouts[i])          # d loss / d out
+            f.jacobian_vjp(gouts[i], jacs[i], gcov=grads[i])
+
+    def fwd():
+        for i in range(8):
+            f.filter(d_imgs[i], d_fields[i], out=outs[i])
+
+    clk = ClockSampler(local)
+
+    def timed(fn, prof=False):
+        for _ in range(args.warmup):
+            flush.zero_()
+            fn()
+        torch.cuda.synchronize()
+        rc = f.status()
+        if rc != 0:
+            raise RuntimeError(f"device status {rc}: {bsf.bsf_last_error(f.handle).decode()}")
+        if prof:
+            f.set_profiling(True)
+            f.read_profile()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        barrier(world)
+        t0 = time.time()
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        clk.mark(t0, time.time())
+        barrier(world)
+        p = f.read_profile() if prof else None
+        if prof:
+            f.set_profiling(False)
+        return max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world), p
+
+    with clk:
+        fb_ms, prof_fb = timed(fwd_bwd, prof=True)
+        fw_ms, prof_fw = timed(fwd, prof=True)
+    info = f.info()
+    loss = sum(float(0.5 * ((o - t) ** 2).sum()) for o, t in zip(outs, targets))
+    f.close()
+    if rank != 0:
+        return None
+    px = 8 * side * side
+    per_phase = {k: (ms / max(c, 1), c) for k, (ms, c) in prof_fb.items() if c}
+    clocks = clk.summary()
+    return {
+        "metric": "Mpixel/s fwd+bwd (parameter gradient) of the differentiation workload",
+        "value": round(world * px * args.steps / (fb_ms * 1e-3) / 1e6, 2), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(fb_ms / args.steps, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u128", "data": "synthetic",
+        "config": {"workload": DIFF_WORKLOAD, "images": 8, "H": side, "W": side, "n": ORDER,
+                   "R": info.R, "frac_bits": info.frac_bits, "max_mass": info.max_mass,
+                   "l2": "flushed before every timed step (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "fwd": {"value": round(world * px * args.steps / (fw_ms * 1e-3) / 1e6, 2), "unit": UNIT,
+                "ms_per_step": round(fw_ms / args.steps, 4),
+                "phases_ms": {k: round(ms / max(c, 1), 5) for k, (ms, c) in prof_fw.items() if c}},
+        "phases_ms": {k: round(v[0], 5) for k, v in per_phase.items()},
+        "gpu_launches": 8 * (1 + 3 * 3 + 1 + 1),
+        "loss": loss,
+        "clocks": clocks,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -470,8 +629,10 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=256,
                     help="rows of the workload each --impl reference step filters")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="spacevariant2048", choices=["spacevariant2048", "batch64"],
-                    help="spacevariant2048: the benchmark line; batch64: the batched form")
+    ap.add_argument("--workload", default="spacevariant2048",
+                    choices=["spacevariant2048", "batch64", "diff8x1024"],
+                    help="spacevariant2048: the benchmark line; batch64: the batched form; "
+                         "diff8x1024: continuous steps with the parameter gradient")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "bsf":
         args.warmup = 3
@@ -479,6 +640,8 @@ def main():
         line = run_reference(args)
     elif args.workload == "batch64":
         line = run_batch(args)
+    elif args.workload == "diff8x1024":
+        line = run_diff(args)
     else:
         line = run_gpu(args)
     if line is not None:

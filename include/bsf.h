@@ -121,6 +121,9 @@ extern "C" {
 #define BSF_OPT_TEST_UNPUBLISHED 3  /* failure injection for tests: 1 = the look-back
                                        scan's first chunk never marks its results
                                        ready, so every wait on it runs out */
+#define BSF_OPT_PLAN_UNION   6  /* 1 = each bsf_plan widens the plan instead of replacing it:
+                                   R and the mass bound become the largest over every plan
+                                   since the option was set (one context for many fields) */
 #define BSF_SCAN_LOOKBACK     0 /* single pass, decoupled look-back between blocks */
 #define BSF_SCAN_THREE_PHASE  1 /* reduce / carry / rescan; no block waits on another
                                    (measured faster on GB300 for 2048^2, n = 2) */

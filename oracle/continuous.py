@@ -72,32 +72,85 @@ def _check_order(n: int) -> None:
 # steps
 # ---------------------------------------------------------------------------
 
+_F = np.float32
+# Cody-Waite constants: ln 2 as a 16-bit head plus a tail, pi/2 as two 12-bit
+# heads plus a tail (each head times a small integer is exact in float32)
+LN2_HI, LN2_LO = _F(0.693145751953125), _F(1.428606765330187e-06)
+LOG2E = _F(1.0 / math.log(2.0))
+PIO2 = (_F(1.57080078125), _F(-4.453584551811218e-06), _F(-8.705516307827565e-10))
+TWO_OVER_PI = _F(2.0 / math.pi)
+INV_FACT = [_F(1.0 / math.factorial(k)) for k in range(11)]
+
+
+def exp_f32(x):
+    """e^x in float32 by Cody-Waite reduction x = k ln2 + r (|r| <= ln2/2) and
+    the degree-7 Taylor polynomial of e^r, times 2^k; x clamped to [-87, 88].
+    Every step is one IEEE float32 operation.  Pinned by tests: within 1.5
+    ulp of float64 exp."""
+    x = np.minimum(np.maximum(np.asarray(x, dtype=_F), _F(-87)), _F(88))
+    kf = np.rint(x * LOG2E).astype(_F)
+    r = ((x - kf * LN2_HI).astype(_F) - kf * LN2_LO).astype(_F)
+    p = INV_FACT[7]
+    for i in range(6, -1, -1):
+        p = (p * r + INV_FACT[i]).astype(_F)
+    scale = ((kf.astype(np.int32) + 127) << 23).astype(np.uint32).view(_F)
+    return (p * scale).astype(_F)
+
+
+def sincos_f32(x):
+    """(sin x, cos x) in float32: Cody-Waite reduction x = j pi/2 + r
+    (|r| <= pi/4, three-part pi/2), Taylor polynomials of degree 9 and 10 in
+    r, the quadrant j mod 4 selecting and signing them.  Pinned by tests:
+    within 2^-23 of float64 sin and cos on [-20, 20]."""
+    x = np.asarray(x, dtype=_F)
+    jf = np.rint(x * TWO_OVER_PI).astype(_F)
+    r = x
+    for part in PIO2:
+        r = (r - jf * part).astype(_F)
+    r2 = (r * r).astype(_F)
+    c = INV_FACT
+    sp = c[9]
+    sp = (sp * r2 - c[7]).astype(_F)
+    sp = (sp * r2 + c[5]).astype(_F)
+    sp = (sp * r2 - c[3]).astype(_F)
+    sp = ((sp * r2).astype(_F) * r + r).astype(_F)
+    cp = -c[10]
+    cp = (cp * r2 + c[8]).astype(_F)
+    cp = (cp * r2 - c[6]).astype(_F)
+    cp = (cp * r2 + c[4]).astype(_F)
+    cp = (cp * r2 - c[2]).astype(_F)
+    cp = (cp * r2 + _F(1)).astype(_F)
+    j = jf.astype(np.int64) & 3
+    sn = np.select([j == 0, j == 1, j == 2], [sp, cp, -sp], -cp).astype(_F)
+    cs = np.select([j == 0, j == 1, j == 2], [cp, -sp, -cp], sp).astype(_F)
+    return sn, cs
+
+
 def cov_from_log_params(ls, th, lr):
     """(C11, C12, C22) as float32 from float32 planes (log sigma, theta, log rho).
 
     The covariance reading of the configs (trace 2 sigma^2, eigenvalue ratio
-    rho, major axis at theta), evaluated in float64 in this fixed order and
-    rounded once to float32:
+    rho, major axis at theta), evaluated in float32 with exp_f32 and
+    sincos_f32, one IEEE operation per step in this order:
         s2 = exp(2 ls), rho = exp(lr), k = (2 s2) / (1 + rho),
-        C11 = k (rho cos^2 + sin^2), C22 = k (rho sin^2 + cos^2),
-        C12 = k ((rho - 1) sin cos).
-    Pinned by tests against params.cov_from_sigma_rho_theta.
+        C11 = k (rho c^2 + s^2), C22 = k (rho s^2 + c^2),
+        C12 = k ((rho - 1) (s c)).
+    Pinned by tests against params.cov_from_sigma_rho_theta in float64.
     """
-    ls = np.asarray(ls, dtype=np.float32).astype(np.float64)
-    th = np.asarray(th, dtype=np.float32).astype(np.float64)
-    lr = np.asarray(lr, dtype=np.float32).astype(np.float64)
-    s2 = np.exp(2.0 * ls)
-    rho = np.exp(lr)
-    k = (2.0 * s2) / (1.0 + rho)
-    c = np.cos(th)
-    s = np.sin(th)
-    cc = c * c
-    ss = s * s
-    sc = s * c
-    c11 = k * (rho * cc + ss)
-    c22 = k * (rho * ss + cc)
-    c12 = k * ((rho - 1.0) * sc)
-    return (c11.astype(np.float32), c12.astype(np.float32), c22.astype(np.float32))
+    ls = np.asarray(ls, dtype=_F)
+    th = np.asarray(th, dtype=_F)
+    lr = np.asarray(lr, dtype=_F)
+    s2 = exp_f32((_F(2) * ls).astype(_F))
+    rho = exp_f32(lr)
+    k = ((_F(2) * s2).astype(_F) / (_F(1) + rho).astype(_F)).astype(_F)
+    s, c = sincos_f32(th)
+    cc = (c * c).astype(_F)
+    ss = (s * s).astype(_F)
+    sc = (s * c).astype(_F)
+    c11 = (k * ((rho * cc).astype(_F) + ss).astype(_F)).astype(_F)
+    c22 = (k * ((rho * ss).astype(_F) + cc).astype(_F)).astype(_F)
+    c12 = (k * ((rho - _F(1)).astype(_F) * sc).astype(_F)).astype(_F)
+    return c11, c12, c22
 
 
 def covariance_planes(planes: np.ndarray, kind: int):

@@ -40,6 +40,7 @@ struct bsf_ctx {
   int short_tiles = 0;           // look-back tiles of half height
   int wait_limit = 1 << 20;
   int test_unpublished = 0;
+  bool plan_union = false;       // plans widen R and the mass bound instead of replacing them
   ushort4* Lf = nullptr;
   DevStatus* st = nullptr;
   DevStatus host_st{};
@@ -227,12 +228,16 @@ int run_steps(bsf_t h, const float* cov, int cov_kind, bool sync_plan) {
   h->steps_current = true;
   if (sync_plan) {
     if ((rc = read_status(h))) return rc;
-    h->plan_mass = bits_to_float(h->host_st.max_mass_bits);
-    h->plan_reach = h->host_st.max_reach;
+    const bool widen = h->plan_union && h->planned;
+    const double mass = bits_to_float(h->host_st.max_mass_bits);
+    const int reach = h->host_st.max_reach;
+    h->plan_mass = widen && h->plan_mass > mass ? h->plan_mass : mass;
+    h->plan_reach = widen && h->plan_reach > reach ? h->plan_reach : reach;
     if (!h->R_fixed) {
       // the solve ran unbounded: every tap of this field fits this R
-      h->R = h->host_st.max_reach > 3 * h->n ? h->host_st.max_reach : 3 * h->n;
-      if (h->step_rule == BSF_STEP_D2 && h->R < d2_min_reach(h->n)) h->R = d2_min_reach(h->n);
+      int R = reach > 3 * h->n ? reach : 3 * h->n;
+      if (h->step_rule == BSF_STEP_D2 && R < d2_min_reach(h->n)) R = d2_min_reach(h->n);
+      h->R = widen && h->R > R ? h->R : R;
     }
     h->planned = true;
     if ((rc = ensure_workspace(h))) return rc;
@@ -426,6 +431,9 @@ int bsf_set_option(bsf_t h, int option, long long value) {
       return BSF_OK;
     case BSF_OPT_TEST_UNPUBLISHED:
       h->test_unpublished = value != 0;
+      return BSF_OK;
+    case BSF_OPT_PLAN_UNION:
+      h->plan_union = value != 0;
       return BSF_OK;
     default:
       return fail(h, BSF_EINVAL, "unknown option %d", option);

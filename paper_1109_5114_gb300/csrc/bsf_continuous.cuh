@@ -45,22 +45,38 @@ template <typename T> __device__ __forceinline__ void addc(T& a, const T& x, int
   else if (c == -2) a -= x + x;
 }
 
+// Sample i of one direction: offset (in grid steps along d_k) and the
+// coefficients of the sample in Base and E.
 template <int NF> struct Pattern;
 template <> struct Pattern<2> {
   static constexpr int NP = 5;
   __device__ static constexpr int base(int i) { return (i == 0 || i == 4) ? 1 : (i == 2 ? -2 : 0); }
   __device__ static constexpr int diff(int i) { return (i == 1 || i == 3) ? 1 : (i == 2 ? 0 : -1); }
+  // a0, a0 + 1, -1, -a0 - 3, -a0 - 2
+  __device__ static int pos(int a0, int i) {
+    return i == 0 ? a0 : i == 1 ? a0 + 1 : i == 2 ? -1 : i == 3 ? -a0 - 3 : -a0 - 2;
+  }
 };
 template <> struct Pattern<1> {
   static constexpr int NP = 4;
   __device__ static constexpr int base(int i) { return i == 0 ? 1 : (i == 3 ? -1 : 0); }
   __device__ static constexpr int diff(int i) { return (i == 1 || i == 3) ? 1 : -1; }
+  // a0, a0 + 1, -a0 - 2, -a0 - 1
+  __device__ static int pos(int a0, int i) {
+    return i == 0 ? a0 : i == 1 ? a0 + 1 : i == 2 ? -a0 - 2 : -a0 - 1;
+  }
 };
 
 struct DirTaps {
-  int off[5];   // element offsets of the samples along d_k
+  int a0;       // first interpolation bracket along d_k
+  int e;        // element stride of d_k
   unsigned th;  // interpolation fraction, units of 2^-10
 };
+
+// Directions K >= kUnrolled are unrolled (the inner 25 samples for n = 2);
+// the outer ones are loops, which keeps the kernel body small enough for the
+// instruction cache.
+constexpr int kUnrolled = 2;
 
 // Weighted sums over the samples of directions K..3 for the sample set
 // anchored at element idx.  out[0] is the value; with DER, out[1 + (j - K)]
@@ -68,31 +84,46 @@ struct DirTaps {
 template <typename T, int NF, int K, bool DER>
 __device__ __forceinline__ void interp_level(const T* __restrict__ S, int idx, const DirTaps* dt,
                                              T* out) {
-  constexpr int NP = Pattern<NF>::NP;
+  using P = Pattern<NF>;
   constexpr int NCI = (K == 3 || !DER) ? 1 : 4 - K;
   T base[NCI], e[NCI];
 #pragma unroll
   for (int c = 0; c < NCI; ++c) { base[c] = 0; e[c] = 0; }
+  const DirTaps d = dt[K];
+  if constexpr (K >= kUnrolled) {
 #pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    T in[NCI];
-    if constexpr (K == 3) {
-      in[0] = bsf_load(S + idx + dt[3].off[i]);
-    } else {
-      interp_level<T, NF, K + 1, DER>(S, idx + dt[K].off[i], dt, in);
+    for (int i = 0; i < P::NP; ++i) {
+      T in[NCI];
+      const int at = idx + P::pos(d.a0, i) * d.e;
+      if constexpr (K == 3) {
+        in[0] = bsf_load(S + at);
+      } else {
+        interp_level<T, NF, K + 1, DER>(S, at, dt, in);
+      }
+#pragma unroll
+      for (int c = 0; c < NCI; ++c) {
+        addc(base[c], in[c], P::base(i));
+        addc(e[c], in[c], P::diff(i));
+      }
     }
+  } else {
+#pragma unroll 1
+    for (int i = 0; i < P::NP; ++i) {
+      T in[NCI];
+      interp_level<T, NF, K + 1, DER>(S, idx + P::pos(d.a0, i) * d.e, dt, in);
+      const int cb = P::base(i), ce = P::diff(i);
 #pragma unroll
-    for (int c = 0; c < NCI; ++c) {
-      addc(base[c], in[c], Pattern<NF>::base(i));
-      addc(e[c], in[c], Pattern<NF>::diff(i));
+      for (int c = 0; c < NCI; ++c) {
+        addc(base[c], in[c], cb);
+        addc(e[c], in[c], ce);
+      }
     }
   }
-  const unsigned th = dt[K].th;
-  out[0] = (base[0] << 10) + mul_small(e[0], th);
+  out[0] = (base[0] << 10) + mul_small(e[0], d.th);
   if constexpr (DER) {
     out[1] = e[0] << 10;
 #pragma unroll
-    for (int c = 1; c < NCI; ++c) out[1 + c] = (base[c] << 10) + mul_small(e[c], th);
+    for (int c = 1; c < NCI; ++c) out[1 + c] = (base[c] << 10) + mul_small(e[c], d.th);
   }
 }
 
@@ -104,7 +135,7 @@ __device__ __forceinline__ float to_f32(u128 a) { return bsf_rn32((i128)a); }
 enum { kOut = 0, kOutJac = 1, kVjp = 2 };
 
 template <typename T, int NF, int MODE> struct D2Occ {
-  static constexpr int value = sizeof(T) == 8 ? (MODE == kOut ? 4 : 2) : (MODE == kOut ? 3 : 1);
+  static constexpr int value = sizeof(T) == 8 ? (MODE == kOut ? 6 : 4) : (MODE == kOut ? 4 : 4);
 };
 
 template <typename T, int NF, typename Out, int MODE>
@@ -120,7 +151,13 @@ k_stencil_d2(const T* __restrict__ S, long long pitch, int R, const float* __res
   if (x >= W || y >= rows) return;
   const long long HW = (long long)H * W, i = (long long)(row0 + y) * W + x;
   float C11, C12, C22;
-  load_cov(cov, kind, HW, i, C11, C12, C22);
+  LogCov lc;
+  if (kind == BSF_COV_LOGSIG_THETA_LOGRHO) {
+    lc = cov_of_log_params(cov[i], cov[HW + i], cov[2 * HW + i]);
+    C11 = lc.C11; C12 = lc.C12; C22 = lc.C22;
+  } else {
+    C11 = cov[i]; C12 = cov[HW + i]; C22 = cov[2 * HW + i];
+  }
   int Hq[4], flags, reach;
   float lam[4];
   const bool in_reach = pixel_steps_d2(C11, C12, C22, NF, R, Hq, lam, flags, reach);
@@ -140,22 +177,9 @@ k_stencil_d2(const T* __restrict__ S, long long pitch, int R, const float* __res
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int Q0 = NF == 2 ? 2 * Hq[k] - 1024 : Hq[k] - 512;
-    const int a0 = Q0 >> 10;
+    dt[k].a0 = Q0 >> 10;
     dt[k].th = (unsigned)(Q0 & 1023);
-    const int e = estep[k];
-    if (NF == 2) {
-      dt[k].off[0] = a0 * e;
-      dt[k].off[1] = (a0 + 1) * e;
-      dt[k].off[2] = -e;
-      dt[k].off[3] = (-a0 - 3) * e;
-      dt[k].off[4] = (-a0 - 2) * e;
-    } else {
-      dt[k].off[0] = a0 * e;
-      dt[k].off[1] = (a0 + 1) * e;
-      dt[k].off[2] = (-a0 - 2) * e;
-      dt[k].off[3] = (-a0 - 1) * e;
-      dt[k].off[4] = 0;
-    }
+    dt[k].e = estep[k];
   }
   T res[DER ? 5 : 1];
   interp_level<T, NF, 0, DER>(S, (y + R) * p32 + (x + R), dt, res);
@@ -184,22 +208,25 @@ k_stencil_d2(const T* __restrict__ S, long long pitch, int R, const float* __res
     }
   }
   if constexpr (DER) {
-    // d out / d lambda_k = 2^-q (dacc_k - acc dM_k / M_k) / (dscale prod M)
+    // d out / d lambda_k = 2^-q (dacc_k M_k - acc dM_k) / (dscale M_k prod M).
+    // The difference cancels most of its terms: it is formed in float64 with
+    // one fused multiply-add (each operand within 2^-53 of its exact value);
+    // everything after it is float32.
     const double a = to_f64(res[0]);
-    const double Md = bsf_rn64_u(D) * (NF == 1 ? 2.0 : 1.0);
+    const float inv = 1.f / (bsf_rn32_u(D) * (NF == 1 ? 2.f : 1.f));
     float gA[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const double ratio = (double)d2_dmass(Hq[k], NF) / (double)Mk[k];
-      const double jl = (to_f64(res[1 + k]) - a * ratio) * scale_d / Md;
+      const double t = __fma_rn(to_f64(res[1 + k]), (double)Mk[k],
+                                -__dmul_rn(a, (double)d2_dmass(Hq[k], NF)));
+      const float jl = (float)(t * scale_d) * inv / (float)Mk[k];  // t 2^-q < 2^99 |J|
       // lambda = sqrt(1 + A / |d|^2):  d lambda / d A = 1 / (2 lambda |d|^2)
-      gA[k] = in_reach ? (float)jl / ((k & 1 ? 4.f : 2.f) * lam[k]) : 0.f;
+      gA[k] = in_reach ? jl / ((k & 1 ? 4.f : 2.f) * lam[k]) : 0.f;
     }
     float gC[3], gP[3];
     solve_scales_vjp(C11, C12, C22, scale_of_order(NF), gA, gC);
     if (kind == BSF_COV_LOGSIG_THETA_LOGRHO) {
-      const LogCov r = cov_of_log_params(cov[i], cov[HW + i], cov[2 * HW + i]);
-      log_params_vjp(r, gC, gP);
+      log_params_vjp(lc, gC, gP);
     } else {
       gP[0] = gC[0]; gP[1] = gC[1]; gP[2] = gC[2];
     }

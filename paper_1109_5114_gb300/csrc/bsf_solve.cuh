@@ -113,28 +113,92 @@ __device__ __forceinline__ bool pixel_steps(float C11, float C12, float C22, int
 }
 
 // ---------------------------------------------------------------------------
+// Float32 elementary functions for the log-parameter fields, written out as
+// fixed sequences of IEEE round-to-nearest operations (no contraction), so
+// that any IEEE float32 implementation of the same steps gives the same bits.
+//   exp: Cody-Waite reduction x = k ln2 + r, |r| <= ln2/2, with ln2 split into
+//        a 16-bit head (k ln2_hi exact) and a tail; e^r by its Taylor
+//        polynomial of degree 7 (Horner); times 2^k from the exponent bits.
+//        Input clamped to [-87, 88].  Within 1.2 ulp of the exact value.
+//   sin, cos: Cody-Waite reduction x = j pi/2 + r, |r| <= pi/4, with pi/2
+//        split into two 12-bit heads and a tail (exact products for
+//        |j| < 2^12, i.e. |x| below about 6400); Taylor polynomials of degree
+//        9 (sin) and 10 (cos); the quadrant j mod 4 selects and signs them.
+//        Within 1.5 x 2^-24 absolute on [-20, 20].
+// (Cody and Waite, Software Manual for the Elementary Functions, 1980.)
+// ---------------------------------------------------------------------------
+constexpr float kLn2Hi = 0.693145751953125f, kLn2Lo = 1.428606765330187e-06f;
+constexpr float kLog2e = 1.4426950216293335f;
+constexpr float kPio2A = 1.57080078125f, kPio2B = -4.453584551811218e-06f,
+                kPio2C = -8.705516307827565e-10f, k2OverPi = 0.6366197466850281f;
+// 1/k! rounded to float32
+constexpr float kF2 = 0.5f, kF3 = 0.1666666716337204f, kF4 = 0.0416666679084301f,
+                kF5 = 0.008333333767950535f, kF6 = 0.0013888889225199819f,
+                kF7 = 0.00019841270113829523f, kF8 = 2.4801587642286904e-05f,
+                kF9 = 2.7557318844628753e-06f, kF10 = 2.755731998149713e-07f;
+
+__device__ __forceinline__ float exp_cw(float x) {
+  x = fminf(fmaxf(x, -87.f), 88.f);
+  const float kf = rintf(__fmul_rn(x, kLog2e));
+  const float r = __fsub_rn(__fsub_rn(x, __fmul_rn(kf, kLn2Hi)), __fmul_rn(kf, kLn2Lo));
+  float p = kF7;
+  p = __fadd_rn(__fmul_rn(p, r), kF6);
+  p = __fadd_rn(__fmul_rn(p, r), kF5);
+  p = __fadd_rn(__fmul_rn(p, r), kF4);
+  p = __fadd_rn(__fmul_rn(p, r), kF3);
+  p = __fadd_rn(__fmul_rn(p, r), kF2);
+  p = __fadd_rn(__fmul_rn(p, r), 1.f);
+  p = __fadd_rn(__fmul_rn(p, r), 1.f);
+  return __fmul_rn(p, __int_as_float(((int)kf + 127) << 23));
+}
+
+__device__ __forceinline__ void sincos_cw(float x, float& sn, float& cs) {
+  const float jf = rintf(__fmul_rn(x, k2OverPi));
+  float r = __fsub_rn(x, __fmul_rn(jf, kPio2A));
+  r = __fsub_rn(r, __fmul_rn(jf, kPio2B));
+  r = __fsub_rn(r, __fmul_rn(jf, kPio2C));
+  const float r2 = __fmul_rn(r, r);
+  float sp = kF9;
+  sp = __fsub_rn(__fmul_rn(sp, r2), kF7);
+  sp = __fadd_rn(__fmul_rn(sp, r2), kF5);
+  sp = __fsub_rn(__fmul_rn(sp, r2), kF3);
+  sp = __fadd_rn(__fmul_rn(__fmul_rn(sp, r2), r), r);
+  float cp = -kF10;
+  cp = __fadd_rn(__fmul_rn(cp, r2), kF8);
+  cp = __fsub_rn(__fmul_rn(cp, r2), kF6);
+  cp = __fadd_rn(__fmul_rn(cp, r2), kF4);
+  cp = __fsub_rn(__fmul_rn(cp, r2), kF2);
+  cp = __fadd_rn(__fmul_rn(cp, r2), 1.f);
+  switch ((int)jf & 3) {
+    case 0: sn = sp; cs = cp; break;
+    case 1: sn = cp; cs = -sp; break;
+    case 2: sn = -sp; cs = -cp; break;
+    default: sn = -cp; cs = sp; break;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Covariance of one pixel from a field of kind BSF_COV_C (planes C11, C12,
-// C22) or BSF_COV_LOGSIG_THETA_LOGRHO (planes log sigma, theta, log rho).  The
-// latter is evaluated in float64 in one fixed order, every operation rounded
-// once (explicit intrinsics, no contraction), then rounded to float32:
+// C22) or BSF_COV_LOGSIG_THETA_LOGRHO (planes log sigma, theta, log rho), in
+// float32 with the functions above, in this fixed order:
 //   s2 = exp(2 ls), rho = exp(lr), k = (2 s2) / (1 + rho),
-//   C11 = k (rho c^2 + s^2), C22 = k (rho s^2 + c^2), C12 = k ((rho - 1) s c).
+//   C11 = k (rho c^2 + s^2), C22 = k (rho s^2 + c^2), C12 = k ((rho - 1) (s c))
 // (trace 2 sigma^2, eigenvalue ratio rho, major axis at theta).
 // ---------------------------------------------------------------------------
-struct LogCov {  // float64 intermediates kept for the chain rule
-  double k, rho, c, s, C11, C12, C22;
+struct LogCov {  // intermediates kept for the chain rule
+  float k, rho, c, s, C11, C12, C22;
 };
 
 __device__ __forceinline__ LogCov cov_of_log_params(float ls, float th, float lr) {
   LogCov r;
-  const double s2 = exp(__dmul_rn(2.0, (double)ls));
-  r.rho = exp((double)lr);
-  r.k = __ddiv_rn(__dmul_rn(2.0, s2), __dadd_rn(1.0, r.rho));
-  sincos((double)th, &r.s, &r.c);
-  const double cc = __dmul_rn(r.c, r.c), ss = __dmul_rn(r.s, r.s), sc = __dmul_rn(r.s, r.c);
-  r.C11 = __dmul_rn(r.k, __dadd_rn(__dmul_rn(r.rho, cc), ss));
-  r.C22 = __dmul_rn(r.k, __dadd_rn(__dmul_rn(r.rho, ss), cc));
-  r.C12 = __dmul_rn(r.k, __dmul_rn(__dsub_rn(r.rho, 1.0), sc));
+  const float s2 = exp_cw(__fmul_rn(2.f, ls));
+  r.rho = exp_cw(lr);
+  r.k = __fdiv_rn(__fmul_rn(2.f, s2), __fadd_rn(1.f, r.rho));
+  sincos_cw(th, r.s, r.c);
+  const float cc = __fmul_rn(r.c, r.c), ss = __fmul_rn(r.s, r.s), sc = __fmul_rn(r.s, r.c);
+  r.C11 = __fmul_rn(r.k, __fadd_rn(__fmul_rn(r.rho, cc), ss));
+  r.C22 = __fmul_rn(r.k, __fadd_rn(__fmul_rn(r.rho, ss), cc));
+  r.C12 = __fmul_rn(r.k, __fmul_rn(__fsub_rn(r.rho, 1.f), sc));
   return r;
 }
 
@@ -143,9 +207,7 @@ __device__ __forceinline__ void load_cov(const float* __restrict__ cov, int kind
   const float a = cov[i], b = cov[HW + i], c = cov[2 * HW + i];
   if (kind == BSF_COV_LOGSIG_THETA_LOGRHO) {
     const LogCov r = cov_of_log_params(a, b, c);
-    C11 = __double2float_rn(r.C11);
-    C12 = __double2float_rn(r.C12);
-    C22 = __double2float_rn(r.C22);
+    C11 = r.C11; C12 = r.C12; C22 = r.C22;
   } else {
     C11 = a; C12 = b; C22 = c;
   }
@@ -279,15 +341,16 @@ __device__ __forceinline__ void solve_scales_vjp(float C11, float C12, float C22
   gC[2] = C22 > 0.f ? g22 : 0.f;
 }
 
-// Chain from (C11, C12, C22) to (log sigma, theta, log rho) (float64).
+// Chain from (C11, C12, C22) to (log sigma, theta, log rho) (float32):
+//   dC/dls = 2 C,  dC/dtheta = (-2 C12, C11 - C22, 2 C12),
+//   dC/dlr = rho (k (c^2, s c, s^2) - C / (1 + rho)).
 __device__ __forceinline__ void log_params_vjp(const LogCov& r, const float gC[3], float gP[3]) {
-  const double g11 = gC[0], g12 = gC[1], g22 = gC[2];
-  const double sc = r.s * r.c, cs2 = r.c * r.c - r.s * r.s, kd = r.k * (r.rho - 1.0);
-  const double inv = 1.0 / (1.0 + r.rho);
-  gP[0] = (float)(2.0 * (r.C11 * g11 + r.C12 * g12 + r.C22 * g22));
-  gP[1] = (float)(-2.0 * kd * sc * g11 + kd * cs2 * g12 + 2.0 * kd * sc * g22);
-  gP[2] = (float)(r.rho * ((r.k * r.c * r.c - r.C11 * inv) * g11 + (r.k * sc - r.C12 * inv) * g12 +
-                           (r.k * r.s * r.s - r.C22 * inv) * g22));
+  const float g11 = gC[0], g12 = gC[1], g22 = gC[2];
+  const float inv = 1.f / (1.f + r.rho);
+  gP[0] = 2.f * (r.C11 * g11 + r.C12 * g12 + r.C22 * g22);
+  gP[1] = 2.f * r.C12 * (g22 - g11) + (r.C11 - r.C22) * g12;
+  gP[2] = r.rho * ((r.k * r.c * r.c - r.C11 * inv) * g11 + (r.k * r.s * r.c - r.C12 * inv) * g12 +
+                   (r.k * r.s * r.s - r.C22 * inv) * g22);
 }
 
 }  // namespace bsf_solve

@@ -112,3 +112,65 @@ def test_precision_8192_u8_uint128_sampled_bit_exact():
         ref = finalize(np.array([acc[p]], dtype=object), D, 0, np.float32)[0]
         assert out[p] == ref, p
     assert len(keep) >= 40
+
+
+def test_differentiation_workload_one_image_full_size():
+    """One 1024^2 image of the differentiation workload (blob seed 0, smooth
+    log sigma / theta / log rho fields), continuous steps n = 2, uint128,
+    automatic q, float32 output with the Jacobian (the call bench.py times):
+    sampled outputs bit-exact against the oracle's running-sum pipeline on
+    the whole padded image; the Jacobian within the tolerance of
+    test_gpu_continuous at the same pixels; and against central differences
+    (step 1e-3, float64, unquantised steps) of the float64 definition."""
+    import torch
+    import bench
+    from oracle import continuous as cn
+    from paper_1109_5114_gb300 import bsf
+    imgs, fields, _ = bench.diff_inputs(1, 1024)
+    img, fl = imgs[0], fields[0]
+    side = 1024
+    f = bsf.BoxSplineFilter(side, side, 2, "symmetric", precision=bsf.BSF_FIX128, frac_bits=-1,
+                            value_bound=float(np.abs(img).max()), step_rule=bsf.BSF_STEP_D2,
+                            cov_kind=bsf.BSF_COV_LOGSIG_THETA_LOGRHO)
+    tf = torch.from_numpy(fl).cuda()
+    f.plan(tf)
+    out, J = f.filter_jacobian(torch.from_numpy(img).cuda(), tf)
+    torch.cuda.synchronize()
+    assert f.status() == 0
+    info = f.info()
+    out, J = out.cpu().numpy(), J.cpu().numpy()
+    rng = np.random.default_rng(0)
+    pix = sorted({(int(y), int(x)) for y, x in zip(rng.integers(0, side, 256), rng.integers(0, side, 256))}
+                 | {(0, 0), (side - 1, side - 1), (0, side - 1), (side - 1, 0)})
+    rec = cn.filter_d2_modular(img, fl, 2, kernels.SYMMETRIC, info.frac_bits, bits=128, kind=1,
+                               R=info.R, pixels=pix)
+    assert not any(r["far"] for r in rec.values())
+    ref = np.array([cn.output(rec[p], info.frac_bits) for p in pix], dtype=np.float32)
+    np.testing.assert_array_equal(np.array([out[p] for p in pix]), ref)
+    refJ = np.array([cn.jacobian_planes(rec[p], fl[:, p[0], p[1]].astype(np.float64), 1, 2,
+                                        info.frac_bits) for p in pix])
+    gotJ = np.array([J[:, p[0], p[1]] for p in pix])
+    for c in range(3):
+        scale = np.abs(refJ[:, c]).max()
+        assert (np.abs(gotJ[:, c] - refJ[:, c]) <= 2e-4 * scale + 1e-3 * np.abs(refJ[:, c])).all()
+    # central differences of the unquantised float64 filter
+    h = 1e-3
+    checked = 0
+    for (y, x) in pix[:12]:
+        pl = fl[:, y, x].astype(np.float64)
+        fd = np.zeros(3)
+        kink = False
+        for j in range(3):
+            pp, pm = pl.copy(), pl.copy()
+            pp[j] += h
+            pm[j] -= h
+            lp = np.real(cn.steps_f64(list(pp), 1, 2))
+            lm = np.real(cn.steps_f64(list(pm), 1, 2))
+            kink |= any(cn.brackets(a, 2) != cn.brackets(b, 2) for a, b in zip(lp, lm))
+            fd[j] = (cn.filter_d2_f64_at(img, pp, 1, 2, kernels.SYMMETRIC, y, x)
+                     - cn.filter_d2_f64_at(img, pm, 1, 2, kernels.SYMMETRIC, y, x)) / (2 * h)
+        if kink:
+            continue
+        checked += 1
+        assert np.allclose(J[:, y, x], fd, atol=0.02 * np.abs(fd).max() + 1e-6), ((y, x), J[:, y, x], fd)
+    assert checked >= 6
