@@ -254,6 +254,41 @@ int bsf_filter_rows(bsf_t h, const void* img, int dtype, long long ld, const flo
 int bsf_filter_backward(bsf_t h, const float* gout, long long ldg, const float* cov, int cov_kind,
                         float* gimg, long long ldgi, float* gcov);
 
+/* Row-band backward (integer steps): the multi-device form of
+ * bsf_filter_backward.  A device that filtered rows [y0, y1) computes the
+ * adjoint of its band alone: the pixels of the band scatter into running
+ * sums over the band's padded rows [y0 - R, y1 + R), which are summed in
+ * reverse and folded by the boundary rule onto image rows
+ * [a0, a1) = [max(0, y0 - R), min(H, y1 + R)).  The band's outputs equal the
+ * whole image's on every input, so these adjoints add up to the whole-image
+ * gradient: each device adds its neighbours' overlapping rows (the halo
+ * add-exchange of R rows each way) to its own rows [y0, y1) and finalises.
+ * The sums are exact integers modulo 2^64 (two's complement int64 in acc),
+ * so the assembled gradient equals bsf_filter_backward's bit for bit when
+ * every band uses the same grad_bits: take bsf_grad_frac_bits of the maximum
+ * of |gout| over all bands (bsf_grad_absmax_rows per band, then the maximum
+ * across devices).
+ *   acc   device int64 [a1 - a0][lda] (written); row 0 is image row a0.
+ * Requires BSF_FIX64, R <= H, integer steps.  Errors: BSF_EINVAL, BSF_ESTATE,
+ * BSF_ENOMEM, BSF_ECUDA. */
+int bsf_filter_backward_rows(bsf_t h, const float* gout, long long ldg, const float* cov,
+                             int cov_kind, int y0, int y1, int grad_bits, long long* acc,
+                             long long lda);
+
+/* Fraction bits qg = 54 - ceil(log2 m) of the fixed-point gradient weights for
+ * m = max |gout| (float32 value of m), clamped to [0, 100].  Pure function. */
+int bsf_grad_frac_bits(double max_abs_gout);
+
+/* max |gout| over rows [y0, y1) of device gout [H][ldg] into *result (host
+ * float).  Synchronises.  Errors: BSF_EINVAL, BSF_ECUDA. */
+int bsf_grad_absmax_rows(bsf_t h, const float* gout, long long ldg, int y0, int y1, float* result);
+
+/* gimg[r][x] = RN32(acc[r][x]) 2^-grad_bits for rows r < rows (device int64
+ * acc [rows][lda], device float32 gimg [rows][ldgi]): the final rounding of
+ * the backward.  Errors: BSF_EINVAL, BSF_ECUDA. */
+int bsf_grad_finalize(bsf_t h, const long long* acc, long long lda, int rows, int grad_bits,
+                      float* gimg, long long ldgi);
+
 /* Continuous-step filter (step rule BSF_STEP_D2) and its Jacobian with
  * respect to the covariance field.
  *

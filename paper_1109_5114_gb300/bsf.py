@@ -82,6 +82,12 @@ bsf_read_profile = _fn("bsf_read_profile", c_int, bsf_t, ctypes.POINTER(c_double
 bsf_filter_jacobian = _fn("bsf_filter_jacobian", c_int, bsf_t, c_void_p, c_int, c_ll, c_void_p, c_int,
                           c_void_p, c_int, c_ll, c_void_p, c_ll)
 bsf_jacobian_vjp = _fn("bsf_jacobian_vjp", c_int, bsf_t, c_void_p, c_ll, c_void_p, c_ll, c_void_p)
+bsf_filter_backward_rows = _fn("bsf_filter_backward_rows", c_int, bsf_t, c_void_p, c_ll, c_void_p, c_int,
+                               c_int, c_int, c_int, c_void_p, c_ll)
+bsf_grad_frac_bits = _fn("bsf_grad_frac_bits", c_int, c_double)
+bsf_grad_absmax_rows = _fn("bsf_grad_absmax_rows", c_int, bsf_t, c_void_p, c_ll, c_int, c_int,
+                           ctypes.POINTER(ctypes.c_float))
+bsf_grad_finalize = _fn("bsf_grad_finalize", c_int, bsf_t, c_void_p, c_ll, c_int, c_int, c_void_p, c_ll)
 
 class bsf_image_desc(ctypes.Structure):
     _fields_ = [("H", c_int), ("W", c_int), ("img", c_void_p), ("dtype", c_int), ("ld", c_ll),
@@ -284,6 +290,39 @@ class BoxSplineFilter:
                                  ctypes.c_void_p(gcov.data_ptr()) if want_gcov else None)
         check(self._h, rc)
         return gimg, gcov
+
+    def grad_absmax_rows(self, gout, y0: int, y1: int) -> float:
+        """max |gout| over rows [y0, y1) (library reduction; synchronises)."""
+        self._stream()
+        r = ctypes.c_float()
+        check(self._h, bsf_grad_absmax_rows(self._h, ctypes.c_void_p(gout.data_ptr()), gout.stride(0),
+                                            y0, y1, ctypes.byref(r)))
+        return float(r.value)
+
+    def backward_rows(self, gout, cov, y0: int, y1: int, grad_bits: int):
+        """Band adjoint: exact int64 sums on image rows [a0, a1) = [y0 - R, y1 + R) clipped.
+
+        Returns (acc, a0, a1), acc an int64 CUDA tensor [a1 - a0][W]."""
+        import torch
+        self._stream()
+        R = self.info().R
+        a0, a1 = max(0, y0 - R), min(self.H, y1 + R)
+        acc = torch.empty((a1 - a0, self.W), dtype=torch.int64, device=gout.device)
+        check(self._h, bsf_filter_backward_rows(self._h, ctypes.c_void_p(gout.data_ptr()), gout.stride(0),
+                                                ctypes.c_void_p(cov.data_ptr()), self.cov_kind, y0, y1,
+                                                grad_bits, ctypes.c_void_p(acc.data_ptr()), acc.stride(0)))
+        return acc, a0, a1
+
+    def grad_finalize(self, acc, grad_bits: int, gimg=None):
+        """gimg = RN32(acc) 2^-grad_bits (library kernel), float32 [rows][W]."""
+        import torch
+        self._stream()
+        rows = acc.shape[0]
+        if gimg is None:
+            gimg = torch.empty((rows, self.W), dtype=torch.float32, device=acc.device)
+        check(self._h, bsf_grad_finalize(self._h, ctypes.c_void_p(acc.data_ptr()), acc.stride(0), rows,
+                                         grad_bits, ctypes.c_void_p(gimg.data_ptr()), gimg.stride(0)))
+        return gimg
 
     def preintegrate(self, img):
         self._stream()

@@ -532,6 +532,97 @@ int bsf_jacobian_vjp(bsf_t h, const float* gout, long long ldg, const float* jac
   return BSF_OK;
 }
 
+// G (adjoint running sums) and Gx (row-folded) for the whole padded domain.
+static int ensure_backward_workspace(bsf_t h) {
+  if (h->precision != BSF_FIX64) return fail(h, BSF_EINVAL, "backward needs BSF_FIX64");
+  if (h->R < 0) return fail(h, BSF_ESTATE, "padding unknown: plan or filter first");
+  int rc;
+  if ((rc = ensure_workspace(h))) return rc;
+  const size_t G_bytes = (size_t)h->pitch * h->Hp * 8, Gx_bytes = (size_t)h->Hp * h->W * 8;
+  if (h->G_bytes != G_bytes || h->Gx_bytes != Gx_bytes) {
+    BSF_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->G) cudaFree(h->G);
+    if (h->Gx) cudaFree(h->Gx);
+    h->G = h->Gx = nullptr;
+    h->G_bytes = h->Gx_bytes = 0;
+    BSF_CUDA(h, cudaMalloc(&h->G, G_bytes));
+    BSF_CUDA(h, cudaMalloc(&h->Gx, Gx_bytes));
+    h->G_bytes = G_bytes;
+    h->Gx_bytes = Gx_bytes;
+  }
+  return BSF_OK;
+}
+
+int bsf_grad_frac_bits(double max_abs_gout) { return bsf_grad_q_host(max_abs_gout); }
+
+int bsf_grad_absmax_rows(bsf_t h, const float* gout, long long ldg, int y0, int y1, float* result) {
+  if (!h) return BSF_EINVAL;
+  if (!gout || !result) return fail(h, BSF_EINVAL, "NULL gout or result");
+  if (ldg < h->W || y0 < 0 || y1 <= y0 || y1 > h->H) return fail(h, BSF_EINVAL, "bad rows or ldg");
+  BSF_CUDA(h, cudaMemsetAsync(&h->st->max_absg_bits, 0, sizeof(unsigned), h->stream));
+  cudaError_t e = bsf_launch_gabsmax(gout + (long long)y0 * ldg, ldg, y1 - y0, h->W, h->st, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "gradient maximum");
+  int rc = read_status(h);
+  if (rc) return rc;
+  const unsigned b = h->host_st.max_absg_bits;
+  std::memcpy(result, &b, sizeof b);
+  return BSF_OK;
+}
+
+int bsf_filter_backward_rows(bsf_t h, const float* gout, long long ldg, const float* cov,
+                             int cov_kind, int y0, int y1, int grad_bits, long long* acc,
+                             long long lda) {
+  if (!h) return BSF_EINVAL;
+  int rc = check_cov_kind(h, cov_kind);
+  if (rc) return rc;
+  if (h->step_rule == BSF_STEP_D2) return fail(h, BSF_EINVAL, "band backward: integer steps only");
+  if (!gout || !cov || !acc) return fail(h, BSF_EINVAL, "NULL gout, cov or acc");
+  if (ldg < h->W || lda < h->W) return fail(h, BSF_EINVAL, "leading dimension < W");
+  if (y0 < 0 || y1 <= y0 || y1 > h->H) return fail(h, BSF_EINVAL, "bad row band");
+  if (grad_bits < 0 || grad_bits > 100) return fail(h, BSF_EINVAL, "grad_bits outside [0, 100]");
+  if ((rc = ensure_backward_workspace(h))) return rc;
+  if (h->R > h->H) return fail(h, BSF_EINVAL, "band backward needs R <= H");
+  const int rows = y1 - y0, Hb = rows + 2 * h->R;
+  const int a0 = y0 - h->R > 0 ? y0 - h->R : 0, a1 = y1 + h->R < h->H ? y1 + h->R : h->H;
+  if ((rc = reset_counters(h, true, false))) return rc;
+  cudaError_t e;
+  {
+    PhaseTimer t(h, BSF_PHASE_BWD_SCATTER);
+    BSF_CUDA(h, cudaMemsetAsync(h->G, 0, (size_t)h->pitch * Hb * 8, h->stream));
+    e = bsf_launch_scatter_d1(h->n, h->G, h->pitch, h->R, cov, cov_kind, h->step_rule, gout, ldg,
+                              h->H, h->W, y0, rows, grad_bits, h->st, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "band scatter");
+  {
+    PhaseTimer t(h, BSF_PHASE_BWD_SCANS);
+    const int skews[3] = {-1, 1, 0};
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+      e = bsf_launch_vscan(BSF_FIX64, h->n, skews[i], true, h->G, h->pitch, Hb, h->Wp, h->scan_chunk,
+                           h->agg, h->carry, h->stream);
+    if (e == cudaSuccess) e = bsf_launch_suffix_rows(8, h->n, h->G, h->pitch, Hb, h->Wp, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "band running sums");
+  {
+    PhaseTimer t(h, BSF_PHASE_BWD_FOLD);
+    e = bsf_launch_fold_band(h->G, h->pitch, Hb, h->H, h->W, h->R, y0, h->boundary, h->Gx, a0, a1,
+                             acc, lda, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "band fold");
+  return BSF_OK;
+}
+
+int bsf_grad_finalize(bsf_t h, const long long* acc, long long lda, int rows, int grad_bits,
+                      float* gimg, long long ldgi) {
+  if (!h) return BSF_EINVAL;
+  if (!acc || !gimg) return fail(h, BSF_EINVAL, "NULL acc or gimg");
+  if (lda < h->W || ldgi < h->W || rows <= 0 || rows > h->H)
+    return fail(h, BSF_EINVAL, "bad rows or leading dimension");
+  if (grad_bits < 0 || grad_bits > 100) return fail(h, BSF_EINVAL, "grad_bits outside [0, 100]");
+  cudaError_t e = bsf_launch_grad_finalize(acc, lda, rows, h->W, grad_bits, gimg, ldgi, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "gradient finalize");
+  return BSF_OK;
+}
+
 static int backward_d2(bsf_t h, const float* gout, long long ldg, const float* cov, int cov_kind,
                        float* gcov) {
   int rc = check_d2(h);
@@ -561,21 +652,8 @@ int bsf_filter_backward(bsf_t h, const float* gout, long long ldg, const float* 
   }
   if (!gout || !cov || !gimg) return fail(h, BSF_EINVAL, "NULL gout, cov or gimg");
   if (ldg < h->W || ldgi < h->W) return fail(h, BSF_EINVAL, "leading dimension < W");
-  if (h->precision != BSF_FIX64) return fail(h, BSF_EINVAL, "backward needs BSF_FIX64");
-  if (h->R < 0) return fail(h, BSF_ESTATE, "padding unknown: plan or filter first");
-  if ((rc = ensure_workspace(h))) return rc;
-  const size_t G_bytes = (size_t)h->pitch * h->Hp * 8, Gx_bytes = (size_t)h->Hp * h->W * 8;
-  if (h->G_bytes != G_bytes || h->Gx_bytes != Gx_bytes) {
-    BSF_CUDA(h, cudaStreamSynchronize(h->stream));
-    if (h->G) cudaFree(h->G);
-    if (h->Gx) cudaFree(h->Gx);
-    h->G = h->Gx = nullptr;
-    h->G_bytes = h->Gx_bytes = 0;
-    BSF_CUDA(h, cudaMalloc(&h->G, G_bytes));
-    BSF_CUDA(h, cudaMalloc(&h->Gx, Gx_bytes));
-    h->G_bytes = G_bytes;
-    h->Gx_bytes = Gx_bytes;
-  }
+  if ((rc = ensure_backward_workspace(h))) return rc;
+  const size_t G_bytes = h->G_bytes;
   if ((rc = reset_counters(h, true, false))) return rc;
   cudaError_t e;
   {
@@ -585,7 +663,7 @@ int bsf_filter_backward(bsf_t h, const float* gout, long long ldg, const float* 
     e = bsf_launch_gabsmax(gout, ldg, h->H, h->W, h->st, h->stream);
     if (e == cudaSuccess)
       e = bsf_launch_scatter_d1(h->n, h->G, h->pitch, h->R, cov, cov_kind, h->step_rule, gout, ldg, h->H,
-                                h->W, h->st, h->stream);
+                                h->W, 0, h->H, -1, h->st, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "backward scatter");
   {

@@ -13,6 +13,8 @@
 // derives the same qg), the scatter adds w_t g(p) with 64-bit integer
 // reductions (exact and order-independent, hence deterministic), the suffix
 // sums wrap modulo 2^64, and gimg = RN32(acc) 2^-qg.
+#include <cstring>
+
 #include "bsf_solve.cuh"
 
 namespace {
@@ -23,7 +25,7 @@ __global__ void k_gabsmax(const float* __restrict__ g, long long ld, int H, int 
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HW;
        i += (long long)gridDim.x * blockDim.x) {
     const long long y = i / W, x = i - y * W;
-    m = fmaxf(m, fabsf(g[y * ld + x]));
+    m = fmaxf(m, fabsf(g[y * ld + x]));  // NaN is ignored here; the weights check it
   }
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) bsf_atomic_max_pos_float(&st->max_absg_bits, m);
@@ -64,21 +66,23 @@ template <int NF>
 __global__ void __launch_bounds__(256)
 k_scatter_d1(unsigned long long* __restrict__ G, long long pitch, int R,
              const float* __restrict__ cov, int kind, int rule, const float* __restrict__ gout,
-             long long ldg, int H, int W, DevStatus* st) {
+             long long ldg, int H, int W, int row0, int rows, int qg_given, DevStatus* st) {
+  // pixel (x, row0 + y) of the band; G holds the band's padded rows
+  // (row 0 = image row row0 - R)
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= W || y >= H) return;
-  const long long HW = (long long)H * W, i = (long long)y * W + x;
+  if (x >= W || y >= rows) return;
+  const long long HW = (long long)H * W, i = (long long)(row0 + y) * W + x;
   int L[4], flags, reach;
   float C11, C12, C22;
   bsf_solve::load_cov(cov, kind, HW, i, C11, C12, C22);
   bsf_solve::pixel_steps(C11, C12, C22, NF, rule, R, L, flags, reach);
-  const int qg = grad_q(st->max_absg_bits);
+  const int qg = qg_given >= 0 ? qg_given : grad_q(st->max_absg_bits);
   unsigned long long D = (unsigned long long)(L[0] * L[1]) * (unsigned long long)(L[2] * L[3]);
   const unsigned long long D1 = D;
 #pragma unroll
   for (int j = 1; j < NF; ++j) D *= D1;
-  const float xg = __fmul_rn(gout[(long long)y * ldg + x], bsf_pow2_f32(qg));  // exact scaling
+  const float xg = __fmul_rn(gout[(long long)(row0 + y) * ldg + x], bsf_pow2_f32(qg));  // exact scaling
   bool ok;
   const unsigned long long g =
       bsf_quantize_f32<unsigned long long>(__fdiv_rn(xg, bsf_rn32_u64(D)), 0, ok);
@@ -138,6 +142,31 @@ __global__ void k_fold_y_out(const unsigned long long* __restrict__ Gx, int H, i
   gimg[(long long)y * ldo + x] = __fmul_rn(bsf_rn32_i64((long long)acc), bsf_pow2_f32(-qg));
 }
 
+// Band form of the row fold: image rows a0 .. a1 - 1 receive the band's
+// padded rows (row r = extended row row0 - R + r, r < Hb) that extend onto
+// them; the exact integer sums are written (no rounding).
+__global__ void k_fold_y_band(const unsigned long long* __restrict__ Gx, int Hb, int H, int W, int R,
+                              int row0, int boundary, int a0, int a1,
+                              long long* __restrict__ acc_out, long long lda) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = a0 + (int)blockIdx.y;
+  if (x >= W || y >= a1) return;
+  unsigned long long acc = 0;
+  for_preimages(y, H, R, boundary, [&](int zp) {
+    const int r = zp - row0;  // zp = z + R, r = z - (row0 - R)
+    if (r >= 0 && r < Hb) acc += Gx[(long long)r * W + x];
+  });
+  acc_out[(long long)(y - a0) * lda + x] = (long long)acc;
+}
+
+__global__ void k_grad_finalize(const long long* __restrict__ acc, long long lda, int rows, int W,
+                                int qg, float* __restrict__ gimg, long long ldo) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= W || y >= rows) return;
+  gimg[(long long)y * ldo + x] = __fmul_rn(bsf_rn32_i64(acc[(long long)y * lda + x]), bsf_pow2_f32(-qg));
+}
+
 int grid_for(long long work, int threads) {
   long long g = (work + threads - 1) / threads;
   const long long cap = 152LL * 16;
@@ -145,6 +174,19 @@ int grid_for(long long work, int threads) {
 }
 
 }  // namespace
+
+int bsf_grad_q_host(double m) {
+  // the rule of grad_q on the float32 value of m
+  const float f = (float)m;
+  unsigned b;
+  std::memcpy(&b, &f, sizeof b);
+  const unsigned E = (b >> 23) & 0xffu, M = b & 0x7fffffu;
+  int c;
+  if (E == 0 || E == 0xffu) c = E == 0 && M != 0 ? -126 : 0;
+  else c = (int)E - 127 + (M != 0 ? 1 : 0);
+  const int q = 54 - c;
+  return q < 0 ? 0 : (q > 100 ? 100 : q);
+}
 
 cudaError_t bsf_launch_gabsmax(const float* gout, long long ldg, int H, int W, DevStatus* st,
                                cudaStream_t s) {
@@ -154,14 +196,35 @@ cudaError_t bsf_launch_gabsmax(const float* gout, long long ldg, int H, int W, D
 
 cudaError_t bsf_launch_scatter_d1(int n, void* G, long long pitch, int R, const float* cov,
                                   int cov_kind, int rule, const float* gout, long long ldg, int H,
-                                  int W, DevStatus* st, cudaStream_t s) {
-  dim3 block(32, 8), grid((W + 31) / 32, (H + 7) / 8);
+                                  int W, int row0, int rows, int qg, DevStatus* st, cudaStream_t s) {
+  dim3 block(32, 8), grid((W + 31) / 32, (rows + 7) / 8);
   auto* g = (unsigned long long*)G;
   const int k = cov_kind;
-  if (n == 1) k_scatter_d1<1><<<grid, block, 0, s>>>(g, pitch, R, cov, k, rule, gout, ldg, H, W, st);
-  else if (n == 2) k_scatter_d1<2><<<grid, block, 0, s>>>(g, pitch, R, cov, k, rule, gout, ldg, H, W, st);
-  else if (n == 3) k_scatter_d1<3><<<grid, block, 0, s>>>(g, pitch, R, cov, k, rule, gout, ldg, H, W, st);
-  else return cudaErrorInvalidValue;
+  if (n == 1)
+    k_scatter_d1<1><<<grid, block, 0, s>>>(g, pitch, R, cov, k, rule, gout, ldg, H, W, row0, rows, qg, st);
+  else if (n == 2)
+    k_scatter_d1<2><<<grid, block, 0, s>>>(g, pitch, R, cov, k, rule, gout, ldg, H, W, row0, rows, qg, st);
+  else if (n == 3)
+    k_scatter_d1<3><<<grid, block, 0, s>>>(g, pitch, R, cov, k, rule, gout, ldg, H, W, row0, rows, qg, st);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t bsf_launch_fold_band(const void* G, long long pitch, int Hb, int H, int W, int R,
+                                 int row0, int boundary, void* Gx, int a0, int a1, long long* acc,
+                                 long long lda, cudaStream_t s) {
+  dim3 blk(128);
+  k_fold_x<<<dim3((W + 127) / 128, Hb), blk, 0, s>>>((const unsigned long long*)G, pitch, Hb, W, R,
+                                                      boundary, (unsigned long long*)Gx);
+  k_fold_y_band<<<dim3((W + 127) / 128, a1 - a0), blk, 0, s>>>((const unsigned long long*)Gx, Hb, H, W,
+                                                               R, row0, boundary, a0, a1, acc, lda);
+  return cudaGetLastError();
+}
+
+cudaError_t bsf_launch_grad_finalize(const long long* acc, long long lda, int rows, int W, int qg,
+                                     float* gimg, long long ldo, cudaStream_t s) {
+  k_grad_finalize<<<dim3((W + 127) / 128, rows), 128, 0, s>>>(acc, lda, rows, W, qg, gimg, ldo);
   return cudaGetLastError();
 }
 

@@ -65,9 +65,22 @@ cudaError_t bsf_launch_suffix_rows(int elem_bytes, int n, void* S, long long pit
 // (zeroed by the caller), extension fold of G (via Gx: [Hp][W]) into gimg.
 cudaError_t bsf_launch_gabsmax(const float* gout, long long ldg, int H, int W, DevStatus* st,
                                cudaStream_t s);
+// Scatter of the pixels of rows [row0, row0 + rows) into G (the band's padded
+// rows); qg >= 0 fixes the weights' fraction bits, -1 takes them from the
+// device maximum of |gout| (bsf_launch_gabsmax).
 cudaError_t bsf_launch_scatter_d1(int n, void* G, long long pitch, int R, const float* cov,
-                                  int cov_kind, int rule, const float* gout, long long ldg, int H, int W,
-                                  DevStatus* st, cudaStream_t s);
+                                  int cov_kind, int rule, const float* gout, long long ldg, int H,
+                                  int W, int row0, int rows, int qg, DevStatus* st, cudaStream_t s);
+// Band fold: G's Hb padded rows (row 0 = image row row0 - R) folded by the
+// extension rule into image rows [a0, a1) as exact int64 sums (acc, lda per row).
+cudaError_t bsf_launch_fold_band(const void* G, long long pitch, int Hb, int H, int W, int R,
+                                 int row0, int boundary, void* Gx, int a0, int a1, long long* acc,
+                                 long long lda, cudaStream_t s);
+// gimg = RN32(acc) 2^-qg, rows x W.
+cudaError_t bsf_launch_grad_finalize(const long long* acc, long long lda, int rows, int W, int qg,
+                                     float* gimg, long long ldo, cudaStream_t s);
+// qg = 54 - ceil(log2 m) of the float32 value of m, clamped to [0, 100].
+int bsf_grad_q_host(double m);
 cudaError_t bsf_launch_fold(const void* G, long long pitch, int Hp, int H, int W, int R,
                             int boundary, void* Gx, float* gimg, long long ldo, const DevStatus* st,
                             cudaStream_t s);
