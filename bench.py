@@ -530,8 +530,9 @@ def run_batch(args):
 DIFF_WORKLOAD = ("differentiation: 8 fp32 blob images of 1024x1024 (seeds 0-7), smooth fields "
                  "log sigma in [0, 3], theta in [0, pi), log rho in [0, 1.1] per image (fp32, "
                  "requiring grad); target = filter(img, fields + smooth perturbation of amplitude "
-                 "0.1 per field, seed 1); loss = 1/2 ||out - target||^2; continuous steps (D2), "
-                 "n=2, 625 samples per pixel, uint128 running sums, symmetric extension")
+                 "0.1 per field, seed 1); loss = 1/2 ||out - target||^2, gradients with respect to "
+                 "the image and the three fields; continuous steps (D2), n=2, 625 samples per "
+                 "pixel, uint128 running sums and adjoint sums, symmetric extension")
 
 
 def diff_inputs(B=8, side=1024):
@@ -577,6 +578,7 @@ def run_diff(args):
     outs = [torch.empty((side, side), dtype=torch.float32, device="cuda") for _ in range(8)]
     jacs = [torch.empty((3, side, side), dtype=torch.float32, device="cuda") for _ in range(8)]
     grads = [torch.empty((3, side, side), dtype=torch.float32, device="cuda") for _ in range(8)]
+    gimgs = [torch.empty((side, side), dtype=torch.float32, device="cuda") for _ in range(8)]
     gouts = [torch.empty((side, side), dtype=torch.float32, device="cuda") for _ in range(8)]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -585,7 +587,8 @@ def run_diff(args):
         for i in range(8):
             f.filter_jacobian(d_imgs[i], d_fields[i], out=outs[i], jac=jacs[i])
             torch.sub(outs[i], targets[i], out=gouts[i])          # d loss / d out
-            f.jacobian_vjp(gouts[i], jacs[i], gcov=grads[i])
+            f.jacobian_vjp(gouts[i], jacs[i], gcov=grads[i])      # d loss / d fields
+            f.backward(gouts[i], d_fields[i], gimg=gimgs[i], want_gimg=True)  # d loss / d image
 
     def fwd():
         for i in range(8):
@@ -633,7 +636,7 @@ def run_diff(args):
     per_phase = {k: (ms / max(c, 1), c) for k, (ms, c) in prof_fb.items() if c}
     clocks = clk.summary()
     return {
-        "metric": "Mpixel/s fwd+bwd (parameter gradient) of the differentiation workload",
+        "metric": "Mpixel/s fwd+bwd (image and parameter gradients) of the differentiation workload",
         "value": round(world * px * args.steps / (fb_ms * 1e-3) / 1e6, 2), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(fb_ms / args.steps, 4), "higher_is_better": True, "scaling": "weak",
@@ -646,7 +649,9 @@ def run_diff(args):
                 "ms_per_step": round(fw_ms / args.steps, 4),
                 "phases_ms": {k: round(ms / max(c, 1), 5) for k, (ms, c) in prof_fw.items() if c}},
         "phases_ms": {k: round(v[0], 5) for k, v in per_phase.items()},
-        "gpu_launches": 8 * (1 + 3 * 3 + 1 + 1),
+        # per image: rows, 3 x (agg + apply), stencil, vjp; backward: absmax,
+        # scatter, 3 x (agg + apply), suffix rows, 2 folds
+        "gpu_launches": 8 * ((1 + 3 * 2 + 1 + 1) + (1 + 1 + 3 * 2 + 1 + 2)),
         "loss": loss,
         "clocks": clocks,
     }

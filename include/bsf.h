@@ -247,9 +247,16 @@ int bsf_filter_rows(bsf_t h, const void* img, int dtype, long long ld, const flo
  *         almost everywhere and is written as zeros.
  * Requires a known R (plan or max_reach) and BSF_FIX64.  The first call
  * allocates the backward workspace (synchronous).
- * With step rule BSF_STEP_D2 only the covariance gradient is available
- * (gimg must be NULL, gcov non-NULL): gcov = gout * d out / d plane, from
- * the held running sums of the forward's image (see bsf_filter_jacobian).
+ * With step rule BSF_STEP_D2: gcov (if not NULL) = gout * d out / d plane,
+ * from the held running sums of the forward's image (see
+ * bsf_filter_jacobian); gimg (if not NULL, BSF_FIX128 contexts) is the image
+ * gradient: each pixel scatters g(p) = RNE(RN32(RN32(gout 2^qg) / RN32(M)))
+ * times the product of its four interpolation weights at its 5^4 (n = 2) or
+ * 4^4 (n = 1) samples into uint128 adjoint sums (128-bit additions built from
+ * two 64-bit atomics and the carry of the first), qg = 118 -
+ * ceil(log2 max|gout|) in [0, 126]; reversed running sums and the extension
+ * fold follow as above, then gimg = RN32(acc) 2^-qg.  At least one of gimg and
+ * gcov must be given.
  * Errors: BSF_EINVAL, BSF_ESTATE, BSF_ENOMEM, BSF_ECUDA. */
 int bsf_filter_backward(bsf_t h, const float* gout, long long ldg, const float* cov, int cov_kind,
                         float* gimg, long long ldgi, float* gcov);

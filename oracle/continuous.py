@@ -559,3 +559,55 @@ def brackets(lam: float, n: int):
         qt = c - t * lam
         out.append(math.floor(qt) if n - 2 * t >= 0 else math.ceil(qt) - 1)
     return tuple(out)
+
+
+# ---------------------------------------------------------------------------
+# adjoint with respect to the image
+# ---------------------------------------------------------------------------
+
+def grad_frac_bits_d2(max_abs_gout: float) -> int:
+    """qg = 118 - ceil(log2 m) for m = max |gout| (float32), clamped to [0, 126]:
+    the gradient sums are exact modulo 2^128 and keep 2^8 of headroom below
+    2^127 (the rule of the integer-step backward, 54 = 62 - 8, moved to 128
+    bits); 126 keeps 2^qg a float32."""
+    m = float(np.float32(max_abs_gout))
+    if m == 0.0 or not math.isfinite(m):
+        c = 0
+    else:
+        mant, e = math.frexp(m)
+        c = e - 1 if mant == 0.5 else e
+    return int(min(max(118 - c, 0), 126))
+
+
+def quantize_weight_d2(gout: float, M: int, qg: int) -> int:
+    """g = RNE(RN32(RN32(gout 2^qg) / RN32(M))) as an exact Python integer."""
+    from .rounding import rn_f32_int
+    x = np.float32(np.float32(gout) * np.float32(math.ldexp(1.0, qg)))
+    y = rn_f32_int(M)
+    q = np.float32(x / y)
+    return int(round(float(q)))  # round half to even; exact above 2^24
+
+
+def adjoint_d2_acc(gq: dict, planes: np.ndarray, n: int, boundary: int, shape, kind: int = 0,
+                   R: int | None = None):
+    """Exact adjoint sums acc(x) = sum_p gq(p) K_p(x - p) folded onto the
+    image by the extension rule, for integer weights gq {(y, x): int}.
+    Python integers, object array [H][W]."""
+    Hh, Ww = shape
+    acc = np.zeros((Hh, Ww), dtype=object)
+    for (y, x), g in gq.items():
+        if g == 0:
+            continue
+        Hs, _, _, _ = _pixel_steps(planes, kind, n, y, x, R)
+        K, _, ox, oy, *_ = kernels_d2(Hs, n)
+        kh, kw = K.shape
+        yi, yv = extend_index(np.arange(y - oy, y - oy + kh), Hh, boundary)
+        xi, xv = extend_index(np.arange(x - ox, x - ox + kw), Ww, boundary)
+        for a in range(kh):
+            if not yv[a]:
+                continue
+            row = K[a] * g
+            for b in range(kw):
+                if xv[b] and row[b] != 0:
+                    acc[yi[a], xi[b]] += row[b]
+    return acc

@@ -387,25 +387,28 @@ def _make_autograd():
             ctx.filt = filt
             ctx.d2 = filt.step_rule == BSF_STEP_D2  # noqa: F821
             if ctx.d2:
-                if img.requires_grad:
-                    raise NotImplementedError("continuous steps: no image gradient")
+                cov = cov.contiguous()
                 if cov.requires_grad:
-                    out, jac = filt.filter_jacobian(img.contiguous(), cov.contiguous())
-                    ctx.save_for_backward(jac)
+                    out, jac = filt.filter_jacobian(img.contiguous(), cov)
+                    ctx.save_for_backward(cov, jac)
                     return out
-                ctx.save_for_backward()
-                return filt.filter(img.contiguous(), cov.contiguous())
+                ctx.save_for_backward(cov)
+                return filt.filter(img.contiguous(), cov)
             out = filt.filter(img.contiguous(), cov.contiguous())
             ctx.save_for_backward(cov)
             return out
 
         @staticmethod
         def backward(ctx, gout):
+            gout = gout.contiguous().float()
             if ctx.d2:
-                if not ctx.needs_input_grad[1]:
-                    return None, None, None
-                (jac,) = ctx.saved_tensors
-                return None, ctx.filt.jacobian_vjp(gout.contiguous().float(), jac), None
+                saved = ctx.saved_tensors
+                gimg = gcov = None
+                if ctx.needs_input_grad[0]:
+                    gimg, _ = ctx.filt.backward(gout, saved[0], want_gimg=True, want_gcov=False)
+                if ctx.needs_input_grad[1]:
+                    gcov = ctx.filt.jacobian_vjp(gout, saved[1])
+                return gimg, gcov, None
             (cov,) = ctx.saved_tensors
             gimg, gcov = ctx.filt.backward(gout.contiguous().float(), cov,
                                            want_gcov=ctx.needs_input_grad[1])

@@ -623,19 +623,66 @@ int bsf_grad_finalize(bsf_t h, const long long* acc, long long lda, int rows, in
   return BSF_OK;
 }
 
+// Continuous steps: gcov = gout * d out / d plane (from the held running sums),
+// and/or the image gradient through uint128 adjoint sums.
 static int backward_d2(bsf_t h, const float* gout, long long ldg, const float* cov, int cov_kind,
-                       float* gcov) {
+                       float* gimg, long long ldgi, float* gcov) {
   int rc = check_d2(h);
   if (rc) return rc;
-  if (!gcov) return fail(h, BSF_EINVAL, "continuous steps: gcov is NULL");
-  if (!h->have_S || h->S_R != h->R || h->S_elem != h->elem || h->S_row0 != 0 || h->S_rows != h->H)
-    return fail(h, BSF_ESTATE, "no whole-image pre-integration is held");
+  if (!gcov && !gimg) return fail(h, BSF_EINVAL, "continuous steps: gimg and gcov are NULL");
+  if (gimg && h->precision != BSF_FIX128)
+    return fail(h, BSF_EINVAL, "continuous steps: the image gradient needs BSF_FIX128");
+  if (h->R < 0) return fail(h, BSF_ESTATE, "padding unknown: plan or filter first");
   if ((rc = reset_counters(h, true, false))) return rc;
-  PhaseTimer t(h, BSF_PHASE_BWD_SCATTER);
-  cudaError_t e = bsf_launch_stencil_d2(h->precision, h->n, 2, h->S, h->pitch, h->R, cov, cov_kind,
-                                        h->H, h->W, 0, h->H, h->S_q, nullptr, BSF_F32, h->W, gcov,
-                                        h->W, (long long)h->H * h->W, gout, ldg, h->st, h->stream);
-  if (e != cudaSuccess) return cuda_fail(h, e, "continuous-step vjp");
+  cudaError_t e = cudaSuccess;
+  if (gcov) {
+    if (!h->have_S || h->S_R != h->R || h->S_elem != h->elem || h->S_row0 != 0 || h->S_rows != h->H)
+      return fail(h, BSF_ESTATE, "no whole-image pre-integration is held");
+    PhaseTimer t(h, BSF_PHASE_BWD_SCATTER);
+    e = bsf_launch_stencil_d2(h->precision, h->n, 2, h->S, h->pitch, h->R, cov, cov_kind, h->H, h->W,
+                              0, h->H, h->S_q, nullptr, BSF_F32, h->W, gcov, h->W,
+                              (long long)h->H * h->W, gout, ldg, h->st, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "continuous-step vjp");
+  }
+  if (!gimg) return BSF_OK;
+  if ((rc = ensure_workspace(h))) return rc;
+  const size_t G_bytes = (size_t)h->pitch * h->Hp * 16, Gx_bytes = (size_t)h->Hp * h->W * 16;
+  if (h->G_bytes != G_bytes || h->Gx_bytes != Gx_bytes) {
+    BSF_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->G) cudaFree(h->G);
+    if (h->Gx) cudaFree(h->Gx);
+    h->G = h->Gx = nullptr;
+    h->G_bytes = h->Gx_bytes = 0;
+    BSF_CUDA(h, cudaMalloc(&h->G, G_bytes));
+    BSF_CUDA(h, cudaMalloc(&h->Gx, Gx_bytes));
+    h->G_bytes = G_bytes;
+    h->Gx_bytes = Gx_bytes;
+  }
+  {
+    PhaseTimer t(h, BSF_PHASE_BWD_SCATTER);
+    BSF_CUDA(h, cudaMemsetAsync(&h->st->max_absg_bits, 0, sizeof(unsigned), h->stream));
+    BSF_CUDA(h, cudaMemsetAsync(h->G, 0, G_bytes, h->stream));
+    e = bsf_launch_gabsmax(gout, ldg, h->H, h->W, h->st, h->stream);
+    if (e == cudaSuccess)
+      e = bsf_launch_scatter_d2(h->n, h->G, h->pitch, h->R, cov, cov_kind, gout, ldg, h->H, h->W,
+                                h->st, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "continuous-step scatter");
+  {
+    PhaseTimer t(h, BSF_PHASE_BWD_SCANS);
+    const int skews[3] = {-1, 1, 0};
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+      e = bsf_launch_vscan(BSF_FIX128, h->n, skews[i], true, h->G, h->pitch, h->Hp, h->Wp,
+                           h->scan_chunk, h->agg, h->carry, h->stream);
+    if (e == cudaSuccess) e = bsf_launch_suffix_rows(16, h->n, h->G, h->pitch, h->Hp, h->Wp, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "continuous-step adjoint sums");
+  {
+    PhaseTimer t(h, BSF_PHASE_BWD_FOLD);
+    e = bsf_launch_fold128(h->G, h->pitch, h->Hp, h->H, h->W, h->R, h->boundary, h->Gx, gimg, ldgi,
+                           h->st, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "continuous-step fold");
   return BSF_OK;
 }
 
@@ -645,10 +692,9 @@ int bsf_filter_backward(bsf_t h, const float* gout, long long ldg, const float* 
   int rc = check_cov_kind(h, cov_kind);
   if (rc) return rc;
   if (h->step_rule == BSF_STEP_D2) {
-    if (gimg) return fail(h, BSF_EINVAL, "continuous steps: the image gradient is not available");
     if (!gout || !cov) return fail(h, BSF_EINVAL, "NULL gout or cov");
-    if (ldg < h->W) return fail(h, BSF_EINVAL, "leading dimension < W");
-    return backward_d2(h, gout, ldg, cov, cov_kind, gcov);
+    if (ldg < h->W || (gimg && ldgi < h->W)) return fail(h, BSF_EINVAL, "leading dimension < W");
+    return backward_d2(h, gout, ldg, cov, cov_kind, gimg, ldgi, gcov);
   }
   if (!gout || !cov || !gimg) return fail(h, BSF_EINVAL, "NULL gout, cov or gimg");
   if (ldg < h->W || ldgi < h->W) return fail(h, BSF_EINVAL, "leading dimension < W");

@@ -17,6 +17,151 @@ cudaError_t bsf_launch_stencil_d2_u128(int n, int mode, const void* S, long long
 
 namespace {
 
+using namespace bsf_d2;
+
+// qg for the continuous-step adjoint: 118 - ceil(log2 max|gout|) in [0, 126]
+// (exact modulo 2^128 with 2^8 of headroom; 2^126 is still a float32).
+__device__ __forceinline__ int grad_q128(unsigned mbits) {
+  const unsigned E = (mbits >> 23) & 0xffu, M = mbits & 0x7fffffu;
+  int c;
+  if (E == 0 || E == 0xffu) c = E == 0 && M != 0 ? -126 : 0;
+  else c = (int)E - 127 + (M != 0 ? 1 : 0);
+  const int q = 118 - c;
+  return q < 0 ? 0 : (q > 126 ? 126 : q);
+}
+
+// 128-bit atomic add from two 64-bit ones: the low word's old value tells
+// this thread whether its addition carried, and the high word receives the
+// high part plus that carry.  The low word then holds the low 64 bits of the
+// sum and the high word every carry out of it, so the pair is the exact sum
+// modulo 2^128 whatever the order of the additions.
+__device__ __forceinline__ void atomic_add_u128(u128* p, u128 v) {
+  unsigned long long* q = reinterpret_cast<unsigned long long*>(p);
+  const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+  const unsigned long long old = atomicAdd(q, lo);
+  const unsigned long long h = hi + ((old + lo < old) ? 1ull : 0ull);
+  if (h) atomicAdd(q + 1, h);
+}
+
+__device__ __forceinline__ u128 mul_signed(u128 x, int v) {
+  return v >= 0 ? mul_small(x, (unsigned)v) : (u128)0 - mul_small(x, (unsigned)(-v));
+}
+
+// Interpolation weights of one direction (see the stencil): n = 2:
+// 1024 - th, th, -2048, th, 1024 - th; n = 1: 1024 - th, th, -th, th - 1024.
+template <int NF> __device__ __forceinline__ int tap_weight(unsigned th, int i) {
+  const int t = (int)th;
+  if (NF == 2) return i == 0 || i == 4 ? 1024 - t : (i == 2 ? -2048 : t);
+  return i == 0 ? 1024 - t : (i == 1 ? t : (i == 2 ? -t : t - 1024));
+}
+
+// Adjoint of the continuous-step taps: each pixel adds g(p) times the
+// product of its four interpolation weights at each of its samples, g(p) =
+// RNE(RN32(RN32(gout 2^qg) / RN32(M))) the quantised normalised weight.
+template <int NF>
+__global__ void __launch_bounds__(128)
+k_scatter_d2(u128* __restrict__ G, long long pitch, int R, const float* __restrict__ cov, int kind,
+             const float* __restrict__ gout, long long ldg, int H, int W, DevStatus* st) {
+  using P = Pattern<NF>;
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= W || y >= H) return;
+  const long long HW = (long long)H * W, i = (long long)y * W + x;
+  float C11, C12, C22;
+  load_cov(cov, kind, HW, i, C11, C12, C22);
+  int Hq[4], flags, reach;
+  float lam[4];
+  pixel_steps_d2(C11, C12, C22, NF, R, Hq, lam, flags, reach);
+  u128 M = 1;
+  for (int k = 0; k < 4; ++k) M *= (u128)d2_mass(Hq[k], NF);
+  const int qg = grad_q128(st->max_absg_bits);
+  const float xg = __fmul_rn(gout[(long long)y * ldg + x], bsf_pow2_f32(qg));  // exact scaling
+  bool ok;
+  const u128 g = bsf_quantize_f32<u128>(__fdiv_rn(xg, bsf_rn32_u(M)), 0, ok);
+  if (!ok) bsf_set_error(st, BSF_EOVERFLOW);
+  if (g == 0) return;
+  const int p32 = (int)pitch;
+  const int estep[4] = {1, p32 + 1, p32, p32 - 1};
+  int a0[4];
+  unsigned th[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int Q0 = NF == 2 ? 2 * Hq[k] - 1024 : Hq[k] - 512;
+    a0[k] = Q0 >> 10;
+    th[k] = (unsigned)(Q0 & 1023);
+  }
+  const int base = (y + R) * p32 + (x + R);
+#pragma unroll 1
+  for (int i1 = 0; i1 < P::NP; ++i1) {
+    const int w1 = tap_weight<NF>(th[0], i1);
+    if (w1 == 0) continue;
+    const u128 c1 = mul_signed(g, w1);
+    const int b1 = base + P::pos(a0[0], i1) * estep[0];
+#pragma unroll 1
+    for (int i2 = 0; i2 < P::NP; ++i2) {
+      const int w2 = tap_weight<NF>(th[1], i2);
+      if (w2 == 0) continue;
+      const u128 c2 = mul_signed(c1, w2);
+      const int b2 = b1 + P::pos(a0[1], i2) * estep[1];
+#pragma unroll
+      for (int i3 = 0; i3 < P::NP; ++i3) {
+        const int w3 = tap_weight<NF>(th[2], i3);
+        if (w3 == 0) continue;
+        const u128 c3 = mul_signed(c2, w3);
+        const int b3 = b2 + P::pos(a0[2], i3) * estep[2];
+#pragma unroll
+        for (int i4 = 0; i4 < P::NP; ++i4) {
+          const int w4 = tap_weight<NF>(th[3], i4);
+          if (w4 == 0) continue;
+          atomic_add_u128(G + b3 + P::pos(a0[3], i4) * estep[3], mul_signed(c3, w4));
+        }
+      }
+    }
+  }
+}
+
+// Extension fold of the 128-bit adjoint sums: columns, then rows with the
+// final rounding RN32(acc) 2^-qg.
+template <typename F>
+__device__ __forceinline__ void for_preimages128(int i, int N, int R, int boundary, F&& f) {
+  if (boundary == BSF_ZERO) {
+    f(i + R);
+  } else if (boundary == BSF_REPLICATE) {
+    const int lo = i == 0 ? -R : i, hi = i == N - 1 ? N - 1 + R : i;
+    for (int z = lo; z <= hi; ++z) f(z + R);
+  } else {
+    const int P2 = 2 * N;
+    for (int fam = 0; fam < 2; ++fam) {
+      const int b = fam == 0 ? i : P2 - 1 - i;
+      int z = b - ((b + R + P2 - 1) / P2) * P2;
+      if (z < -R) z += P2;
+      for (; z < N + R; z += P2) f(z + R);
+    }
+  }
+}
+
+__global__ void k_fold_x128(const u128* __restrict__ G, long long pitch, int Hp, int W, int R,
+                            int boundary, u128* __restrict__ Gx) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int yr = blockIdx.y;
+  if (x >= W || yr >= Hp) return;
+  const u128* row = G + (long long)yr * pitch;
+  u128 acc = 0;
+  for_preimages128(x, W, R, boundary, [&](int xp) { acc += bsf_load(row + xp); });
+  Gx[(long long)yr * W + x] = acc;
+}
+
+__global__ void k_fold_y_out128(const u128* __restrict__ Gx, int H, int W, int R, int boundary,
+                                float* __restrict__ gimg, long long ldo, const DevStatus* st) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= W || y >= H) return;
+  u128 acc = 0;
+  for_preimages128(y, H, R, boundary, [&](int yp) { acc += bsf_load(Gx + (long long)yp * W + x); });
+  const int qg = grad_q128(st->max_absg_bits);
+  gimg[(long long)y * ldo + x] = __fmul_rn(bsf_rn32((i128)acc), bsf_pow2_f32(-qg));
+}
+
 __global__ void k_jacobian_vjp(const float* __restrict__ gout, long long ldg,
                                const float* __restrict__ jac, long long ldj, float* __restrict__ gcov,
                                int H, int W) {
@@ -55,5 +200,29 @@ cudaError_t bsf_launch_jacobian_vjp(const float* gout, long long ldg, const floa
   long long blocks = ((long long)H * W + threads - 1) / threads;
   if (blocks > 152LL * 16) blocks = 152LL * 16;
   k_jacobian_vjp<<<(int)blocks, threads, 0, s>>>(gout, ldg, jac, ldj, gcov, H, W);
+  return cudaGetLastError();
+}
+
+cudaError_t bsf_launch_scatter_d2(int n, void* G, long long pitch, int R, const float* cov,
+                                  int cov_kind, const float* gout, long long ldg, int H, int W,
+                                  DevStatus* st, cudaStream_t s) {
+  const dim3 block(32, 4), grid((W + 31) / 32, (H + 3) / 4);
+  if (n == 1)
+    k_scatter_d2<1><<<grid, block, 0, s>>>((u128*)G, pitch, R, cov, cov_kind, gout, ldg, H, W, st);
+  else if (n == 2)
+    k_scatter_d2<2><<<grid, block, 0, s>>>((u128*)G, pitch, R, cov, cov_kind, gout, ldg, H, W, st);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t bsf_launch_fold128(const void* G, long long pitch, int Hp, int H, int W, int R,
+                               int boundary, void* Gx, float* gimg, long long ldo, const DevStatus* st,
+                               cudaStream_t s) {
+  dim3 blk(128);
+  k_fold_x128<<<dim3((W + 127) / 128, Hp), blk, 0, s>>>((const u128*)G, pitch, Hp, W, R, boundary,
+                                                         (u128*)Gx);
+  k_fold_y_out128<<<dim3((W + 127) / 128, H), blk, 0, s>>>((const u128*)Gx, H, W, R, boundary, gimg,
+                                                            ldo, st);
   return cudaGetLastError();
 }

@@ -127,6 +127,15 @@ cudaError_t bsf_launch_stencil_d2(int prec, int n, int mode, const void* S, long
                                   int q, void* out, int out_dtype, long long ldo, float* jac,
                                   long long ldj, long long jac_plane, const float* gout,
                                   long long ldg, DevStatus* st, cudaStream_t s);
+// Image-gradient adjoint of the continuous-step taps into G (uint128, [Hp][pitch],
+// zeroed by the caller), and the 128-bit extension fold into gimg; both take
+// qg from the device maximum of |gout| (bsf_launch_gabsmax).
+cudaError_t bsf_launch_scatter_d2(int n, void* G, long long pitch, int R, const float* cov,
+                                  int cov_kind, const float* gout, long long ldg, int H, int W,
+                                  DevStatus* st, cudaStream_t s);
+cudaError_t bsf_launch_fold128(const void* G, long long pitch, int Hp, int H, int W, int R,
+                               int boundary, void* Gx, float* gimg, long long ldo, const DevStatus* st,
+                               cudaStream_t s);
 // gcov[c][y][x] = gout[y][x] * jac[c][y][x] (jac planes H * ldj apart; gcov [3][H][W]).
 cudaError_t bsf_launch_jacobian_vjp(const float* gout, long long ldg, const float* jac,
                                     long long ldj, float* gcov, int H, int W, cudaStream_t s);

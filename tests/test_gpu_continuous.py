@@ -228,11 +228,14 @@ def test_argument_errors():
     f = bsf.BoxSplineFilter(H, W, 2, precision=2, step_rule=0)
     with pytest.raises(bsf.BsfError):
         f.filter_jacobian(img, cov)
-    f = bsf.BoxSplineFilter(H, W, 2, precision=2, step_rule=2)
+    # the image gradient of continuous steps runs on uint128 contexts only
+    f = bsf.BoxSplineFilter(H, W, 2, precision=1, frac_bits=4, step_rule=2)
     f.filter(img, cov)
     gout = torch.zeros((H, W), dtype=torch.float32, device="cuda")
     with pytest.raises(bsf.BsfError):
         f.backward(gout, cov, want_gimg=True, want_gcov=True)
+    with pytest.raises(bsf.BsfError):
+        f.backward(gout, cov, want_gimg=False, want_gcov=False)
 
 
 def test_log_parameter_field_in_the_integer_step_filter():
@@ -250,3 +253,55 @@ def test_log_parameter_field_in_the_integer_step_filter():
         outs.append(f.filter(img, torch.from_numpy(np.ascontiguousarray(field)).cuda()).cpu().numpy())
         assert f.status() == 0
     np.testing.assert_array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("n,boundary,kind", [(2, 2, 1), (2, 0, 0), (1, 1, 1), (2, 1, 0)])
+def test_image_gradient_bit_exact(n, boundary, kind):
+    import torch
+    from oracle.rounding import rn_f32_int
+    H, W = 22, 45
+    planes = _fields(H, W, seed=15 + n, kind=kind)
+    gout = wl.uniform_image(H, W, seed=16, lo=-1, hi=1).astype(np.float32)
+    f = _filter(H, W, n, boundary, -1, 2, kind)
+    tc = torch.from_numpy(planes).cuda()
+    f.plan(tc)
+    gimg, _ = f.backward(torch.from_numpy(gout).cuda(), tc, want_gimg=True, want_gcov=False)
+    torch.cuda.synchronize()
+    assert f.status() == 0
+    R = f.info().R
+    qg = cn.grad_frac_bits_d2(float(np.abs(gout).max()))
+    pix = [(y, x) for y in range(H) for x in range(W)]
+    recs = cn.filter_d2_direct(np.zeros((H, W), dtype=np.int64), planes, n, boundary, pix, kind=kind, R=R)
+    gq = {p: cn.quantize_weight_d2(float(gout[p]), recs[p]["M"], qg) for p in pix}
+    acc = cn.adjoint_d2_acc(gq, planes, n, boundary, (H, W), kind=kind, R=R)
+    ref = np.array([[np.float32(rn_f32_int(acc[y, x]) * np.float32(2.0 ** -qg)) for x in range(W)]
+                    for y in range(H)], dtype=np.float32)
+    np.testing.assert_array_equal(gimg.cpu().numpy(), ref)
+
+
+def test_autograd_image_and_parameter_gradients():
+    import torch
+    from paper_1109_5114_gb300 import bsf
+    H, W = 30, 41
+    img = torch.from_numpy(wl.blob_image(H, W, seed=4, n_blobs=9, sigma_range=(2.0, 6.0))).cuda()
+    planes = torch.from_numpy(_fields(H, W, seed=17, kind=1)).cuda()
+    target = torch.from_numpy(wl.uniform_image(H, W, seed=6, lo=0, hi=1).astype(np.float32)).cuda()
+    f = _filter(H, W, 2, kernels.SYMMETRIC, -1, 2, 1)
+    f.plan(planes)
+    x = img.clone().requires_grad_(True)
+    p = planes.clone().requires_grad_(True)
+    out = bsf.box_spline_filter(x, p, f)
+    loss = 0.5 * ((out - target) ** 2).sum()
+    loss.backward()
+    gout = (out.detach() - target).contiguous()
+    gimg, _ = f.backward(gout, planes, want_gimg=True, want_gcov=False)
+    _, J = f.filter_jacobian(img, planes)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(x.grad.cpu().numpy(), gimg.cpu().numpy())
+    np.testing.assert_array_equal(p.grad.cpu().numpy(), (gout[None] * J).cpu().numpy())
+    # the image gradient is the adjoint: <gout, A d> = <A^T gout, d> for a probe d
+    d = torch.from_numpy(wl.uniform_image(H, W, seed=8, lo=-1, hi=1).astype(np.float32)).cuda()
+    Ad = f.filter(d, planes)
+    lhs = float((gout.double() * Ad.double()).sum())
+    rhs = float((gimg.double() * d.double()).sum())
+    assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), 1e-3)
