@@ -248,3 +248,33 @@ def test_output_rule_and_orders_above_two_rejected():
     assert abs(Fraction(float(val)) - exact) <= abs(exact) * Fraction(1, 1 << 50)
     with pytest.raises(ValueError):
         cn.line_taps(1024, 3)
+
+
+@pytest.mark.parametrize("n", [1, 2])
+def test_image_adjoint_identity(n):
+    # <A f, g> = <f, A^T g> exactly, for integer f and integer weights g,
+    # where A f is the definition's sum and A^T g the adjoint's
+    H, W = 13, 11
+    f = synth.random_integer_image(H, W, seed=2, lo=-20, hi=20).astype(np.int64)
+    cov = synth.random_cov_field(H, W, seed=3, sigma_range=(0.4, 1.8), rho_range=(1.0, 3.0))
+    rng = np.random.default_rng(n)
+    for b in (kernels.ZERO, kernels.REPLICATE, kernels.SYMMETRIC):
+        gq = {(y, x): int(rng.integers(-50, 50)) for y in range(H) for x in range(W)}
+        fwd = cn.filter_d2_direct(f, cov, n, b, list(gq))
+        lhs = sum(gq[p] * fwd[p]["acc"] for p in gq)
+        adj = cn.adjoint_d2_acc(gq, cov, n, b, (H, W))
+        rhs = sum(int(f[y, x]) * adj[y, x] for y in range(H) for x in range(W))
+        assert lhs == rhs
+
+
+def test_image_gradient_scale_rule():
+    for m in (1e-30, 2.0 ** -7, 0.37, 0.5, 1.0, 3.0, 4.0, 1e6, 3e38):
+        qg = cn.grad_frac_bits_d2(m)
+        mf = float(np.float32(m))
+        if 0 < qg < 126:
+            assert 2.0 ** 117 < mf * 2.0 ** qg <= 2.0 ** 118
+        assert 0 <= qg <= 126
+    # weights: the float32 quotient, rounded half to even
+    assert cn.quantize_weight_d2(1.5, 1, 0) == 2 and cn.quantize_weight_d2(2.5, 1, 0) == 2
+    assert cn.quantize_weight_d2(-0.37, 2 ** 50, 100) == int(round(float(
+        np.float32(np.float32(-0.37 * 2.0 ** 100) / np.float32(2.0 ** 50)))))
