@@ -31,9 +31,16 @@ namespace {
 
 // ---------------------------------------------------------------------------
 // d1 with fused extension + quantisation: one block of kRowThreads per padded
-// row; each thread owns V consecutive elements of a chunk of kRowThreads * V.
-// A fold is a thread-local scan, a warp shuffle scan of the thread totals, a
-// block scan of the warp totals through shared memory, and a carry per row.
+// row.  A pass covers kRowThreads * V elements: warp w owns a segment of
+// 32 V, lane l its V consecutive elements.  Each fold is a lane-local scan
+// and a warp shuffle scan of the lane totals, so a warp holds the n-fold
+// running sums of its segment as if the row started there; the segment's
+// carry-in state (the fold values just before it) then enters in closed form:
+// with carry-in c_1..c_n, the n-th fold at position i of a segment is the
+// local value plus sum_k c_k C(i + n - k, n - k), and the state at its end
+// is s_f + sum_{k<=f} c_k C(m - 1 + f - k, f - k) for a segment of m elements
+// whose own end state is s.  One barrier per pass exchanges the warps' end
+// states.
 // ---------------------------------------------------------------------------
 constexpr int kRowThreads = 256;
 
@@ -55,13 +62,25 @@ __device__ __forceinline__ T quantize_one(In fv, int q, float scale_f, bool& ok,
     ax = (float)fv * scale_f;
     return (T)fv << q;
   } else if constexpr (sizeof(In) == 4) {
-    ax = fabsf(fv) * scale_f;  // exact unless it overflows to inf (then ok is false too)
-    return bsf_quantize_f32<T>(fv, q, ok);
+    // f 2^q is exact in float32 (a power-of-two scaling of a finite value
+    // that stays finite); below 2^63 the conversion rounds it half to even
+    const float x = __fmul_rn(fv, scale_f);
+    ax = fabsf(x);
+    if (ax < 9223372036854775808.f) {
+      ok = true;
+      return (T)(long long)__float2ll_rn(x);
+    }
+    return bsf_quantize_f32<T>(fv, q, ok);  // large or non-finite: integer path
   } else {
     const double xq = (double)fv * (double)scale_f;
     ax = __double2float_ru(fabs(xq));
     return bsf_round_to_elem<T>(xq, ok);
   }
+}
+
+// C(a, j) for j = 0, 1, 2 (the folds n <= 3 need no more)
+__device__ __forceinline__ long long binom_small(long long a, int j) {
+  return j == 0 ? 1 : (j == 1 ? a : a * (a - 1) / 2);
 }
 
 template <typename T, int NF, typename In, int V>
@@ -70,22 +89,26 @@ __device__ __forceinline__ void scan_rows_body(const In* __restrict__ img, long 
                                                int q, T* __restrict__ S, long long pitch, int Hp,
                                                int Wp, DevStatus* st, int yp) {
   constexpr int NW = kRowThreads / 32;
-  __shared__ T s_warp[NF][NW];
+  constexpr int SEG = 32 * V;
+  constexpr int VP = V + 1;  // padded stride of the store transpose (fewer bank conflicts)
+  __shared__ T s_end[NW][NF];
+  __shared__ T s_tr[NW][32 * VP];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   bool yvalid;
   const int ys = bsf_map_index(row0 + yp - R, H, boundary, yvalid);  // row0: first row of a band
   const In* src = img + (long long)ys * ld;
   T* row = S + (long long)yp * pitch;
-  T carry[NF];
+  T carry[NF];  // fold values just before the pass (uniform across the block)
 #pragma unroll
   for (int f = 0; f < NF; ++f) carry[f] = 0;
   float amax = 0.f;
   bool all_ok = true;
   for (int x0 = 0; x0 < Wp; x0 += kRowThreads * V) {
+    const int xl0 = x0 + wid * SEG + lane * V;  // this lane's first element
     T v[V];
 #pragma unroll
     for (int j = 0; j < V; ++j) {
-      const int xp = x0 + tid * V + j;
+      const int xp = xl0 + j;
       v[j] = 0;
       if (xp < Wp && yvalid) {
         bool xvalid;
@@ -99,6 +122,7 @@ __device__ __forceinline__ void scan_rows_body(const In* __restrict__ img, long 
         }
       }
     }
+    // the folds within the warp's segment (zero carry-in at its start)
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
 #pragma unroll
@@ -110,26 +134,69 @@ __device__ __forceinline__ void scan_rows_body(const In* __restrict__ img, long 
         const T t = bsf_shfl_up(incl, o);
         if (lane >= o) incl += t;
       }
-      if (lane == 31) s_warp[f][wid] = incl;
-      __syncthreads();
-      T wpre = 0, btot = 0;
+      const T excl = incl - tot;
 #pragma unroll
-      for (int w = 0; w < NW; ++w) {
-        const T t = s_warp[f][w];
-        if (w < wid) wpre += t;
-        btot += t;
+      for (int j = 0; j < V; ++j) v[j] += excl;
+      if (lane == 31) s_end[wid][f] = incl;  // fold f at the segment's last element
+    }
+    __syncthreads();
+    // carry-in state of this warp's segment, and the block's state after the pass
+    T cin[NF], cnext[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) cnext[f] = carry[f];
+    for (int w = 0; w < NW; ++w) {
+      if (w == wid) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) cin[f] = cnext[f];
       }
-      const T add = carry[f] + wpre + (incl - tot);
+      T e[NF];
 #pragma unroll
-      for (int j = 0; j < V; ++j) v[j] += add;
-      carry[f] += btot;
-    }
-    __syncthreads();  // s_warp is rewritten by the next chunk
+      for (int f = 0; f < NF; ++f) {
+        e[f] = s_end[w][f];
 #pragma unroll
-    for (int j = 0; j < V; ++j) {
-      const int xp = x0 + tid * V + j;
-      if (xp < Wp) row[xp] = v[j];
+        for (int k = 0; k <= f; ++k) e[f] += bsf_mul_int(cnext[k], binom_small(SEG - 1 + f - k, f - k));
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) cnext[f] = e[f];
     }
+    // n-th fold += a(i) = sum_k cin_k C(i + n - 1 - k, n - 1 - k), i = position in
+    // the segment; a is a polynomial of degree n - 1 in i, stepped by its forward
+    // differences: a(i+1) - a(i) = sum_{k<n-1} cin_k C(i + n - 1 - k, n - 2 - k),
+    // whose own difference is cin_0 (n = 3)
+    {
+      const long long i0 = (long long)lane * V;
+      T a = cin[NF - 1];
+#pragma unroll
+      for (int k = 0; k < NF - 1; ++k) a += bsf_mul_int(cin[k], binom_small(i0 + NF - 1 - k, NF - 1 - k));
+      T d = 0;
+      if constexpr (NF >= 2) {
+        d = cin[NF - 2];
+        if constexpr (NF == 3) d += bsf_mul_int(cin[0], i0 + 2);
+      }
+#pragma unroll
+      for (int j = 0; j < V; ++j) {
+        v[j] += a;
+        if constexpr (NF >= 2) {
+          a += d;
+          if constexpr (NF == 3) d += cin[0];
+        }
+      }
+    }
+    // store through shared memory so that each store instruction writes 32
+    // consecutive elements of the row
+#pragma unroll
+    for (int j = 0; j < V; ++j) s_tr[wid][lane * VP + j] = v[j];
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < V; ++r) {
+      const int e = r * 32 + lane;
+      const int xp = x0 + wid * SEG + e;
+      if (xp < Wp) row[xp] = s_tr[wid][(e / V) * VP + e % V];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int f = 0; f < NF; ++f) carry[f] = cnext[f];
+    __syncthreads();  // s_end is rewritten by the next pass
   }
   for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   const bool bad = __any_sync(0xffffffffu, !all_ok);
@@ -523,14 +590,21 @@ cudaError_t launch_rows_v(const void* img, int dtype, long long ld, int H, int W
   return cudaGetLastError();
 }
 
-// V consecutive elements per thread (measured: longer per-thread runs lengthen
-// the serial dependence of the local scans more than they save in barriers)
+// V consecutive elements per thread, chosen so that one pass of 256 V
+// elements covers most of a padded row without leaving warps idle
 template <typename T, int NF>
 cudaError_t launch_rows_t(const void* img, int dtype, long long ld, int H, int W, int R, int row0,
                           int boundary, int q, T* S, long long pitch, int Hp, int Wp,
                           DevStatus* st, cudaStream_t s) {
-  constexpr int V0 = sizeof(T) == 8 ? 4 : 2;
-  return launch_rows_v<T, NF, V0>(img, dtype, ld, H, W, R, row0, boundary, q, S, pitch, Hp, Wp, st, s);
+  if (Wp <= kRowThreads * 4)
+    return launch_rows_v<T, NF, 4>(img, dtype, ld, H, W, R, row0, boundary, q, S, pitch, Hp, Wp, st, s);
+  if constexpr (sizeof(T) > 8) {  // 16-byte elements: V = 9 keeps the transpose under 48 KB
+    return launch_rows_v<T, NF, 9>(img, dtype, ld, H, W, R, row0, boundary, q, S, pitch, Hp, Wp, st, s);
+  } else {
+    if (Wp <= kRowThreads * 9)
+      return launch_rows_v<T, NF, 9>(img, dtype, ld, H, W, R, row0, boundary, q, S, pitch, Hp, Wp, st, s);
+    return launch_rows_v<T, NF, 12>(img, dtype, ld, H, W, R, row0, boundary, q, S, pitch, Hp, Wp, st, s);
+  }
 }
 
 template <typename T, int NF, int SKEW, bool REV>

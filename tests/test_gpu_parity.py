@@ -43,6 +43,23 @@ def test_steps_bit_exact(n, rule):
     assert g["info"].clamp_count == int((fl & params.CLAMP_FLAG != 0).sum())
 
 
+@pytest.mark.parametrize("n,prec,W", [(2, 1, 3500), (3, 2, 2300), (1, 1, 6200), (2, 2, 4200)])
+def test_running_sums_of_rows_longer_than_one_pass(n, prec, W):
+    # a block covers 3072 (uint64) or 2048 (uint128) elements of a padded row
+    # per pass; longer rows carry the n-fold state from pass to pass
+    H = 5
+    img = wl.random_integer_image(H, W, seed=n + W, lo=-500, hi=500).astype(np.float32)
+    cov = _cov(H, W, seed=n, smax=1.5)
+    g = run_gpu(img, cov, n, 2, q=3, precision=prec, want_S=True)
+    bits = 64 if prec == 1 else 128
+    S = oracle_S(img, n, 2, 3, g["R"], bits)
+    if bits == 64:
+        np.testing.assert_array_equal(g["S"], S)
+    else:
+        np.testing.assert_array_equal(g["S"][0], S.lo)
+        np.testing.assert_array_equal(g["S"][1], S.hi)
+
+
 @pytest.mark.parametrize("n,boundary,prec", list(itertools.product([1, 2, 3], [0, 1, 2], [1, 2])))
 def test_running_sums_bit_exact(n, boundary, prec):
     H, W = 29, 70   # several warps per row, ragged chunks
