@@ -218,6 +218,13 @@ k_scan_rows(const In* __restrict__ img, long long ld, int H, int W, int R, int r
 // ---------------------------------------------------------------------------
 // d3 / d2 / d4 in skewed coordinates
 // ---------------------------------------------------------------------------
+// State after m more rows of zeros: the folds keep adding their lower folds.
+template <typename T, int NF>
+__device__ __forceinline__ void zero_rows_transfer(T* s, long long m) {
+  if constexpr (NF >= 3) s[2] += bsf_mul_int(s[1], m) + bsf_mul_int(s[0], m * (m + 1) / 2);
+  if constexpr (NF >= 2) s[1] += bsf_mul_int(s[0], m);
+}
+
 template <typename T, int NF, int SKEW, bool REV>
 __device__ __forceinline__ void vscan_agg_body(const T* __restrict__ S, long long pitch, int Hp,
                                                int Wp, int umin, int Nu, int ch,
@@ -226,23 +233,36 @@ __device__ __forceinline__ void vscan_agg_body(const T* __restrict__ S, long lon
   if (ui >= Nu) return;
   const int u = umin + ui;
   const int y0 = c * ch, y1 = min(y0 + ch, Hp);
+  // in scan order yl the line sits at column x = A + B yl; only the rows with
+  // 0 <= x < Wp hold data (the rest of the line is zero)
+  const int A = REV ? u + SKEW * (Hp - 1) : u, B = REV ? -SKEW : SKEW;
+  int lo = y0, hi = y1;
+  if (B == 0) {
+    if (A < 0 || A >= Wp) hi = lo;
+  } else if (B == 1) {
+    lo = max(lo, -A);
+    hi = min(hi, Wp - A);
+  } else {
+    lo = max(lo, A - Wp + 1);
+    hi = min(hi, A + 1);
+  }
   T s[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) s[f] = 0;
+  if (lo < hi) {
 #pragma unroll 8
-  for (int yl = y0; yl < y1; ++yl) {
-    const int y = REV ? Hp - 1 - yl : yl;  // REV: suffix sums, rows bottom-up
-    const int x = u + SKEW * y;
-    T v = 0;
-    if (x >= 0 && x < Wp) v = S[(long long)y * pitch + x];
-    s[0] += v;
+    for (int yl = lo; yl < hi; ++yl) {
+      const int y = REV ? Hp - 1 - yl : yl;  // REV: suffix sums, rows bottom-up
+      const T v = S[(long long)y * pitch + (A + B * yl)];
+      s[0] += v;
 #pragma unroll
-    for (int f = 1; f < NF; ++f) s[f] += s[f - 1];
+      for (int f = 1; f < NF; ++f) s[f] += s[f - 1];
+    }
+    zero_rows_transfer<T, NF>(s, y1 - hi);  // leading zero rows leave the state at zero
   }
 #pragma unroll
   for (int f = 0; f < NF; ++f) agg[((long long)c * NF + f) * Nu + ui] = s[f];
 }
-
 template <typename T, int NF, int SKEW, bool REV>
 __global__ void __launch_bounds__(128)
 k_vscan_agg(const T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, int Nu, int ch,
@@ -277,31 +297,42 @@ __device__ __forceinline__ void vscan_apply_body(T* __restrict__ S, long long pi
   if (ui >= Nu) return;
   const int u = umin + ui;
   const int y0 = c * ch, y1 = min(y0 + ch, Hp);
-  // skip lines that do not cross this chunk
-  const int ya = REV ? Hp - 1 - y0 : y0, yb = REV ? Hp - y1 : y1 - 1;
-  const int xa = u + SKEW * ya, xb = u + SKEW * yb;
-  if (max(xa, xb) < 0 || min(xa, xb) >= Wp) return;
+  // the rows [glo, ghi) (scan order) where the line holds data: column x = A + B yl
+  const int A = REV ? u + SKEW * (Hp - 1) : u, B = REV ? -SKEW : SKEW;
+  int glo = 0, ghi = Hp;
+  if (B == 0) {
+    if (A < 0 || A >= Wp) return;
+  } else if (B == 1) {
+    glo = max(0, -A);
+    ghi = min(Hp, Wp - A);
+  } else {
+    glo = max(0, A - Wp + 1);
+    ghi = min(Hp, A + 1);
+  }
+  const int lo = max(y0, glo), hi = min(y1, ghi);
+  if (lo >= hi) return;  // nothing of this line in this chunk
+  // carried-in state: the line is zero before its first chunk with data
   T s[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) s[f] = 0;
 #pragma unroll 4
-  for (int j = 0; j < c; ++j) {
+  for (int j = glo / ch; j < c; ++j) {
     T a[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) a[f] = agg[((long long)j * NF + f) * Nu + ui];
     tp_combine<T, NF>(s, a, ch);  // every earlier chunk is full
   }
+  zero_rows_transfer<T, NF>(s, lo - y0);  // empty rows at the top of this chunk
   const int p32 = (int)pitch;
-  for (int yb0 = y0; yb0 < y1; yb0 += kApplyBatch) {
+  for (int yb0 = lo; yb0 < hi; yb0 += kApplyBatch) {
     T v[kApplyBatch];
     int idx[kApplyBatch];
 #pragma unroll
     for (int r = 0; r < kApplyBatch; ++r) {
       const int yl = yb0 + r;
       const int y = REV ? Hp - 1 - yl : yl;
-      const int x = u + SKEW * y;
-      const bool in = yl < y1 && x >= 0 && x < Wp;
-      idx[r] = in ? y * p32 + x : -1;
+      const bool in = yl < hi;
+      idx[r] = in ? y * p32 + (A + B * yl) : -1;
       v[r] = in ? S[idx[r]] : (T)0;
     }
 #pragma unroll
@@ -313,7 +344,6 @@ __device__ __forceinline__ void vscan_apply_body(T* __restrict__ S, long long pi
     }
   }
 }
-
 template <typename T, int NF, int SKEW, bool REV>
 __global__ void __launch_bounds__(128)
 k_vscan_apply(T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, int Nu, int ch,
