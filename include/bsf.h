@@ -216,6 +216,21 @@ int bsf_preintegrate(bsf_t h, const void* img, int dtype, long long ld);
 int bsf_filter(bsf_t h, const void* img, int dtype, long long ld,
                const float* cov, int cov_kind, void* out, int out_dtype, long long ldo);
 
+/* Whole forward filter on HOST buffers, overlapping the transfers with the
+ * work: the image is uploaded first and pre-integrated as soon as it has
+ * arrived, while the covariance planes follow in eight row bands on a second
+ * stream; the stencil runs band by band as each band's field arrives, and
+ * each finished band of the output goes back on a third stream while the
+ * next is computed.  img: host [H][ld] of dtype; cov: host [3][H][W] float32
+ * of cov_kind; out: host [H][ldo] of out_dtype.  Use page-locked host memory
+ * (cudaHostAlloc / torch pin_memory) for the copies to overlap; pageable
+ * memory works but serialises them.  The library keeps device copies of the
+ * inputs and output (allocated on first use, synchronously).  Synchronous:
+ * returns when out holds the result.  The first call plans (waits for the
+ * whole field).  Errors: as bsf_filter. */
+int bsf_filter_host(bsf_t h, const void* img, int dtype, long long ld, const float* cov, int cov_kind,
+                    void* out, int out_dtype, long long ldo);
+
 /* Forward filter of the band of rows [y0, y1) only (0 <= y0 < y1 <= H).
  * img and cov are the whole image and field ([H][ld], [3][H][W]); out
  * receives the band's rows ([y1-y0][ldo], row 0 = image row y0).  The

@@ -87,6 +87,8 @@ bsf_filter_backward_rows = _fn("bsf_filter_backward_rows", c_int, bsf_t, c_void_
 bsf_grad_frac_bits = _fn("bsf_grad_frac_bits", c_int, c_double)
 bsf_grad_absmax_rows = _fn("bsf_grad_absmax_rows", c_int, bsf_t, c_void_p, c_ll, c_int, c_int,
                            ctypes.POINTER(ctypes.c_float))
+bsf_filter_host = _fn("bsf_filter_host", c_int, bsf_t, c_void_p, c_int, c_ll, c_void_p, c_int, c_void_p,
+                      c_int, c_ll)
 bsf_grad_finalize = _fn("bsf_grad_finalize", c_int, bsf_t, c_void_p, c_ll, c_int, c_int, c_void_p, c_ll)
 
 class bsf_image_desc(ctypes.Structure):
@@ -225,6 +227,23 @@ class BoxSplineFilter:
                             ctypes.c_void_p(cov.data_ptr()), self.cov_kind,
                             ctypes.c_void_p(out.data_ptr()), oc, out.stride(0))
         check(self._h, rc)
+        return out
+
+    def filter_host(self, img, cov, out=None):
+        """Forward filter from and to host (CPU) tensors, transfers overlapped
+        with the work (bsf_filter_host); pinned tensors for the overlap."""
+        import torch
+        self._stream()
+        H, W = self.H, self.W
+        assert not img.is_cuda and img.shape == (H, W) and img.stride(1) == 1
+        assert not cov.is_cuda and cov.dtype == torch.float32 and cov.shape == (3, H, W) and cov.is_contiguous()
+        if out is None:
+            out = torch.empty((H, W), dtype=torch.float32, pin_memory=True)
+        assert not out.is_cuda and out.stride(1) == 1
+        oc = BSF_F32 if out.dtype == torch.float32 else BSF_F64  # noqa: F821
+        check(self._h, bsf_filter_host(self._h, ctypes.c_void_p(img.data_ptr()), _dtype_code(img),
+                                       img.stride(0), ctypes.c_void_p(cov.data_ptr()), self.cov_kind,
+                                       ctypes.c_void_p(out.data_ptr()), oc, out.stride(0)))
         return out
 
     def filter_jacobian(self, img, cov, out=None, jac=None):

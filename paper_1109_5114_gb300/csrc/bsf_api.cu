@@ -56,6 +56,17 @@ struct bsf_ctx {
   int S_row0 = 0, S_rows = 0;        // image rows the held running sums cover
   char msg[512] = "ok";
 
+  // host-buffer entry (bsf_filter_host): device staging copies of the inputs
+  // and the output, one stream per copy direction, and the band events
+  static constexpr int kHostBands = 8;
+  void* hs_img = nullptr;
+  void* hs_cov = nullptr;
+  void* hs_out = nullptr;
+  size_t hs_img_bytes = 0, hs_cov_bytes = 0, hs_out_bytes = 0;
+  cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+  cudaEvent_t hev[2 * kHostBands + 1] = {};
+  bool hev_ready = false;
+
   // phase timing (bsf_set_profiling)
   static constexpr int kMaxRec = 4096;
   bool profiling = false;
@@ -364,6 +375,13 @@ void bsf_destroy(bsf_t h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   free_workspace(h);
+  if (h->hs_img) cudaFree(h->hs_img);
+  if (h->hs_cov) cudaFree(h->hs_cov);
+  if (h->hs_out) cudaFree(h->hs_out);
+  if (h->hev_ready)
+    for (auto& e : h->hev) cudaEventDestroy(e);
+  if (h->s_h2d) cudaStreamDestroy(h->s_h2d);
+  if (h->s_d2h) cudaStreamDestroy(h->s_d2h);
   if (h->ev) {
     for (int i = 0; i < 2 * bsf_ctx::kMaxRec; ++i) cudaEventDestroy(h->ev[i]);
     delete[] h->ev;
@@ -501,6 +519,110 @@ int bsf_filter(bsf_t h, const void* img, int dtype, long long ld, const float* c
                void* out, int out_dtype, long long ldo) {
   if (!h) return BSF_EINVAL;
   return filter_impl(h, img, dtype, ld, cov, cov_kind, out, out_dtype, ldo, 0, h->H);
+}
+
+// (Re)allocate a device staging buffer of at least `bytes`.
+static int ensure_staging(bsf_t h, void*& buf, size_t& have, size_t bytes) {
+  if (have >= bytes) return BSF_OK;
+  BSF_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (buf) cudaFree(buf);
+  buf = nullptr;
+  have = 0;
+  BSF_CUDA(h, cudaMalloc(&buf, bytes));
+  have = bytes;
+  return BSF_OK;
+}
+
+// Output rows [y0, y0 + rows) from the whole image's running sums (the
+// stencil reads S from row y0 of the padded domain on).
+static cudaError_t stencil_band(bsf_t h, const float* cov, int cov_kind, int y0, int rows, void* out,
+                                int out_dtype, long long ldo) {
+  const void* S = static_cast<const char*>(h->S) + (size_t)y0 * h->pitch * h->elem;
+  if (h->step_rule == BSF_STEP_D2)
+    return bsf_launch_stencil_d2(h->precision, h->n, 0, S, h->pitch, h->R, cov, cov_kind, h->H, h->W,
+                                 y0, rows, h->S_q, out, out_dtype, ldo, nullptr, 0, 0, nullptr, 0,
+                                 h->st, h->stream);
+  return bsf_launch_stencil_d1(h->precision, h->n, S, h->pitch, h->R, cov, cov_kind, h->step_rule,
+                               h->H, h->W, y0, rows, h->S_q, out, out_dtype, ldo, h->st, h->stream);
+}
+
+int bsf_filter_host(bsf_t h, const void* img, int dtype, long long ld, const float* cov, int cov_kind,
+                    void* out, int out_dtype, long long ldo) {
+  if (!h) return BSF_EINVAL;
+  if (!img || !cov || !out) return fail(h, BSF_EINVAL, "NULL img, cov or out");
+  if (dtype != BSF_U8 && dtype != BSF_F32 && dtype != BSF_F64)
+    return fail(h, BSF_EINVAL, "bad image dtype %d", dtype);
+  if (out_dtype != BSF_F32 && out_dtype != BSF_F64) return fail(h, BSF_EINVAL, "bad out dtype %d", out_dtype);
+  if (ld < h->W || ldo < h->W) return fail(h, BSF_EINVAL, "leading dimension < W");
+  int rc = check_cov_kind(h, cov_kind);
+  if (rc) return rc;
+  if (h->step_rule == BSF_STEP_D2 && (rc = check_d2(h))) return rc;
+  const int H = h->H, W = h->W;
+  const size_t HW = (size_t)H * W;
+  const size_t es = dtype == BSF_U8 ? 1 : (dtype == BSF_F32 ? 4 : 8), eo = out_dtype == BSF_F32 ? 4 : 8;
+  if ((rc = ensure_staging(h, h->hs_img, h->hs_img_bytes, HW * es))) return rc;
+  if ((rc = ensure_staging(h, h->hs_cov, h->hs_cov_bytes, 3 * HW * sizeof(float)))) return rc;
+  if ((rc = ensure_staging(h, h->hs_out, h->hs_out_bytes, HW * eo))) return rc;
+  if (!h->s_h2d) BSF_CUDA(h, cudaStreamCreateWithFlags(&h->s_h2d, cudaStreamNonBlocking));
+  if (!h->s_d2h) BSF_CUDA(h, cudaStreamCreateWithFlags(&h->s_d2h, cudaStreamNonBlocking));
+  if (!h->hev_ready) {
+    for (auto& e : h->hev) BSF_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    h->hev_ready = true;
+  }
+  const int K = H < bsf_ctx::kHostBands ? H : bsf_ctx::kHostBands;
+  cudaEvent_t ev_img = h->hev[0];
+  cudaEvent_t* ev_cov = h->hev + 1;
+  cudaEvent_t* ev_out = h->hev + 1 + bsf_ctx::kHostBands;
+  auto band = [&](int k, int& y0, int& rows) {
+    y0 = (int)((long long)H * k / K);
+    rows = (int)((long long)H * (k + 1) / K) - y0;
+  };
+  float* dcov = static_cast<float*>(h->hs_cov);
+  // the previous call's output copies must be done before the staging buffers are reused
+  BSF_CUDA(h, cudaStreamSynchronize(h->s_d2h));
+  // image, then the covariance planes band by band, on the upload stream
+  BSF_CUDA(h, cudaMemcpy2DAsync(h->hs_img, W * es, img, ld * es, W * es, H, cudaMemcpyHostToDevice,
+                                h->s_h2d));
+  BSF_CUDA(h, cudaEventRecord(ev_img, h->s_h2d));
+  for (int k = 0; k < K; ++k) {
+    int y0, rows;
+    band(k, y0, rows);
+    for (int c = 0; c < 3; ++c)
+      BSF_CUDA(h, cudaMemcpyAsync(dcov + c * HW + (size_t)y0 * W, cov + c * HW + (size_t)y0 * W,
+                                  (size_t)rows * W * sizeof(float), cudaMemcpyHostToDevice, h->s_h2d));
+    BSF_CUDA(h, cudaEventRecord(ev_cov[k], h->s_h2d));
+  }
+  // a plan (first call) needs the whole field
+  if (h->R < 0 || (h->frac_req < 0 && !h->planned)) {
+    BSF_CUDA(h, cudaStreamWaitEvent(h->stream, ev_cov[K - 1], 0));
+    if ((rc = run_steps(h, dcov, cov_kind, true))) return rc;
+  }
+  if ((rc = reset_counters(h, true, false))) return rc;
+  BSF_CUDA(h, cudaStreamWaitEvent(h->stream, ev_img, 0));
+  if ((rc = preintegrate_impl(h, h->hs_img, dtype, W, 0, H))) return rc;
+  for (int k = 0; k < K; ++k) {
+    int y0, rows;
+    band(k, y0, rows);
+    BSF_CUDA(h, cudaStreamWaitEvent(h->stream, ev_cov[k], 0));
+    cudaError_t e;
+    {
+      PhaseTimer t(h, BSF_PHASE_STENCIL);
+      e = stencil_band(h, dcov, cov_kind, y0, rows, static_cast<char*>(h->hs_out) + (size_t)y0 * W * eo,
+                       out_dtype, W);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "stencil");
+    BSF_CUDA(h, cudaEventRecord(ev_out[k], h->stream));
+    // each finished band goes back while the next one is computed
+    BSF_CUDA(h, cudaStreamWaitEvent(h->s_d2h, ev_out[k], 0));
+    BSF_CUDA(h, cudaMemcpy2DAsync(static_cast<char*>(out) + (size_t)y0 * ldo * eo, ldo * eo,
+                                  static_cast<const char*>(h->hs_out) + (size_t)y0 * W * eo, W * eo,
+                                  W * eo, rows, cudaMemcpyDeviceToHost, h->s_d2h));
+  }
+  h->last_cov = nullptr;  // the staged field is overwritten by the next call
+  h->steps_current = false;
+  BSF_CUDA(h, cudaStreamSynchronize(h->s_d2h));
+  BSF_CUDA(h, cudaStreamSynchronize(h->stream));
+  return BSF_OK;
 }
 
 int bsf_filter_rows(bsf_t h, const void* img, int dtype, long long ld, const float* cov,

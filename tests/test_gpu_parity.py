@@ -272,3 +272,35 @@ def test_row_bands_equal_whole_image_bit_exact(n, boundary):
     assert f.status() == 0
     f.close()
     torch.testing.assert_close(torch.cat(parts, 0), whole, rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("dtype,out64,pinned,rule,n", [(np.float32, False, True, 0, 2), (np.uint8, True, False, 0, 3),
+                                                       (np.float64, False, True, 2, 2), (np.float32, False, False, 2, 1)])
+def test_host_buffer_entry_equals_device_filter(dtype, out64, pinned, rule, n):
+    # bsf_filter_host: uploads, band-wise stencil and downloads overlapped on
+    # three streams; padded host strides; the result must equal bsf_filter's
+    import torch
+    from paper_1109_5114_gb300 import bsf
+    H, W = 157, 203
+    base = wl.blob_image(H, W + 5, seed=3, n_blobs=20)
+    img = (np.clip(base * 255, 0, 255).astype(np.uint8) if dtype == np.uint8 else base.astype(dtype))
+    img_v = img[:, :W]                       # row stride W + 5
+    cov = _cov(H, W, seed=9)
+    prec = 2 if rule == 2 else 1
+    q = -1 if rule == 2 else 6
+    odt = torch.float64 if out64 else torch.float32
+    f_dev = bsf.BoxSplineFilter(H, W, n, "symmetric", precision=prec, frac_bits=q, step_rule=rule)
+    ref = f_dev.filter(torch.from_numpy(np.ascontiguousarray(img_v)).cuda(), torch.from_numpy(cov).cuda(),
+                       out_dtype=odt).cpu().numpy()
+    f_host = bsf.BoxSplineFilter(H, W, n, "symmetric", precision=prec, frac_bits=q, step_rule=rule)
+    t_img = torch.from_numpy(img)[:, :W]
+    t_cov = torch.from_numpy(cov)
+    out = torch.zeros((H, W + 3), dtype=odt)[:, :W]
+    if pinned:
+        t_img = torch.from_numpy(img).pin_memory()[:, :W]
+        t_cov = t_cov.pin_memory()
+        out = torch.zeros((H, W + 3), dtype=odt).pin_memory()[:, :W]
+    for _ in range(2):  # the second call reuses the staging buffers and the plan
+        f_host.filter_host(t_img, t_cov, out)
+        assert f_host.status() == 0
+        np.testing.assert_array_equal(out.numpy(), ref)
