@@ -124,6 +124,7 @@ extern "C" {
 #define BSF_OPT_PLAN_UNION   6  /* 1 = each bsf_plan widens the plan instead of replacing it:
                                    R and the mass bound become the largest over every plan
                                    since the option was set (one context for many fields) */
+#define BSF_OPT_HOST_BANDS   7  /* row bands of bsf_filter_host's overlapped transfers, 1..32 (default 4) */
 #define BSF_SCAN_LOOKBACK     0 /* single pass, decoupled look-back between blocks */
 #define BSF_SCAN_THREE_PHASE  1 /* reduce / carry / rescan; no block waits on another
                                    (measured faster on GB300 for 2048^2, n = 2) */
@@ -218,7 +219,8 @@ int bsf_filter(bsf_t h, const void* img, int dtype, long long ld,
 
 /* Whole forward filter on HOST buffers, overlapping the transfers with the
  * work: the image is uploaded first and pre-integrated as soon as it has
- * arrived, while the covariance planes follow in eight row bands on a second
+ * arrived, while the covariance planes follow in row bands (four by default,
+ * BSF_OPT_HOST_BANDS) on a second
  * stream; the stencil runs band by band as each band's field arrives, and
  * each finished band of the output goes back on a third stream while the
  * next is computed.  img: host [H][ld] of dtype; cov: host [3][H][W] float32

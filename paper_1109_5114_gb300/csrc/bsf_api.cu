@@ -58,7 +58,8 @@ struct bsf_ctx {
 
   // host-buffer entry (bsf_filter_host): device staging copies of the inputs
   // and the output, one stream per copy direction, and the band events
-  static constexpr int kHostBands = 8;
+  static constexpr int kHostBands = 32;  // most bands of bsf_filter_host
+  int host_bands = 4;
   void* hs_img = nullptr;
   void* hs_cov = nullptr;
   void* hs_out = nullptr;
@@ -453,6 +454,10 @@ int bsf_set_option(bsf_t h, int option, long long value) {
     case BSF_OPT_PLAN_UNION:
       h->plan_union = value != 0;
       return BSF_OK;
+    case BSF_OPT_HOST_BANDS:
+      if (value < 1 || value > bsf_ctx::kHostBands) return fail(h, BSF_EINVAL, "bad band count %lld", value);
+      h->host_bands = (int)value;
+      return BSF_OK;
     default:
       return fail(h, BSF_EINVAL, "unknown option %d", option);
   }
@@ -569,7 +574,7 @@ int bsf_filter_host(bsf_t h, const void* img, int dtype, long long ld, const flo
     for (auto& e : h->hev) BSF_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     h->hev_ready = true;
   }
-  const int K = H < bsf_ctx::kHostBands ? H : bsf_ctx::kHostBands;
+  const int K = H < h->host_bands ? H : h->host_bands;
   cudaEvent_t ev_img = h->hev[0];
   cudaEvent_t* ev_cov = h->hev + 1;
   cudaEvent_t* ev_out = h->hev + 1 + bsf_ctx::kHostBands;
@@ -580,26 +585,37 @@ int bsf_filter_host(bsf_t h, const void* img, int dtype, long long ld, const flo
   float* dcov = static_cast<float*>(h->hs_cov);
   // the previous call's output copies must be done before the staging buffers are reused
   BSF_CUDA(h, cudaStreamSynchronize(h->s_d2h));
-  // image, then the covariance planes band by band, on the upload stream
+  // the image on the upload stream, and its pre-integration queued right
+  // behind it; then the field band by band (the three planes of a band in one
+  // two-dimensional copy)
   BSF_CUDA(h, cudaMemcpy2DAsync(h->hs_img, W * es, img, ld * es, W * es, H, cudaMemcpyHostToDevice,
                                 h->s_h2d));
   BSF_CUDA(h, cudaEventRecord(ev_img, h->s_h2d));
-  for (int k = 0; k < K; ++k) {
-    int y0, rows;
-    band(k, y0, rows);
-    for (int c = 0; c < 3; ++c)
-      BSF_CUDA(h, cudaMemcpyAsync(dcov + c * HW + (size_t)y0 * W, cov + c * HW + (size_t)y0 * W,
-                                  (size_t)rows * W * sizeof(float), cudaMemcpyHostToDevice, h->s_h2d));
-    BSF_CUDA(h, cudaEventRecord(ev_cov[k], h->s_h2d));
-  }
-  // a plan (first call) needs the whole field
+  auto upload_field = [&]() -> int {
+    for (int k = 0; k < K; ++k) {
+      int y0, rows;
+      band(k, y0, rows);
+      BSF_CUDA(h, cudaMemcpy2DAsync(dcov + (size_t)y0 * W, HW * sizeof(float), cov + (size_t)y0 * W,
+                                    HW * sizeof(float), (size_t)rows * W * sizeof(float), 3,
+                                    cudaMemcpyHostToDevice, h->s_h2d));
+      BSF_CUDA(h, cudaEventRecord(ev_cov[k], h->s_h2d));
+    }
+    return BSF_OK;
+  };
   if (h->R < 0 || (h->frac_req < 0 && !h->planned)) {
+    // a plan (first call) needs the whole field first
+    if ((rc = upload_field())) return rc;
     BSF_CUDA(h, cudaStreamWaitEvent(h->stream, ev_cov[K - 1], 0));
     if ((rc = run_steps(h, dcov, cov_kind, true))) return rc;
+    if ((rc = reset_counters(h, true, false))) return rc;
+    BSF_CUDA(h, cudaStreamWaitEvent(h->stream, ev_img, 0));
+    if ((rc = preintegrate_impl(h, h->hs_img, dtype, W, 0, H))) return rc;
+  } else {
+    if ((rc = reset_counters(h, true, false))) return rc;
+    BSF_CUDA(h, cudaStreamWaitEvent(h->stream, ev_img, 0));
+    if ((rc = preintegrate_impl(h, h->hs_img, dtype, W, 0, H))) return rc;
+    if ((rc = upload_field())) return rc;
   }
-  if ((rc = reset_counters(h, true, false))) return rc;
-  BSF_CUDA(h, cudaStreamWaitEvent(h->stream, ev_img, 0));
-  if ((rc = preintegrate_impl(h, h->hs_img, dtype, W, 0, H))) return rc;
   for (int k = 0; k < K; ++k) {
     int y0, rows;
     band(k, y0, rows);
