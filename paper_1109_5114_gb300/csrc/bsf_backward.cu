@@ -41,61 +41,94 @@ __device__ __forceinline__ int grad_q(unsigned mbits) {
   return q < 0 ? 0 : (q > 100 ? 100 : q);
 }
 
-template <int NF, int LVL>
-__device__ __forceinline__ void scatter(unsigned long long* p, const long long* s,
-                                        unsigned long long v) {
-  if constexpr (LVL == 0) {
-    atomicAdd(p, v);
-  } else {
-    const long long sk = s[LVL - 1];
-    scatter<NF, LVL - 1>(p, s, v);
-    if constexpr (NF == 1) {
-      scatter<NF, LVL - 1>(p - sk, s, 0ull - v);
-    } else if constexpr (NF == 2) {
-      scatter<NF, LVL - 1>(p - sk, s, 0ull - (v << 1));
-      scatter<NF, LVL - 1>(p - 2 * sk, s, v);
-    } else {
-      scatter<NF, LVL - 1>(p - sk, s, 0ull - 3ull * v);
-      scatter<NF, LVL - 1>(p - 2 * sk, s, 3ull * v);
-      scatter<NF, LVL - 1>(p - 3 * sk, s, 0ull - v);
-    }
-  }
+// (-1)^t C(n, t) as a two's-complement 64-bit weight
+template <int NF> __device__ __forceinline__ unsigned long long tap_w(int t) {
+  const long long c = NF == 1 ? 1 : (NF == 2 ? (t == 1 ? 2 : 1) : (t == 1 || t == 2 ? 3 : 1));
+  return (unsigned long long)((t & 1) ? -c : c);
 }
 
+// Transposed taps: pixel p adds w_t g(p) at each of its (n+1)^4 taps.  A warp
+// is 32 consecutive pixels of one row; along d1 the taps of lanes L1 apart
+// fall on each other (lane x + t L1's tap t is lane x's tap 0) whenever the
+// two pixels have the same steps, so lane x adds its partners' tap values to
+// its own tap 0 through shuffles and issues one reduction for all of them;
+// a tap whose lane x - t L1 took it is not issued again.  Sums are modulo
+// 2^64, so the grouping changes nothing but the number of reductions.
 template <int NF>
 __global__ void __launch_bounds__(256)
 k_scatter_d1(unsigned long long* __restrict__ G, long long pitch, int R,
              const float* __restrict__ cov, int kind, int rule, const float* __restrict__ gout,
              long long ldg, int H, int W, int row0, int rows, int qg_given, DevStatus* st) {
   // pixel (x, row0 + y) of the band; G holds the band's padded rows
-  // (row 0 = image row row0 - R)
-  const int x = blockIdx.x * 32 + threadIdx.x;
+  // (row 0 = image row row0 - R).  blockDim.x == 32: one warp per row segment.
+  const int lane = threadIdx.x;
+  const int x = blockIdx.x * 32 + lane;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= W || y >= rows) return;
-  const long long HW = (long long)H * W, i = (long long)(row0 + y) * W + x;
-  int L[4], flags, reach;
-  float C11, C12, C22;
-  bsf_solve::load_cov(cov, kind, HW, i, C11, C12, C22);
-  bsf_solve::pixel_steps(C11, C12, C22, NF, rule, R, L, flags, reach);
-  const int qg = qg_given >= 0 ? qg_given : grad_q(st->max_absg_bits);
-  unsigned long long D = (unsigned long long)(L[0] * L[1]) * (unsigned long long)(L[2] * L[3]);
-  const unsigned long long D1 = D;
+  if (y >= rows) return;  // uniform across the warp
+  const bool in = x < W;
+  int L[4] = {1, 1, 1, 1};
+  unsigned long long g = 0;
+  if (in) {
+    const long long HW = (long long)H * W, i = (long long)(row0 + y) * W + x;
+    int flags, reach;
+    float C11, C12, C22;
+    bsf_solve::load_cov(cov, kind, HW, i, C11, C12, C22);
+    bsf_solve::pixel_steps(C11, C12, C22, NF, rule, R, L, flags, reach);
+    const int qg = qg_given >= 0 ? qg_given : grad_q(st->max_absg_bits);
+    unsigned long long D = (unsigned long long)(L[0] * L[1]) * (unsigned long long)(L[2] * L[3]);
+    const unsigned long long D1 = D;
 #pragma unroll
-  for (int j = 1; j < NF; ++j) D *= D1;
-  const float xg = __fmul_rn(gout[(long long)(row0 + y) * ldg + x], bsf_pow2_f32(qg));  // exact scaling
-  bool ok;
-  const unsigned long long g =
-      bsf_quantize_f32<unsigned long long>(__fdiv_rn(xg, bsf_rn32_u64(D)), 0, ok);
-  if (!ok) bsf_set_error(st, BSF_EOVERFLOW);
-  if (g == 0) return;
-  const long long L1 = L[0], L2 = L[1], L3 = L[2], L4 = L[3];
+    for (int j = 1; j < NF; ++j) D *= D1;
+    const float xg = __fmul_rn(gout[(long long)(row0 + y) * ldg + x], bsf_pow2_f32(qg));  // exact scaling
+    bool ok;
+    g = bsf_quantize_f32<unsigned long long>(__fdiv_rn(xg, bsf_rn32_u64(D)), 0, ok);
+    if (!ok) bsf_set_error(st, BSF_EOVERFLOW);
+  }
+  // lanes with equal steps share tap positions; L < 2^15, so the pair packs
+  const unsigned sa = in ? (unsigned)L[0] | ((unsigned)L[1] << 16) : 0xffffffffu;
+  const unsigned sb = in ? (unsigned)L[2] | ((unsigned)L[3] << 16) : 0xffffffffu;
+  const int L1 = L[0];
+  bool up[NF + 1], dn[NF + 1];
+  int src[NF + 1];
+#pragma unroll
+  for (int t = 1; t <= NF; ++t) {
+    const int u = lane + t * L1, d = lane - t * L1;
+    src[t] = u < 32 ? u : lane;
+    const unsigned ua = __shfl_sync(0xffffffffu, sa, src[t]), ub = __shfl_sync(0xffffffffu, sb, src[t]);
+    const unsigned da = __shfl_sync(0xffffffffu, sa, d >= 0 ? d : lane),
+                   db = __shfl_sync(0xffffffffu, sb, d >= 0 ? d : lane);
+    up[t] = in && u < 32 && ua == sa && ub == sb;
+    dn[t] = in && d >= 0 && da == sa && db == sb;
+  }
   const long long e1 = 1, e2 = pitch + 1, e3 = pitch, e4 = pitch - 1;
-  const long long c1 = NF * (L1 - 1) / 2, c2 = NF * (L2 - 1) / 2, c3 = NF * (L3 - 1) / 2,
-                  c4 = NF * (L4 - 1) / 2;
+  const long long c1 = NF * (L[0] - 1) / 2, c2 = NF * (L[1] - 1) / 2, c3 = NF * (L[2] - 1) / 2,
+                  c4 = NF * (L[3] - 1) / 2;
   unsigned long long* base =
       G + (long long)(y + R) * pitch + (x + R) + c1 * e1 + c2 * e2 + c3 * e3 + c4 * e4;
-  const long long s[4] = {L1 * e1, L2 * e2, L3 * e3, L4 * e4};
-  scatter<NF, 4>(base, s, g);
+  const long long s2 = L[1] * e2, s3 = L[2] * e3, s4 = L[3] * e4;
+#pragma unroll 1
+  for (int t4 = 0; t4 <= NF; ++t4) {
+#pragma unroll
+    for (int t3 = 0; t3 <= NF; ++t3) {
+#pragma unroll
+      for (int t2 = 0; t2 <= NF; ++t2) {
+        const unsigned long long w = g * tap_w<NF>(t2) * tap_w<NF>(t3) * tap_w<NF>(t4);
+        unsigned long long* p = base - t2 * s2 - t3 * s3 - t4 * s4;
+        unsigned long long tot = w;  // tap 0 (weight 1)
+        unsigned long long v[NF + 1];
+#pragma unroll
+        for (int t = 1; t <= NF; ++t) {
+          v[t] = w * tap_w<NF>(t);
+          const unsigned long long pv = __shfl_sync(0xffffffffu, v[t], src[t]);
+          if (up[t]) tot += pv;
+        }
+        if (in && tot != 0) atomicAdd(p, tot);
+#pragma unroll
+        for (int t = 1; t <= NF; ++t)
+          if (in && !dn[t] && v[t] != 0) atomicAdd(p - t * L1, v[t]);
+      }
+    }
+  }
 }
 
 // Padded coordinates z in [-R, N + R) whose extension maps onto image
