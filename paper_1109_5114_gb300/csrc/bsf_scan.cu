@@ -83,45 +83,28 @@ __device__ __forceinline__ long long binom_small(long long a, int j) {
   return j == 0 ? 1 : (j == 1 ? a : a * (a - 1) / 2);
 }
 
-template <typename T, int NF, typename In, int V>
-__device__ __forceinline__ void scan_rows_body(const In* __restrict__ img, long long ld, int H,
-                                               int W, int R, int row0, int boundary, float scale_f,
-                                               int q, T* __restrict__ S, long long pitch, int Hp,
-                                               int Wp, DevStatus* st, int yp) {
+// n-fold running sums of one row of Wp elements by the block, in passes of
+// kRowThreads * V elements: element xl (scan order) comes from load(xl) and
+// its n-th fold goes to store(xl, value).  The block must call it uniformly.
+template <typename T, int NF, int V, typename Load, typename Store>
+__device__ __forceinline__ void row_scan_segments(int Wp, Load&& load, Store&& store) {
   constexpr int NW = kRowThreads / 32;
   constexpr int SEG = 32 * V;
   constexpr int VP = V + 1;  // padded stride of the store transpose (fewer bank conflicts)
-  __shared__ T s_end[NW][NF];
-  __shared__ T s_tr[NW][32 * VP];
+  // raw storage: the element types with constructors are written before read
+  __shared__ __align__(16) unsigned char s_end_raw[NW * NF * sizeof(T)];
+  __shared__ __align__(16) unsigned char s_tr_raw[NW * 32 * VP * sizeof(T)];
+  T(*s_end)[NF] = reinterpret_cast<T(*)[NF]>(s_end_raw);
+  T(*s_tr)[32 * VP] = reinterpret_cast<T(*)[32 * VP]>(s_tr_raw);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  bool yvalid;
-  const int ys = bsf_map_index(row0 + yp - R, H, boundary, yvalid);  // row0: first row of a band
-  const In* src = img + (long long)ys * ld;
-  T* row = S + (long long)yp * pitch;
   T carry[NF];  // fold values just before the pass (uniform across the block)
 #pragma unroll
   for (int f = 0; f < NF; ++f) carry[f] = 0;
-  float amax = 0.f;
-  bool all_ok = true;
   for (int x0 = 0; x0 < Wp; x0 += kRowThreads * V) {
     const int xl0 = x0 + wid * SEG + lane * V;  // this lane's first element
     T v[V];
 #pragma unroll
-    for (int j = 0; j < V; ++j) {
-      const int xp = xl0 + j;
-      v[j] = 0;
-      if (xp < Wp && yvalid) {
-        bool xvalid;
-        const int xs = bsf_map_index(xp - R, W, boundary, xvalid);
-        if (xvalid) {
-          bool ok;
-          float ax;
-          v[j] = quantize_one<T, In>(src[xs], q, scale_f, ok, ax);
-          all_ok &= ok;
-          amax = fmaxf(amax, ax);
-        }
-      }
-    }
+    for (int j = 0; j < V; ++j) v[j] = xl0 + j < Wp ? load(xl0 + j) : (T)0;
     // the folds within the warp's segment (zero carry-in at its start)
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -190,14 +173,43 @@ __device__ __forceinline__ void scan_rows_body(const In* __restrict__ img, long 
 #pragma unroll
     for (int r = 0; r < V; ++r) {
       const int e = r * 32 + lane;
-      const int xp = x0 + wid * SEG + e;
-      if (xp < Wp) row[xp] = s_tr[wid][(e / V) * VP + e % V];
+      const int xl = x0 + wid * SEG + e;
+      if (xl < Wp) store(xl, s_tr[wid][(e / V) * VP + e % V]);
     }
     __syncwarp();
 #pragma unroll
     for (int f = 0; f < NF; ++f) carry[f] = cnext[f];
     __syncthreads();  // s_end is rewritten by the next pass
   }
+}
+
+template <typename T, int NF, typename In, int V>
+__device__ __forceinline__ void scan_rows_body(const In* __restrict__ img, long long ld, int H,
+                                               int W, int R, int row0, int boundary, float scale_f,
+                                               int q, T* __restrict__ S, long long pitch, int Hp,
+                                               int Wp, DevStatus* st, int yp) {
+  const int lane = threadIdx.x & 31;
+  bool yvalid;
+  const int ys = bsf_map_index(row0 + yp - R, H, boundary, yvalid);  // row0: first row of a band
+  const In* src = img + (long long)ys * ld;
+  T* row = S + (long long)yp * pitch;
+  float amax = 0.f;
+  bool all_ok = true;
+  row_scan_segments<T, NF, V>(
+      Wp,
+      [&](int xp) -> T {
+        if (!yvalid) return (T)0;
+        bool xvalid;
+        const int xs = bsf_map_index(xp - R, W, boundary, xvalid);
+        if (!xvalid) return (T)0;
+        bool ok;
+        float ax;
+        const T q_ = quantize_one<T, In>(src[xs], q, scale_f, ok, ax);
+        all_ok &= ok;
+        amax = fmaxf(amax, ax);
+        return q_;
+      },
+      [&](int xp, T val) { row[xp] = val; });
   for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   const bool bad = __any_sync(0xffffffffu, !all_ok);
   if (lane == 0) {
@@ -549,54 +561,11 @@ cudaError_t launch_lb_skew(int skew, T* S, long long pitch, int Hp, int Wp, T* a
 template <typename T, int NF, int V>
 __global__ void __launch_bounds__(kRowThreads)
 k_suffix_rows(T* __restrict__ S, long long pitch, int Wp) {
-  constexpr int NW = kRowThreads / 32;
-  __shared__ T s_warp[NF][NW];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // suffix sums: scan order runs from the row's end to its start
   T* row = S + (long long)blockIdx.x * pitch;
-  T carry[NF];
-#pragma unroll
-  for (int f = 0; f < NF; ++f) carry[f] = 0;
-  for (int x0 = 0; x0 < Wp; x0 += kRowThreads * V) {
-    T v[V];
-#pragma unroll
-    for (int j = 0; j < V; ++j) {
-      const int xl = x0 + tid * V + j;
-      v[j] = xl < Wp ? row[Wp - 1 - xl] : (T)0;
-    }
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-#pragma unroll
-      for (int j = 1; j < V; ++j) v[j] += v[j - 1];
-      const T tot = v[V - 1];
-      T incl = tot;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const T t = bsf_shfl_up(incl, o);
-        if (lane >= o) incl += t;
-      }
-      if (lane == 31) s_warp[f][wid] = incl;
-      __syncthreads();
-      T wpre = 0, btot = 0;
-#pragma unroll
-      for (int w = 0; w < NW; ++w) {
-        const T t = s_warp[f][w];
-        if (w < wid) wpre += t;
-        btot += t;
-      }
-      const T add = carry[f] + wpre + (incl - tot);
-#pragma unroll
-      for (int j = 0; j < V; ++j) v[j] += add;
-      carry[f] += btot;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < V; ++j) {
-      const int xl = x0 + tid * V + j;
-      if (xl < Wp) row[Wp - 1 - xl] = v[j];
-    }
-  }
+  row_scan_segments<T, NF, V>(Wp, [&](int xl) -> T { return row[Wp - 1 - xl]; },
+                              [&](int xl, T val) { row[Wp - 1 - xl] = val; });
 }
-
 template <typename T, int NF, int V>
 cudaError_t launch_rows_v(const void* img, int dtype, long long ld, int H, int W, int R, int row0,
                           int boundary, int q, T* S, long long pitch, int Hp, int Wp,
@@ -688,19 +657,32 @@ cudaError_t bsf_launch_scan_rows(int prec, int n, const void* img, int dtype, lo
 #undef BSF_ROWS
 }
 
+namespace {
+template <typename T, int NF>
+void launch_suffix_t(void* S, long long pitch, int Hp, int Wp, cudaStream_t s) {
+  // elements per thread chosen like the forward row pass
+  if (Wp <= kRowThreads * 4) {
+    k_suffix_rows<T, NF, 4><<<Hp, kRowThreads, 0, s>>>((T*)S, pitch, Wp);
+  } else if constexpr (sizeof(T) > 8) {
+    k_suffix_rows<T, NF, 9><<<Hp, kRowThreads, 0, s>>>((T*)S, pitch, Wp);
+  } else {
+    if (Wp <= kRowThreads * 9) k_suffix_rows<T, NF, 9><<<Hp, kRowThreads, 0, s>>>((T*)S, pitch, Wp);
+    else k_suffix_rows<T, NF, 12><<<Hp, kRowThreads, 0, s>>>((T*)S, pitch, Wp);
+  }
+}
+}  // namespace
+
 cudaError_t bsf_launch_suffix_rows(int elem_bytes, int n, void* S, long long pitch, int Hp, int Wp,
                                    cudaStream_t s) {
-#define BSF_SR(T, NF, V) k_suffix_rows<T, NF, V><<<Hp, kRowThreads, 0, s>>>((T*)S, pitch, Wp); break
   switch (elem_bytes * 10 + n) {
-    case 81: BSF_SR(uint64_t, 1, 4);
-    case 82: BSF_SR(uint64_t, 2, 4);
-    case 83: BSF_SR(uint64_t, 3, 4);
-    case 161: BSF_SR(u128, 1, 2);
-    case 162: BSF_SR(u128, 2, 2);
-    case 163: BSF_SR(u128, 3, 2);
+    case 81: launch_suffix_t<uint64_t, 1>(S, pitch, Hp, Wp, s); break;
+    case 82: launch_suffix_t<uint64_t, 2>(S, pitch, Hp, Wp, s); break;
+    case 83: launch_suffix_t<uint64_t, 3>(S, pitch, Hp, Wp, s); break;
+    case 161: launch_suffix_t<u128, 1>(S, pitch, Hp, Wp, s); break;
+    case 162: launch_suffix_t<u128, 2>(S, pitch, Hp, Wp, s); break;
+    case 163: launch_suffix_t<u128, 3>(S, pitch, Hp, Wp, s); break;
     default: return cudaErrorInvalidValue;
   }
-#undef BSF_SR
   return cudaGetLastError();
 }
 
