@@ -163,14 +163,23 @@ __global__ void k_fold_x(const unsigned long long* __restrict__ G, long long pit
   Gx[(long long)yr * W + x] = acc;
 }
 
-__global__ void k_fold_y_out(const unsigned long long* __restrict__ Gx, int H, int W, int R,
-                             int boundary, float* __restrict__ gimg, long long ldo,
-                             const DevStatus* st) {
+// Both folds at once: pixel (x, y) sums G over the padded positions that
+// extend onto it in each dimension (interior pixels: one), then rounds.
+__global__ void k_fold_xy_out(const unsigned long long* __restrict__ G, long long pitch, int H, int W,
+                              int R, int boundary, float* __restrict__ gimg, long long ldo,
+                              const DevStatus* st) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   if (x >= W || y >= H) return;
   unsigned long long acc = 0;
-  for_preimages(y, H, R, boundary, [&](int yp) { acc += Gx[(long long)yp * W + x]; });
+  if (x >= R && x < W - R && y >= R && y < H - R) {  // no preimage but itself
+    acc = G[(long long)(y + R) * pitch + (x + R)];
+  } else {
+    for_preimages(y, H, R, boundary, [&](int yp) {
+      const unsigned long long* row = G + (long long)yp * pitch;
+      for_preimages(x, W, R, boundary, [&](int xp) { acc += row[xp]; });
+    });
+  }
   const int qg = grad_q(st->max_absg_bits);
   gimg[(long long)y * ldo + x] = __fmul_rn(bsf_rn32_i64((long long)acc), bsf_pow2_f32(-qg));
 }
@@ -264,10 +273,10 @@ cudaError_t bsf_launch_grad_finalize(const long long* acc, long long lda, int ro
 cudaError_t bsf_launch_fold(const void* G, long long pitch, int Hp, int H, int W, int R,
                             int boundary, void* Gx, float* gimg, long long ldo, const DevStatus* st,
                             cudaStream_t s) {
+  (void)Hp;
+  (void)Gx;
   dim3 blk(128);
-  k_fold_x<<<dim3((W + 127) / 128, Hp), blk, 0, s>>>((const unsigned long long*)G, pitch, Hp, W,
-                                                      R, boundary, (unsigned long long*)Gx);
-  k_fold_y_out<<<dim3((W + 127) / 128, H), blk, 0, s>>>((const unsigned long long*)Gx, H, W, R,
-                                                         boundary, gimg, ldo, st);
+  k_fold_xy_out<<<dim3((W + 127) / 128, H), blk, 0, s>>>((const unsigned long long*)G, pitch, H, W, R,
+                                                          boundary, gimg, ldo, st);
   return cudaGetLastError();
 }

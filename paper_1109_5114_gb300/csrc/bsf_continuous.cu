@@ -140,24 +140,22 @@ __device__ __forceinline__ void for_preimages128(int i, int N, int R, int bounda
   }
 }
 
-__global__ void k_fold_x128(const u128* __restrict__ G, long long pitch, int Hp, int W, int R,
-                            int boundary, u128* __restrict__ Gx) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int yr = blockIdx.y;
-  if (x >= W || yr >= Hp) return;
-  const u128* row = G + (long long)yr * pitch;
-  u128 acc = 0;
-  for_preimages128(x, W, R, boundary, [&](int xp) { acc += bsf_load(row + xp); });
-  Gx[(long long)yr * W + x] = acc;
-}
-
-__global__ void k_fold_y_out128(const u128* __restrict__ Gx, int H, int W, int R, int boundary,
-                                float* __restrict__ gimg, long long ldo, const DevStatus* st) {
+// Both folds at once (see the 64-bit form): interior pixels read one element.
+__global__ void k_fold_xy_out128(const u128* __restrict__ G, long long pitch, int H, int W, int R,
+                                 int boundary, float* __restrict__ gimg, long long ldo,
+                                 const DevStatus* st) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   if (x >= W || y >= H) return;
   u128 acc = 0;
-  for_preimages128(y, H, R, boundary, [&](int yp) { acc += bsf_load(Gx + (long long)yp * W + x); });
+  if (x >= R && x < W - R && y >= R && y < H - R) {
+    acc = bsf_load(G + (long long)(y + R) * pitch + (x + R));
+  } else {
+    for_preimages128(y, H, R, boundary, [&](int yp) {
+      const u128* row = G + (long long)yp * pitch;
+      for_preimages128(x, W, R, boundary, [&](int xp) { acc += bsf_load(row + xp); });
+    });
+  }
   const int qg = grad_q128(st->max_absg_bits);
   gimg[(long long)y * ldo + x] = __fmul_rn(bsf_rn32((i128)acc), bsf_pow2_f32(-qg));
 }
@@ -219,10 +217,10 @@ cudaError_t bsf_launch_scatter_d2(int n, void* G, long long pitch, int R, const 
 cudaError_t bsf_launch_fold128(const void* G, long long pitch, int Hp, int H, int W, int R,
                                int boundary, void* Gx, float* gimg, long long ldo, const DevStatus* st,
                                cudaStream_t s) {
+  (void)Hp;
+  (void)Gx;
   dim3 blk(128);
-  k_fold_x128<<<dim3((W + 127) / 128, Hp), blk, 0, s>>>((const u128*)G, pitch, Hp, W, R, boundary,
-                                                         (u128*)Gx);
-  k_fold_y_out128<<<dim3((W + 127) / 128, H), blk, 0, s>>>((const u128*)Gx, H, W, R, boundary, gimg,
-                                                            ldo, st);
+  k_fold_xy_out128<<<dim3((W + 127) / 128, H), blk, 0, s>>>((const u128*)G, pitch, H, W, R, boundary,
+                                                             gimg, ldo, st);
   return cudaGetLastError();
 }
