@@ -58,28 +58,42 @@ template <int NF> __device__ __forceinline__ int tap_weight(unsigned th, int i) 
 // Adjoint of the continuous-step taps: each pixel adds g(p) times the
 // product of its four interpolation weights at each of its samples, g(p) =
 // RNE(RN32(RN32(gout 2^qg) / RN32(M))) the quantised normalised weight.
+// A warp is 32 consecutive pixels of one row (blockDim.x == 32).  Along d1
+// the second sample of a bracket pair of lane x falls on the first sample of
+// lane x + 1 when both pixels have the same brackets a0 in every direction,
+// so lane x + 1 adds it to its own through a shuffle and one 128-bit add
+// serves both (n = 2: samples 0/1 and 3/4 pair up, n = 1: 0/1 and 2/3).  The
+// low-word atomics of a group are all issued before their high-word adds.
 template <int NF>
 __global__ void __launch_bounds__(128)
 k_scatter_d2(u128* __restrict__ G, long long pitch, int R, const float* __restrict__ cov, int kind,
              const float* __restrict__ gout, long long ldg, int H, int W, DevStatus* st) {
   using P = Pattern<NF>;
-  const int x = blockIdx.x * 32 + threadIdx.x;
+  constexpr int NP = P::NP;
+  // the pairs along d1: (first, second) sample indices
+  constexpr int PA0 = 0, PA1 = 1, PB0 = NF == 2 ? 3 : 2, PB1 = NF == 2 ? 4 : 3;
+  const int lane = threadIdx.x;
+  const int x = blockIdx.x * 32 + lane;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= W || y >= H) return;
-  const long long HW = (long long)H * W, i = (long long)y * W + x;
-  float C11, C12, C22;
-  load_cov(cov, kind, HW, i, C11, C12, C22);
-  int Hq[4], flags, reach;
-  float lam[4];
-  pixel_steps_d2(C11, C12, C22, NF, R, Hq, lam, flags, reach);
-  u128 M = 1;
-  for (int k = 0; k < 4; ++k) M *= (u128)d2_mass(Hq[k], NF);
-  const int qg = grad_q128(st->max_absg_bits);
-  const float xg = __fmul_rn(gout[(long long)y * ldg + x], bsf_pow2_f32(qg));  // exact scaling
-  bool ok;
-  const u128 g = bsf_quantize_f32<u128>(__fdiv_rn(xg, bsf_rn32_u(M)), 0, ok);
-  if (!ok) bsf_set_error(st, BSF_EOVERFLOW);
-  if (g == 0) return;
+  if (y >= H) return;  // uniform across the warp
+  const bool in = x < W;
+  int Hq[4] = {kHalf, kHalf, kHalf, kHalf};
+  u128 g = 0;
+  if (in) {
+    const long long HW = (long long)H * W, i = (long long)y * W + x;
+    float C11, C12, C22;
+    load_cov(cov, kind, HW, i, C11, C12, C22);
+    int flags, reach;
+    float lam[4];
+    pixel_steps_d2(C11, C12, C22, NF, R, Hq, lam, flags, reach);
+    u128 M = 1;
+    for (int k = 0; k < 4; ++k) M *= (u128)d2_mass(Hq[k], NF);
+    const int qg = grad_q128(st->max_absg_bits);
+    const float xg = __fmul_rn(gout[(long long)y * ldg + x], bsf_pow2_f32(qg));  // exact scaling
+    bool ok;
+    g = bsf_quantize_f32<u128>(__fdiv_rn(xg, bsf_rn32_u(M)), 0, ok);
+    if (!ok) bsf_set_error(st, BSF_EOVERFLOW);
+  }
   const int p32 = (int)pitch;
   const int estep[4] = {1, p32 + 1, p32, p32 - 1};
   int a0[4];
@@ -90,30 +104,64 @@ k_scatter_d2(u128* __restrict__ G, long long pitch, int R, const float* __restri
     a0[k] = Q0 >> 10;
     th[k] = (unsigned)(Q0 & 1023);
   }
+  // lanes whose brackets agree in every direction share sample positions
+  const unsigned sa = in ? (unsigned)a0[0] | ((unsigned)a0[1] << 16) : 0xffffffffu;
+  const unsigned sb = in ? (unsigned)a0[2] | ((unsigned)a0[3] << 16) : 0xffffffffu;
+  const unsigned la = __shfl_up_sync(0xffffffffu, sa, 1), lb = __shfl_up_sync(0xffffffffu, sb, 1);
+  const unsigned ra = __shfl_down_sync(0xffffffffu, sa, 1), rb = __shfl_down_sync(0xffffffffu, sb, 1);
+  const bool from_left = in && lane > 0 && la == sa && lb == sb;     // take lane - 1's seconds
+  const bool to_right = in && lane < 31 && ra == sa && rb == sb;     // lane + 1 takes mine
   const int base = (y + R) * p32 + (x + R);
-#pragma unroll 1
-  for (int i1 = 0; i1 < P::NP; ++i1) {
-    const int w1 = tap_weight<NF>(th[0], i1);
-    if (w1 == 0) continue;
-    const u128 c1 = mul_signed(g, w1);
-    const int b1 = base + P::pos(a0[0], i1) * estep[0];
-#pragma unroll 1
-    for (int i2 = 0; i2 < P::NP; ++i2) {
-      const int w2 = tap_weight<NF>(th[1], i2);
-      if (w2 == 0) continue;
-      const u128 c2 = mul_signed(c1, w2);
-      const int b2 = b1 + P::pos(a0[1], i2) * estep[1];
+  // weights of the first direction's samples, and their positions
+  int w1[NP], off1[NP];
 #pragma unroll
-      for (int i3 = 0; i3 < P::NP; ++i3) {
-        const int w3 = tap_weight<NF>(th[2], i3);
-        if (w3 == 0) continue;
-        const u128 c3 = mul_signed(c2, w3);
-        const int b3 = b2 + P::pos(a0[2], i3) * estep[2];
+  for (int i = 0; i < NP; ++i) {
+    w1[i] = tap_weight<NF>(th[0], i);
+    off1[i] = P::pos(a0[0], i);
+  }
+#pragma unroll 1
+  for (int i4 = 0; i4 < NP; ++i4) {
+    const int w4 = tap_weight<NF>(th[3], i4);
+    const u128 c4 = mul_signed(g, w4);
+    const int b4 = base + P::pos(a0[3], i4) * estep[3];
+#pragma unroll 1
+    for (int i3 = 0; i3 < NP; ++i3) {
+      const int w3 = tap_weight<NF>(th[2], i3);
+      const u128 c3 = mul_signed(c4, w3);
+      const int b3 = b4 + P::pos(a0[2], i3) * estep[2];
 #pragma unroll
-        for (int i4 = 0; i4 < P::NP; ++i4) {
-          const int w4 = tap_weight<NF>(th[3], i4);
-          if (w4 == 0) continue;
-          atomic_add_u128(G + b3 + P::pos(a0[3], i4) * estep[3], mul_signed(c3, w4));
+      for (int i2 = 0; i2 < NP; ++i2) {
+        const int w2 = tap_weight<NF>(th[1], i2);
+        const u128 c2 = mul_signed(c3, w2);
+        const int b2 = b3 + P::pos(a0[1], i2) * estep[1];
+        u128 v[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) v[i] = mul_signed(c2, w1[i]);
+        // merge the left neighbour's second samples into my first ones
+        const u128 sA = bsf_shfl_up(v[PA1], 1), sB = bsf_shfl_up(v[PB1], 1);
+        if (from_left) {
+          v[PA0] += sA;
+          v[PB0] += sB;
+        }
+        if (to_right) {
+          v[PA1] = 0;
+          v[PB1] = 0;
+        }
+        // 128-bit adds: every low word first, then the high words with carries
+        unsigned long long old[NP], lo[NP], hi[NP];
+        unsigned long long* q[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          q[i] = reinterpret_cast<unsigned long long*>(G + b2 + off1[i]);
+          lo[i] = (unsigned long long)v[i];
+          hi[i] = (unsigned long long)(v[i] >> 64);
+          old[i] = (in && v[i] != 0) ? atomicAdd(q[i], lo[i]) : 0ull;
+        }
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          if (!in || v[i] == 0) continue;
+          const unsigned long long h = hi[i] + ((old[i] + lo[i] < old[i]) ? 1ull : 0ull);
+          if (h) atomicAdd(q[i] + 1, h);
         }
       }
     }
