@@ -354,14 +354,17 @@ def run_gpu(args):
     hbm_peak, peak_src = peaks()
     dom_ms = per_phase[dominant][0]
     achieved = alg[dominant] / (dom_ms * 1e-3) / 1e9
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
+    traffic = None  # ncu DRAM bytes of one launch, valid while the kernel's sources are unchanged
+    tfile = os.path.join(ROOT, "profiles", "traffic_stencil_spacevariant_2048_n2.txt")
+    if dominant in KERNEL_SOURCES and os.path.exists(tfile):
+        ent = {}
         with open(tfile) as fh:
-            tj = json.load(fh)
-        ent = tj.get(dominant)
-        if ent and dominant in KERNEL_SOURCES and ent.get("kernel_rev") == kernel_revision(dominant):
-            traffic = ent.get("bytes_per_launch")
+            for line in fh:
+                if "=" in line and not line.lstrip().startswith("#"):
+                    k, v = line.split("=", 1)
+                    ent[k.strip()] = v.strip()
+        if ent.get("kernel") == dominant and ent.get("kernel_rev") == kernel_revision(dominant):
+            traffic = int(ent["bytes_per_launch"])
 
     clocks = clk.summary()
     line = {
