@@ -66,10 +66,9 @@ __device__ __forceinline__ T quantize_one(In fv, int q, float scale_f, bool& ok,
     // that stays finite); below 2^63 the conversion rounds it half to even
     const float x = __fmul_rn(fv, scale_f);
     ax = fabsf(x);
-    if (ax < 9223372036854775808.f) {
-      ok = true;
-      return (T)(long long)__float2ll_rn(x);
-    }
+    ok = true;
+    if (ax < 2147483648.f) return (T)(long long)__float2int_rn(x);  // 32-bit conversion suffices
+    if (ax < 9223372036854775808.f) return (T)(long long)__float2ll_rn(x);
     return bsf_quantize_f32<T>(fv, q, ok);  // large or non-finite: integer path
   } else {
     const double xq = (double)fv * (double)scale_f;
