@@ -65,8 +65,12 @@ struct bsf_ctx {
   void* hs_out = nullptr;
   size_t hs_img_bytes = 0, hs_cov_bytes = 0, hs_out_bytes = 0;
   cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
-  cudaEvent_t hev[2 * kHostBands + 1] = {};
+  cudaEvent_t hev[2 * kHostBands + 4] = {};
   bool hev_ready = false;
+  // the whole host-buffer call as a CUDA graph, replayed while its key holds
+  cudaStream_t s_cap = nullptr;
+  cudaGraphExec_t hgraph = nullptr;
+  long long hkey[16] = {};
 
   // phase timing (bsf_set_profiling)
   static constexpr int kMaxRec = 4096;
@@ -381,6 +385,8 @@ void bsf_destroy(bsf_t h) {
   if (h->hs_out) cudaFree(h->hs_out);
   if (h->hev_ready)
     for (auto& e : h->hev) cudaEventDestroy(e);
+  if (h->hgraph) cudaGraphExecDestroy(h->hgraph);
+  if (h->s_cap) cudaStreamDestroy(h->s_cap);
   if (h->s_h2d) cudaStreamDestroy(h->s_h2d);
   if (h->s_d2h) cudaStreamDestroy(h->s_d2h);
   if (h->ev) {
@@ -551,29 +557,13 @@ static cudaError_t stencil_band(bsf_t h, const float* cov, int cov_kind, int y0,
                                h->H, h->W, y0, rows, h->S_q, out, out_dtype, ldo, h->st, h->stream);
 }
 
-int bsf_filter_host(bsf_t h, const void* img, int dtype, long long ld, const float* cov, int cov_kind,
-                    void* out, int out_dtype, long long ldo) {
-  if (!h) return BSF_EINVAL;
-  if (!img || !cov || !out) return fail(h, BSF_EINVAL, "NULL img, cov or out");
-  if (dtype != BSF_U8 && dtype != BSF_F32 && dtype != BSF_F64)
-    return fail(h, BSF_EINVAL, "bad image dtype %d", dtype);
-  if (out_dtype != BSF_F32 && out_dtype != BSF_F64) return fail(h, BSF_EINVAL, "bad out dtype %d", out_dtype);
-  if (ld < h->W || ldo < h->W) return fail(h, BSF_EINVAL, "leading dimension < W");
-  int rc = check_cov_kind(h, cov_kind);
-  if (rc) return rc;
-  if (h->step_rule == BSF_STEP_D2 && (rc = check_d2(h))) return rc;
+// The work of bsf_filter_host after the staging buffers exist: uploads on
+// s_h2d, pre-integration and band stencils on h->stream, downloads on s_d2h.
+static int enqueue_host_filter(bsf_t h, const void* img, int dtype, long long ld, const float* cov,
+                               int cov_kind, void* out, int out_dtype, long long ldo, bool plan) {
   const int H = h->H, W = h->W;
   const size_t HW = (size_t)H * W;
   const size_t es = dtype == BSF_U8 ? 1 : (dtype == BSF_F32 ? 4 : 8), eo = out_dtype == BSF_F32 ? 4 : 8;
-  if ((rc = ensure_staging(h, h->hs_img, h->hs_img_bytes, HW * es))) return rc;
-  if ((rc = ensure_staging(h, h->hs_cov, h->hs_cov_bytes, 3 * HW * sizeof(float)))) return rc;
-  if ((rc = ensure_staging(h, h->hs_out, h->hs_out_bytes, HW * eo))) return rc;
-  if (!h->s_h2d) BSF_CUDA(h, cudaStreamCreateWithFlags(&h->s_h2d, cudaStreamNonBlocking));
-  if (!h->s_d2h) BSF_CUDA(h, cudaStreamCreateWithFlags(&h->s_d2h, cudaStreamNonBlocking));
-  if (!h->hev_ready) {
-    for (auto& e : h->hev) BSF_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    h->hev_ready = true;
-  }
   const int K = H < h->host_bands ? H : h->host_bands;
   cudaEvent_t ev_img = h->hev[0];
   cudaEvent_t* ev_cov = h->hev + 1;
@@ -583,8 +573,7 @@ int bsf_filter_host(bsf_t h, const void* img, int dtype, long long ld, const flo
     rows = (int)((long long)H * (k + 1) / K) - y0;
   };
   float* dcov = static_cast<float*>(h->hs_cov);
-  // the previous call's output copies must be done before the staging buffers are reused
-  BSF_CUDA(h, cudaStreamSynchronize(h->s_d2h));
+  int rc;
   // the image on the upload stream, and its pre-integration queued right
   // behind it; then the field band by band (the three planes of a band in one
   // two-dimensional copy)
@@ -602,7 +591,7 @@ int bsf_filter_host(bsf_t h, const void* img, int dtype, long long ld, const flo
     }
     return BSF_OK;
   };
-  if (h->R < 0 || (h->frac_req < 0 && !h->planned)) {
+  if (plan) {
     // a plan (first call) needs the whole field first
     if ((rc = upload_field())) return rc;
     BSF_CUDA(h, cudaStreamWaitEvent(h->stream, ev_cov[K - 1], 0));
@@ -633,6 +622,82 @@ int bsf_filter_host(bsf_t h, const void* img, int dtype, long long ld, const flo
     BSF_CUDA(h, cudaMemcpy2DAsync(static_cast<char*>(out) + (size_t)y0 * ldo * eo, ldo * eo,
                                   static_cast<const char*>(h->hs_out) + (size_t)y0 * W * eo, W * eo,
                                   W * eo, rows, cudaMemcpyDeviceToHost, h->s_d2h));
+  }
+  return BSF_OK;
+}
+
+int bsf_filter_host(bsf_t h, const void* img, int dtype, long long ld, const float* cov, int cov_kind,
+                    void* out, int out_dtype, long long ldo) {
+  if (!h) return BSF_EINVAL;
+  if (!img || !cov || !out) return fail(h, BSF_EINVAL, "NULL img, cov or out");
+  if (dtype != BSF_U8 && dtype != BSF_F32 && dtype != BSF_F64)
+    return fail(h, BSF_EINVAL, "bad image dtype %d", dtype);
+  if (out_dtype != BSF_F32 && out_dtype != BSF_F64) return fail(h, BSF_EINVAL, "bad out dtype %d", out_dtype);
+  if (ld < h->W || ldo < h->W) return fail(h, BSF_EINVAL, "leading dimension < W");
+  int rc = check_cov_kind(h, cov_kind);
+  if (rc) return rc;
+  if (h->step_rule == BSF_STEP_D2 && (rc = check_d2(h))) return rc;
+  const size_t HW = (size_t)h->H * h->W;
+  const size_t es = dtype == BSF_U8 ? 1 : (dtype == BSF_F32 ? 4 : 8), eo = out_dtype == BSF_F32 ? 4 : 8;
+  if ((rc = ensure_staging(h, h->hs_img, h->hs_img_bytes, HW * es))) return rc;
+  if ((rc = ensure_staging(h, h->hs_cov, h->hs_cov_bytes, 3 * HW * sizeof(float)))) return rc;
+  if ((rc = ensure_staging(h, h->hs_out, h->hs_out_bytes, HW * eo))) return rc;
+  if (!h->s_h2d) BSF_CUDA(h, cudaStreamCreateWithFlags(&h->s_h2d, cudaStreamNonBlocking));
+  if (!h->s_d2h) BSF_CUDA(h, cudaStreamCreateWithFlags(&h->s_d2h, cudaStreamNonBlocking));
+  if (!h->s_cap) BSF_CUDA(h, cudaStreamCreateWithFlags(&h->s_cap, cudaStreamNonBlocking));
+  if (!h->hev_ready) {
+    for (auto& e : h->hev) BSF_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    h->hev_ready = true;
+  }
+  // the previous call's output copies must be done before the staging buffers are reused
+  BSF_CUDA(h, cudaStreamSynchronize(h->s_d2h));
+  const bool plan = h->R < 0 || (h->frac_req < 0 && !h->planned);
+  // q known without a device reduction (which synchronises)?
+  const bool q_known = !is_fixed(h->precision) || h->frac_req >= 0 || dtype == BSF_U8 || h->has_bound;
+  if (plan || !q_known || h->profiling) {
+    if ((rc = enqueue_host_filter(h, img, dtype, ld, cov, cov_kind, out, out_dtype, ldo, plan))) return rc;
+  } else {
+    if ((rc = ensure_workspace(h))) return rc;
+    if ((rc = resolve_q(h, nullptr, dtype, ld))) return rc;  // host arithmetic only here
+    const long long key[16] = {(long long)img, (long long)cov, (long long)out, dtype, ld, ldo, out_dtype,
+                               cov_kind, h->host_bands, h->step_rule, h->precision, h->q, h->R,
+                               (long long)h->S, h->pitch, h->scan_chunk};
+    if (!h->hgraph || std::memcmp(key, h->hkey, sizeof key) != 0) {
+      if (h->hgraph) {
+        cudaGraphExecDestroy(h->hgraph);
+        h->hgraph = nullptr;
+      }
+      // capture on a private stream (the legacy default stream cannot be
+      // captured); the copy streams join through events
+      cudaStream_t user = h->stream;
+      h->stream = h->s_cap;
+      cudaEvent_t fork = h->hev[2 * bsf_ctx::kHostBands + 1];
+      cudaEvent_t j1 = h->hev[2 * bsf_ctx::kHostBands + 2], j2 = h->hev[2 * bsf_ctx::kHostBands + 3];
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(h->s_cap, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) e = cudaEventRecord(fork, h->s_cap);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_h2d, fork, 0);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_d2h, fork, 0);
+      int rc2 = e == cudaSuccess ? enqueue_host_filter(h, img, dtype, ld, cov, cov_kind, out, out_dtype,
+                                                       ldo, false)
+                                 : BSF_OK;
+      if (e == cudaSuccess) e = cudaEventRecord(j1, h->s_h2d);
+      if (e == cudaSuccess) e = cudaEventRecord(j2, h->s_d2h);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_cap, j1, 0);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_cap, j2, 0);
+      const cudaError_t ec = cudaStreamEndCapture(h->s_cap, &graph);
+      h->stream = user;
+      if (e == cudaSuccess) e = ec;
+      if (rc2) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc2;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&h->hgraph, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(h, e, "host-buffer graph");
+      std::memcpy(h->hkey, key, sizeof key);
+    }
+    BSF_CUDA(h, cudaGraphLaunch(h->hgraph, h->stream));
   }
   h->last_cov = nullptr;  // the staged field is overwritten by the next call
   h->steps_current = false;
