@@ -19,8 +19,9 @@ gaussian  Gaussian-approximation errors of continuous box splines (Theorem 1,
 backward  the adjoint of the integer-step filter with respect to the image.
 continuous  the continuous-step filter (interpolated taps, Section 2.3) and
           the derivative of its output with respect to the covariance field.
+two_pass  Algorithm 1: an isotropic pass, then the space-variant residual pass.
 
 Parity status of each function is stated in its docstring; "parity unpinned"
 marks a function with no independent pin.
 """
-from . import params, kernels, modular, gaussian, backward, continuous  # noqa: F401
+from . import params, kernels, modular, gaussian, backward, continuous, two_pass  # noqa: F401
