@@ -233,6 +233,27 @@ int bsf_filter(bsf_t h, const void* img, int dtype, long long ld,
 int bsf_filter_host(bsf_t h, const void* img, int dtype, long long ld, const float* cov, int cov_kind,
                     void* out, int out_dtype, long long ldo);
 
+/* Algorithm 1 of the paper (better Gaussian approximation): split each
+ * covariance C = sigma^2 I + Delta C (eq. "SigmaIso"), filter the image with
+ * the isotropic box spline of covariance sigma^2 I, then filter that result
+ * with the space-variant box spline of the residual Delta C.  sigma^2 is
+ * `frac` (the paper takes 1/2) times the smallest eq. "condition2" bound over
+ * the field, floored at zero, which keeps every residual within the
+ * elongation bound e(phi); the bound is evaluated without trigonometry in a
+ * fixed float64 order ((e+1)/(e-1) = (1+t)/sqrt(1+t^2),
+ * t = |tan(phi) - cot(phi)|/2 of the orientation phi of C), and
+ * sigma^2 = RN32(frac * min).  Both passes run bsf_filter (integer steps,
+ * the context's precision and q); the first pass's float32 output is the
+ * second pass's input.  The library keeps the two fields and the
+ * intermediate image (allocated on first use, synchronously).  The first
+ * call plans both fields (synchronous).  sigma2: NULL, or host float that
+ * receives sigma^2 (synchronises).  img / dtype / ld / cov / cov_kind / out /
+ * out_dtype / ldo as in bsf_filter.  Errors: BSF_EINVAL (frac outside (0, 1),
+ * BSF_STEP_D2), as bsf_filter. */
+int bsf_filter_two_pass(bsf_t h, const void* img, int dtype, long long ld, const float* cov,
+                        int cov_kind, double frac, void* out, int out_dtype, long long ldo,
+                        float* sigma2);
+
 /* Forward filter of the band of rows [y0, y1) only (0 <= y0 < y1 <= H).
  * img and cov are the whole image and field ([H][ld], [3][H][W]); out
  * receives the band's rows ([y1-y0][ldo], row 0 = image row y0).  The

@@ -89,6 +89,8 @@ bsf_grad_absmax_rows = _fn("bsf_grad_absmax_rows", c_int, bsf_t, c_void_p, c_ll,
                            ctypes.POINTER(ctypes.c_float))
 bsf_filter_host = _fn("bsf_filter_host", c_int, bsf_t, c_void_p, c_int, c_ll, c_void_p, c_int, c_void_p,
                       c_int, c_ll)
+bsf_filter_two_pass = _fn("bsf_filter_two_pass", c_int, bsf_t, c_void_p, c_int, c_ll, c_void_p, c_int,
+                          c_double, c_void_p, c_int, c_ll, ctypes.POINTER(ctypes.c_float))
 bsf_grad_finalize = _fn("bsf_grad_finalize", c_int, bsf_t, c_void_p, c_ll, c_int, c_int, c_void_p, c_ll)
 
 class bsf_image_desc(ctypes.Structure):
@@ -228,6 +230,24 @@ class BoxSplineFilter:
                             ctypes.c_void_p(out.data_ptr()), oc, out.stride(0))
         check(self._h, rc)
         return out
+
+    def filter_two_pass(self, img, cov, frac: float = 0.5, out=None, want_sigma2: bool = False):
+        """Algorithm 1: isotropic pass, then the residual pass (bsf_filter_two_pass).
+        Returns out, or (out, sigma^2) with want_sigma2."""
+        import torch
+        self._stream()
+        H, W = self.H, self.W
+        assert img.is_cuda and img.shape == (H, W) and img.stride(1) == 1
+        assert cov.is_cuda and cov.dtype == torch.float32 and cov.shape == (3, H, W) and cov.is_contiguous()
+        if out is None:
+            out = torch.empty((H, W), dtype=torch.float32, device=cov.device)
+        oc = BSF_F32 if out.dtype == torch.float32 else BSF_F64  # noqa: F821
+        s2 = ctypes.c_float()
+        check(self._h, bsf_filter_two_pass(self._h, ctypes.c_void_p(img.data_ptr()), _dtype_code(img),
+                                           img.stride(0), ctypes.c_void_p(cov.data_ptr()), self.cov_kind,
+                                           float(frac), ctypes.c_void_p(out.data_ptr()), oc, out.stride(0),
+                                           ctypes.byref(s2) if want_sigma2 else None))
+        return (out, float(s2.value)) if want_sigma2 else out
 
     def filter_host(self, img, cov, out=None):
         """Forward filter from and to host (CPU) tensors, transfers overlapped

@@ -72,6 +72,12 @@ struct bsf_ctx {
   cudaGraphExec_t hgraph = nullptr;
   long long hkey[16] = {};
 
+  // Algorithm 1 (bsf_filter_two_pass): the two fields, the first pass's
+  // output and the minimum of the condition-2 bound
+  float* tp_fields = nullptr;  // [2][3][H][W]: isotropic, residual
+  float* tp_g = nullptr;       // [H][W]
+  unsigned long long* tp_min = nullptr;
+
   // phase timing (bsf_set_profiling)
   static constexpr int kMaxRec = 4096;
   bool profiling = false;
@@ -380,6 +386,9 @@ void bsf_destroy(bsf_t h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   free_workspace(h);
+  if (h->tp_fields) cudaFree(h->tp_fields);
+  if (h->tp_g) cudaFree(h->tp_g);
+  if (h->tp_min) cudaFree(h->tp_min);
   if (h->hs_img) cudaFree(h->hs_img);
   if (h->hs_cov) cudaFree(h->hs_cov);
   if (h->hs_out) cudaFree(h->hs_out);
@@ -703,6 +712,54 @@ int bsf_filter_host(bsf_t h, const void* img, int dtype, long long ld, const flo
   h->steps_current = false;
   BSF_CUDA(h, cudaStreamSynchronize(h->s_d2h));
   BSF_CUDA(h, cudaStreamSynchronize(h->stream));
+  return BSF_OK;
+}
+
+int bsf_filter_two_pass(bsf_t h, const void* img, int dtype, long long ld, const float* cov,
+                        int cov_kind, double frac, void* out, int out_dtype, long long ldo,
+                        float* sigma2) {
+  if (!h) return BSF_EINVAL;
+  if (!img || !cov || !out) return fail(h, BSF_EINVAL, "NULL img, cov or out");
+  if (!(frac > 0.0 && frac < 1.0)) return fail(h, BSF_EINVAL, "frac must lie in (0, 1)");
+  if (h->step_rule == BSF_STEP_D2) return fail(h, BSF_EINVAL, "two passes: integer steps only");
+  int rc = check_cov_kind(h, cov_kind);
+  if (rc) return rc;
+  const size_t HW = (size_t)h->H * h->W;
+  if (!h->tp_fields) {
+    BSF_CUDA(h, cudaStreamSynchronize(h->stream));
+    BSF_CUDA(h, cudaMalloc(&h->tp_fields, 6 * HW * sizeof(float)));
+    BSF_CUDA(h, cudaMalloc(&h->tp_g, HW * sizeof(float)));
+    BSF_CUDA(h, cudaMalloc(&h->tp_min, 2 * sizeof(unsigned long long)));
+  }
+  float* iso = h->tp_fields;
+  float* res = h->tp_fields + 3 * HW;
+  cudaError_t e;
+  {
+    PhaseTimer t(h, BSF_PHASE_STEPS);
+    e = bsf_launch_cov_split(cov, cov_kind, h->H, h->W, frac, h->tp_min, iso, res, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "field split");
+  if (h->R < 0 || (h->frac_req < 0 && !h->planned)) {
+    // the padding and the mass bound must cover both fields
+    const bool was_union = h->plan_union;
+    h->plan_union = true;
+    h->planned = false;
+    rc = run_steps(h, iso, BSF_COV_C, true);
+    if (!rc) rc = run_steps(h, res, BSF_COV_C, true);
+    h->plan_union = was_union;
+    if (rc) return rc;
+  }
+  if ((rc = filter_impl(h, img, dtype, ld, iso, BSF_COV_C, h->tp_g, BSF_F32, h->W, 0, h->H))) return rc;
+  if ((rc = filter_impl(h, h->tp_g, BSF_F32, h->W, res, BSF_COV_C, out, out_dtype, ldo, 0, h->H)))
+    return rc;
+  if (sigma2) {
+    unsigned long long b = 0;
+    BSF_CUDA(h, cudaMemcpyAsync(&b, h->tp_min, sizeof b, cudaMemcpyDeviceToHost, h->stream));
+    BSF_CUDA(h, cudaStreamSynchronize(h->stream));
+    double m;
+    std::memcpy(&m, &b, sizeof m);
+    *sigma2 = (float)(frac * m);
+  }
   return BSF_OK;
 }
 

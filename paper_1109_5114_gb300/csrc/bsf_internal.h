@@ -139,3 +139,11 @@ cudaError_t bsf_launch_fold128(const void* G, long long pitch, int Hp, int H, in
 // gcov[c][y][x] = gout[y][x] * jac[c][y][x] (jac planes H * ldj apart; gcov [3][H][W]).
 cudaError_t bsf_launch_jacobian_vjp(const float* gout, long long ldg, const float* jac,
                                     long long ldj, float* gcov, int H, int W, cudaStream_t s);
+
+// Algorithm 1's split of a field: min over pixels of the condition-2 bound
+// (floored at zero) into *min_bits (device, double bits), then the isotropic
+// field s2 I and the residual C - s2 I (float32 [3][H][W], BSF_COV_C),
+// s2 = RN32(frac * min).
+cudaError_t bsf_launch_cov_split(const float* cov, int cov_kind, int H, int W, double frac,
+                                 unsigned long long* min_bits, float* iso, float* res,
+                                 cudaStream_t s);
