@@ -1,13 +1,15 @@
 """Pins of Algorithm 1's oracle (oracle/two_pass.py): the algebraic
 condition-2 bound against the trigonometric one, the isotropic closed form,
-the validity of the residual covariance, and Proposition 1 for the composed
-passes (impulse response covariance = sum of the two realised covariances)."""
+the validity of the residual covariance, Proposition 1 for the composed
+passes (impulse response covariance = sum of the two realised covariances),
+and the continuous-model accuracy of the split against Tables 2 and 3."""
 import math
 
 import numpy as np
 
-from oracle import kernels, modular, params
+from oracle import gaussian, kernels, modular, params
 from oracle import two_pass as tp
+from tests.conftest import golden_rows
 from workloads import synth
 
 
@@ -74,3 +76,57 @@ def test_zero_sigma_reduces_to_one_pass():
     out, _, g = tp.algorithm1(f, cov, 1, kernels.SYMMETRIC, q=8, R=20)
     np.testing.assert_array_equal(g, f)
     np.testing.assert_array_equal(out, modular.filter_modular(f, cov, 1, kernels.SYMMETRIC, q=8, R=20))
+
+
+def _split_errors(s, rho, theta, frac, dw=0.04):
+    """Normalised L2 errors (Section 3) of the BoxFilter and of Algorithm 1 for
+    one target, the split taken by this module on a one-pixel field: the
+    min-kurtosis scales of C, then sqrt(6) sigma0 and the min-kurtosis scales
+    of the residual (n = 1: A_k are the squared scales)."""
+    C = np.array(params.cov_from_sigma_rho_theta(math.sqrt(s / 2.0), rho, theta), dtype=np.float64)
+    field = np.asarray(C, dtype=np.float32).reshape(3, 1, 1)
+    s2 = tp.sigma2_global(field, frac)
+    iso, res = tp.split_field(field, s2)
+
+    def scales(c):
+        A, flags = params.solve_scales_f32(c[0, 0, 0], c[1, 0, 0], c[2, 0, 0], 1)
+        assert int(flags) == 0
+        return [math.sqrt(float(a)) for a in np.asarray(A).ravel()]
+
+    target = np.array([[C[0], C[1]], [C[1], C[2]]])
+    e_box = gaussian.normalized_l2_error([(scales(field), gaussian.CARTESIAN)], target, dw=dw)
+    e_alg1 = gaussian.normalized_l2_error([(gaussian.isotropic_scales(math.sqrt(float(s2))), gaussian.CARTESIAN),
+                                           (scales(res), gaussian.CARTESIAN)], target, dw=dw)
+    return e_box, e_alg1
+
+
+def test_table2_isotropic_columns_through_the_split():
+    # the isotropic columns of Table 2 again, now through sigma2_global and
+    # split_field instead of the closed form sigma0^2 = sigma^2 / 2
+    for name, box_pct, alg1_pct in golden_rows("table2_isotropic.txt"):
+        s = float(name.strip("()").split(",")[0])
+        e_box, e_alg1 = _split_errors(s, 1.0, 0.0, 0.5, dw=0.02)
+        assert round(100 * e_box, 1) == float(box_pct)
+        assert round(100 * e_alg1, 1) == float(alg1_pct)
+
+
+def test_table3_improvement_peaks_near_half_the_bound():
+    # Table 3's shape.  Its values are not reproduced: with this module's
+    # kurtosis reading the BoxFilter error of this target is 18.1 % and the
+    # improvements run 16-39 % against the printed 3.5-33.3 %.  What holds:
+    # the improvement grows from 10 % to 50 % of the bound, peaks at 50-60 %
+    # (the printed 33.3 and 33.13 differ by 0.2 points; here by 0.6) and falls
+    # beyond.
+    rows = golden_rows("table3_sigma_fraction.txt")
+    pct = [int(r[0]) for r in rows]
+    printed = [float(r[1]) for r in rows]
+    got = []
+    for p in pct:
+        e_box, e_alg1 = _split_errors(5.0, 3.0, math.pi / 4, p / 100.0)
+        got.append(100 * (e_box - e_alg1) / e_box)
+    for seq in (printed, got):
+        i50, i60 = pct.index(50), pct.index(60)
+        assert all(seq[i] < seq[i + 1] for i in range(i50))           # rising up to 50 %
+        assert max(seq) in (seq[i50], seq[i60]) and abs(seq[i50] - seq[i60]) < 1.0
+        assert all(seq[i] > seq[i + 1] for i in range(i60, len(seq) - 1))  # falling after 60 %
+    assert all(g > 0 for g in got)
