@@ -77,17 +77,19 @@ def box_power_1d(L: int, n: int) -> tuple:
 
 
 @lru_cache(maxsize=4096)
-def kernel_d1(L: tuple, n: int):
+def kernel_d1(L: tuple, n: int, dirs: tuple = DIRS):
     """2-D integer kernel K for integer steps L = (L1..L4), order n.
 
     Returns (K, ox, oy): K[oy + dy, ox + dx] is the weight at offset (dx, dy)
     (dx the column offset).  Built as the convolution of the four line
     kernels box_power_1d(L_k, n) placed on Z d_k, each centred.  Entries are
-    Python ints (object array); sum(K) = prod_k L_k^n.
+    Python ints (object array); sum(K) = prod_k L_k^n.  dirs: the grid
+    vectors d_k (default the Cartesian set; the second set of Section 2.3 is
+    ((2,1), (1,2), (-1,2), (-2,1))).
     """
     K = np.ones((1, 1), dtype=object)
     ox = oy = 0
-    for k, (dx, dy) in enumerate(DIRS):
+    for k, (dx, dy) in enumerate(dirs):
         h = box_power_1d(int(L[k]), n)
         half = n * (int(L[k]) - 1) // 2
         offs = np.arange(-half, half + 1)
@@ -113,7 +115,7 @@ def kernel_mass(L, n: int) -> int:
 
 
 def correlate_exact(fq: np.ndarray, Lfield: np.ndarray, n: int, boundary: int,
-                    pixels=None):
+                    pixels=None, dirs: tuple = DIRS):
     """Exact integer accumulator acc(p) = sum_j K_p(j) fq~(p + j) (Python ints).
 
     fq is an integer image (int64 or object), Lfield is int[4][H][W].
@@ -126,7 +128,7 @@ def correlate_exact(fq: np.ndarray, Lfield: np.ndarray, n: int, boundary: int,
     it = pixels if pixels is not None else ((y, x) for y in range(H) for x in range(W))
     for (y, x) in it:
         Lt = tuple(int(Lfield[k, y, x]) for k in range(4))
-        K, ox, oy = kernel_d1(Lt, n)
+        K, ox, oy = kernel_d1(Lt, n, dirs)
         kh, kw = K.shape
         yi, yv = extend_index(np.arange(y - oy, y - oy + kh), H, boundary)
         xi, xv = extend_index(np.arange(x - ox, x - ox + kw), W, boundary)
