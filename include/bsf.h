@@ -100,6 +100,22 @@ extern "C" {
 #define BSF_STEP_D2        2  /* continuous steps with interpolated taps (n = 1, 2; fixed
                                  point only): see bsf_filter_jacobian */
 
+/* direction sets (BSF_OPT_DIRECTIONS), Section 2.3 of the paper */
+#define BSF_DIRS_CARTESIAN 0  /* beta_a: d1 = (1,0), d2 = (1,1), d3 = (0,1), d4 = (-1,1) (default) */
+#define BSF_DIRS_SECOND    1  /* beta'_a of Algorithm 3: e1 = (2,1), e2 = (1,2), e3 = (-1,2),
+                                 e4 = (-2,1) (x the column), the mesh of Table 1 with integer
+                                 steps; C = (n/60) sum_k A_k e_k e_k^T, feasible for
+                                 4 C11 >= C22, 4 C22 >= C11, |C12| <= (2/5)(C11 + C22) (beyond:
+                                 clamped and counted like BSF_DIRS_CARTESIAN's e(phi)) */
+#define BSF_DIRS_PAIR      2  /* Algorithm 2: both sets of running sums; each pixel takes
+                                 beta'_a where its elongation bound is the larger one, i.e.
+                                 |C11 - C22| < 3|C12| < 6|C11 - C22| (|C11 - C22| rounded once
+                                 to float64), else beta_a.  Twice the running-sum workspace.
+   BSF_DIRS_SECOND and BSF_DIRS_PAIR: forward filtering only (bsf_filter, bsf_filter_rows,
+   bsf_filter_host, bsf_filter_two_pass), step rules BSF_STEP_D1 / BSF_STEP_D1_PAPER,
+   precisions BSF_FIX64 / BSF_FIX128; other calls return BSF_EINVAL.  The second set's
+   vertical running sums always use the three-phase scan. */
+
 /* phases timed by bsf_set_profiling / bsf_read_profile */
 #define BSF_PHASE_STEPS    0  /* per-pixel step solve */
 #define BSF_PHASE_ROWS     1  /* extension + quantisation + running sums along d1 */
@@ -110,7 +126,9 @@ extern "C" {
 #define BSF_PHASE_BWD_SCATTER 6  /* backward: weight quantisation + tap scatter */
 #define BSF_PHASE_BWD_SCANS   7  /* backward: suffix sums along d4, d2, d3, d1 */
 #define BSF_PHASE_BWD_FOLD    8  /* backward: extension adjoint + output */
-#define BSF_NUM_PHASES        9
+#define BSF_PHASE_SECOND      9  /* BSF_DIRS_SECOND / _PAIR: extension + quantisation, then the
+                                    running sums along e1..e4 (nine kernels) */
+#define BSF_NUM_PHASES        10
 
 /* options of bsf_set_option */
 #define BSF_OPT_SCAN_MODE    1  /* value BSF_SCAN_THREE_PHASE (default) or BSF_SCAN_LOOKBACK */
@@ -125,6 +143,8 @@ extern "C" {
                                    R and the mass bound become the largest over every plan
                                    since the option was set (one context for many fields) */
 #define BSF_OPT_HOST_BANDS   7  /* row bands of bsf_filter_host's overlapped transfers, 1..32 (default 4) */
+#define BSF_OPT_DIRECTIONS   8  /* direction set of the integer-step filter (BSF_DIRS_*); changing
+                                   it drops the plan (the next call plans again) */
 #define BSF_SCAN_LOOKBACK     0 /* single pass, decoupled look-back between blocks */
 #define BSF_SCAN_THREE_PHASE  1 /* reduce / carry / rescan; no block waits on another
                                    (measured faster on GB300 for 2048^2, n = 2) */

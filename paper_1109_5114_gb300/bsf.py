@@ -167,11 +167,14 @@ class BoxSplineFilter:
     float32 CUDA tensor of cov_kind (0: C11, C12, C22; 1: log sigma, theta,
     log rho).  step_rule 2 (BSF_STEP_D2) selects the continuous-step filter,
     whose derivative with respect to cov comes from filter_jacobian.
+    directions: BSF_DIRS_CARTESIAN (0), BSF_DIRS_SECOND (1: the box spline on
+    (2,1), (1,2), (-1,2), (-2,1)) or BSF_DIRS_PAIR (2: both, switched per
+    pixel by sector).
     """
 
     def __init__(self, H: int, W: int, n: int, boundary="symmetric", max_reach: int = -1,
                  precision: int = 1, frac_bits: int = -1, value_bound=None, step_rule: int = 0,
-                 cov_kind: int = 0):
+                 cov_kind: int = 0, directions: int = 0):
         if isinstance(boundary, str):
             boundary = _BOUNDARY[boundary]
         self.H, self.W, self.n = H, W, n
@@ -186,6 +189,9 @@ class BoxSplineFilter:
         check(h, bsf_set_step_rule(h, step_rule))
         if value_bound is not None:
             check(h, bsf_set_value_bound(h, float(value_bound)))
+        self.directions = 0
+        if directions:
+            self.set_option(BSF_OPT_DIRECTIONS, directions)  # noqa: F821
 
     def close(self):
         if getattr(self, "_h", None):
@@ -370,6 +376,8 @@ class BoxSplineFilter:
 
     def set_option(self, option: int, value: int):
         check(self._h, bsf_set_option(self._h, option, value))
+        if option == BSF_OPT_DIRECTIONS:  # noqa: F821
+            self.directions = int(value)
 
     def set_profiling(self, on: bool = True):
         check(self._h, bsf_set_profiling(self._h, 1 if on else 0))
@@ -382,7 +390,8 @@ class BoxSplineFilter:
         rc = bsf_read_profile(self._h, ms, cnt)
         if rc < 0:
             check(self._h, rc)
-        names = ["steps", "rows", "d3", "d2", "d4", "stencil", "bwd_scatter", "bwd_scans", "bwd_fold"]
+        names = ["steps", "rows", "d3", "d2", "d4", "stencil", "bwd_scatter", "bwd_scans", "bwd_fold",
+                 "second"]
         return {names[i]: (ms[i], cnt[i]) for i in range(n)}
 
     def status(self) -> int:
@@ -404,6 +413,8 @@ class BoxSplineFilter:
         import torch
         inf = self.info()
         nb = inf.Hp * inf.Wp * inf.elem_bytes
+        if self.directions == BSF_DIRS_PAIR:  # noqa: F821  (the second set's sums follow)
+            nb *= 2
         dst = torch.empty(nb, dtype=torch.uint8, device="cuda")
         self._stream()
         check(self._h, bsf_copy_preintegrated(self._h, ctypes.c_void_p(dst.data_ptr())))

@@ -17,6 +17,7 @@ struct bsf_ctx {
   int frac_req = -1;        // requested q (-1 = automatic)
   int q = -1;               // q of the current pre-integration
   int step_rule = BSF_STEP_D1;
+  int dirset = BSF_DIRS_CARTESIAN;  // direction set (BSF_OPT_DIRECTIONS)
   bool has_bound = false;
   double value_bound = 0.0;
   cudaStream_t stream = nullptr;
@@ -26,6 +27,7 @@ struct bsf_ctx {
   long long pitch = 0;
   int elem = 8;
   void* S = nullptr;
+  void* S2 = nullptr;               // BSF_DIRS_PAIR: running sums of the second set
   size_t S_bytes = 0;
   void* agg = nullptr;
   void* carry = nullptr;
@@ -52,7 +54,7 @@ struct bsf_ctx {
   int last_kind = BSF_COV_C;
   bool steps_current = false;       // Lf holds the steps of last_cov
   bool have_S = false;       // S holds a pre-integration made with (R, elem, q)
-  int S_R = -1, S_elem = 0, S_q = -1;
+  int S_R = -1, S_elem = 0, S_q = -1, S_dirset = BSF_DIRS_CARTESIAN;
   int S_row0 = 0, S_rows = 0;        // image rows the held running sums cover
   char msg[512] = "ok";
 
@@ -115,6 +117,8 @@ bool is_fixed(int precision) { return precision == BSF_FIX64 || precision == BSF
 
 void free_workspace(bsf_t h) {
   if (h->S) cudaFree(h->S);
+  if (h->S2) cudaFree(h->S2);
+  h->S2 = nullptr;
   if (h->agg) cudaFree(h->agg);
   if (h->carry) cudaFree(h->carry);
   if (h->sync_words) cudaFree(h->sync_words);
@@ -143,12 +147,18 @@ int ensure_workspace(bsf_t h) {
   size_t scan_bytes = (size_t)nchunks * h->n * (size_t)(Wp + Hp - 1) * elem;
   const size_t lb_bytes = bsf_vscan_lb_bytes(elem, h->n, Hp, Wp, &sync_bytes);
   if (lb_bytes > scan_bytes) scan_bytes = lb_bytes;
-  if (h->S && h->S_bytes == S_bytes && h->scan_bytes == scan_bytes && h->Hp == Hp &&
-      h->Wp == Wp && h->elem == elem)
+  if (h->dirset != BSF_DIRS_CARTESIAN) {  // the second set's skew-2 and row-parity scans
+    const size_t second = bsf_second_scan_elems(h->n, Hp, Wp, kScanChunkMin) * elem;
+    if (second > scan_bytes) scan_bytes = second;
+  }
+  const bool need_S2 = h->dirset == BSF_DIRS_PAIR;
+  if (h->S && h->S_bytes == S_bytes && h->scan_bytes >= scan_bytes && h->Hp == Hp &&
+      h->Wp == Wp && h->elem == elem && (!need_S2 || h->S2))
     return BSF_OK;
   BSF_CUDA(h, cudaStreamSynchronize(h->stream));
   free_workspace(h);
   BSF_CUDA(h, cudaMalloc(&h->S, S_bytes));
+  if (need_S2) BSF_CUDA(h, cudaMalloc(&h->S2, S_bytes));
   BSF_CUDA(h, cudaMalloc(&h->agg, scan_bytes));
   BSF_CUDA(h, cudaMalloc(&h->carry, scan_bytes));
   BSF_CUDA(h, cudaMalloc(&h->sync_words, sync_bytes));
@@ -241,7 +251,7 @@ int run_steps(bsf_t h, const float* cov, int cov_kind, bool sync_plan) {
   cudaError_t e;
   {
     PhaseTimer t(h, BSF_PHASE_STEPS);
-    e = bsf_launch_steps(cov, cov_kind, h->H, h->W, h->n, h->step_rule, bounded ? h->R : -1,
+    e = bsf_launch_steps(cov, cov_kind, h->H, h->W, h->n, h->step_rule, h->dirset, bounded ? h->R : -1,
                          h->Lf, h->st, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "steps kernel");
@@ -314,12 +324,35 @@ int preintegrate_impl(bsf_t h, const void* img, int dtype, long long ld, int row
     return fail(h, BSF_EINVAL, "bad image dtype %d", dtype);
   if (ld < h->W) return fail(h, BSF_EINVAL, "ld %lld < W %d", ld, h->W);
   if (h->R < 0) return fail(h, BSF_ESTATE, "padding unknown: give max_reach or call bsf_plan");
+  if (h->dirset != BSF_DIRS_CARTESIAN && !is_fixed(h->precision))
+    return fail(h, BSF_EINVAL, "the second direction set needs fixed point");
   int rc;
   if ((rc = ensure_workspace(h))) return rc;
   if ((rc = resolve_q(h, img, dtype, ld))) return rc;
   if ((rc = reset_counters(h, false, true))) return rc;
   const int Hb = rows + 2 * h->R;  // padded rows of the band
   cudaError_t e;
+  if (h->dirset != BSF_DIRS_CARTESIAN) {
+    // extension + quantisation, then the running sums along e1..e4
+    void* S2 = h->dirset == BSF_DIRS_PAIR ? h->S2 : h->S;
+    PhaseTimer t(h, BSF_PHASE_SECOND);
+    e = bsf_launch_extend(h->precision, img, dtype, ld, h->H, h->W, h->R, row0, h->boundary, h->q, S2,
+                          h->pitch, Hb, h->Wp, h->st, h->stream);
+    if (e == cudaSuccess)
+      e = bsf_launch_scans_second(h->precision, h->n, S2, h->pitch, Hb, h->Wp, h->scan_chunk, h->agg,
+                                  h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "second-set running sums");
+  }
+  if (h->dirset == BSF_DIRS_SECOND) {
+    h->have_S = true;
+    h->S_R = h->R;
+    h->S_elem = h->elem;
+    h->S_q = h->q;
+    h->S_row0 = row0;
+    h->S_rows = rows;
+    h->S_dirset = h->dirset;
+    return BSF_OK;
+  }
   {
     PhaseTimer t(h, BSF_PHASE_ROWS);
     e = bsf_launch_scan_rows(h->precision, h->n, img, dtype, ld, h->H, h->W, h->R, row0,
@@ -346,6 +379,7 @@ int preintegrate_impl(bsf_t h, const void* img, int dtype, long long ld, int row
   h->S_q = h->q;
   h->S_row0 = row0;
   h->S_rows = rows;
+  h->S_dirset = h->dirset;
   return BSF_OK;
 }
 
@@ -469,6 +503,16 @@ int bsf_set_option(bsf_t h, int option, long long value) {
     case BSF_OPT_PLAN_UNION:
       h->plan_union = value != 0;
       return BSF_OK;
+    case BSF_OPT_DIRECTIONS:
+      if (value < BSF_DIRS_CARTESIAN || value > BSF_DIRS_PAIR)
+        return fail(h, BSF_EINVAL, "bad direction set %lld", value);
+      if (value != h->dirset) {
+        h->dirset = (int)value;
+        h->planned = false;  // reach and mass differ between the sets
+        h->have_S = false;
+        h->steps_current = false;
+      }
+      return BSF_OK;
     case BSF_OPT_HOST_BANDS:
       if (value < 1 || value > bsf_ctx::kHostBands) return fail(h, BSF_EINVAL, "bad band count %lld", value);
       h->host_bands = (int)value;
@@ -497,6 +541,10 @@ static int filter_impl(bsf_t h, const void* img, int dtype, long long ld, const 
     const int rc = check_d2(h);
     if (rc) return rc;
   }
+  if (h->dirset != BSF_DIRS_CARTESIAN) {
+    if (h->step_rule == BSF_STEP_D2) return fail(h, BSF_EINVAL, "the second direction set: integer steps only");
+    if (!is_fixed(h->precision)) return fail(h, BSF_EINVAL, "the second direction set needs fixed point");
+  }
   if (out_dtype != BSF_F32 && out_dtype != BSF_F64) return fail(h, BSF_EINVAL, "bad out dtype %d", out_dtype);
   if (ldo < h->W) return fail(h, BSF_EINVAL, "ldo %lld < W %d", ldo, h->W);
   if (row0 < 0 || rows <= 0 || row0 + rows > h->H) return fail(h, BSF_EINVAL, "bad row band");
@@ -513,7 +561,7 @@ static int filter_impl(bsf_t h, const void* img, int dtype, long long ld, const 
   if (img) {
     if ((rc = preintegrate_impl(h, img, dtype, ld, row0, rows))) return rc;
   } else if (!h->have_S || h->S_R != h->R || h->S_elem != h->elem || h->S_row0 != row0 ||
-             h->S_rows != rows) {
+             h->S_rows != rows || h->S_dirset != h->dirset) {
     return fail(h, BSF_ESTATE, "img is NULL and no matching pre-integration is held");
   }
   cudaError_t e;
@@ -523,10 +571,14 @@ static int filter_impl(bsf_t h, const void* img, int dtype, long long ld, const 
       e = bsf_launch_stencil_d2(h->precision, h->n, jac ? 1 : 0, h->S, h->pitch, h->R, cov, cov_kind,
                                 h->H, h->W, row0, rows, h->S_q, out, out_dtype, ldo, jac, ldj,
                                 (long long)rows * ldj, nullptr, 0, h->st, h->stream);
-    else
+    else if (h->dirset == BSF_DIRS_CARTESIAN)
       e = bsf_launch_stencil_d1(h->precision, h->n, h->S, h->pitch, h->R, cov, cov_kind,
                                 h->step_rule, h->H, h->W, row0, rows, h->S_q, out, out_dtype, ldo,
                                 h->st, h->stream);
+    else
+      e = bsf_launch_stencil_sets(h->precision, h->n, h->dirset, h->S, h->S2, h->pitch, h->R, cov,
+                                  cov_kind, h->step_rule, h->H, h->W, row0, rows, h->S_q, out,
+                                  out_dtype, ldo, h->st, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "stencil");
   if (h->last_cov != cov || h->last_kind != cov_kind) h->steps_current = false;
@@ -558,6 +610,12 @@ static int ensure_staging(bsf_t h, void*& buf, size_t& have, size_t bytes) {
 static cudaError_t stencil_band(bsf_t h, const float* cov, int cov_kind, int y0, int rows, void* out,
                                 int out_dtype, long long ldo) {
   const void* S = static_cast<const char*>(h->S) + (size_t)y0 * h->pitch * h->elem;
+  if (h->dirset != BSF_DIRS_CARTESIAN) {
+    const void* S2 = h->S2 ? static_cast<const char*>(h->S2) + (size_t)y0 * h->pitch * h->elem : nullptr;
+    return bsf_launch_stencil_sets(h->precision, h->n, h->dirset, S, S2, h->pitch, h->R, cov, cov_kind,
+                                   h->step_rule, h->H, h->W, y0, rows, h->S_q, out, out_dtype, ldo,
+                                   h->st, h->stream);
+  }
   if (h->step_rule == BSF_STEP_D2)
     return bsf_launch_stencil_d2(h->precision, h->n, 0, S, h->pitch, h->R, cov, cov_kind, h->H, h->W,
                                  y0, rows, h->S_q, out, out_dtype, ldo, nullptr, 0, 0, nullptr, 0,
@@ -836,6 +894,7 @@ int bsf_filter_backward_rows(bsf_t h, const float* gout, long long ldg, const fl
   int rc = check_cov_kind(h, cov_kind);
   if (rc) return rc;
   if (h->step_rule == BSF_STEP_D2) return fail(h, BSF_EINVAL, "band backward: integer steps only");
+  if (h->dirset != BSF_DIRS_CARTESIAN) return fail(h, BSF_EINVAL, "backward: Cartesian direction set only");
   if (!gout || !cov || !acc) return fail(h, BSF_EINVAL, "NULL gout, cov or acc");
   if (ldg < h->W || lda < h->W) return fail(h, BSF_EINVAL, "leading dimension < W");
   if (y0 < 0 || y1 <= y0 || y1 > h->H) return fail(h, BSF_EINVAL, "bad row band");
@@ -951,6 +1010,7 @@ int bsf_filter_backward(bsf_t h, const float* gout, long long ldg, const float* 
   if (!h) return BSF_EINVAL;
   int rc = check_cov_kind(h, cov_kind);
   if (rc) return rc;
+  if (h->dirset != BSF_DIRS_CARTESIAN) return fail(h, BSF_EINVAL, "backward: Cartesian direction set only");
   if (h->step_rule == BSF_STEP_D2) {
     if (!gout || !cov) return fail(h, BSF_EINVAL, "NULL gout or cov");
     if (ldg < h->W || (gimg && ldgi < h->W)) return fail(h, BSF_EINVAL, "leading dimension < W");
@@ -1059,9 +1119,13 @@ int bsf_copy_steps(bsf_t h, uint16_t* dst) {
 int bsf_copy_preintegrated(bsf_t h, void* dst) {
   if (!h || !dst) return BSF_EINVAL;
   if (!h->have_S) return fail(h, BSF_ESTATE, "no pre-integration held");
+  const size_t rows = (size_t)h->S_rows + 2 * h->S_R;
   BSF_CUDA(h, cudaMemcpy2DAsync(dst, (size_t)h->Wp * h->elem, h->S, (size_t)h->pitch * h->elem,
-                                (size_t)h->Wp * h->elem, h->S_rows + 2 * h->S_R,
-                                cudaMemcpyDeviceToDevice, h->stream));
+                                (size_t)h->Wp * h->elem, rows, cudaMemcpyDeviceToDevice, h->stream));
+  if (h->S_dirset == BSF_DIRS_PAIR)  // the second set's sums follow the first's
+    BSF_CUDA(h, cudaMemcpy2DAsync(static_cast<char*>(dst) + rows * h->Wp * h->elem, (size_t)h->Wp * h->elem,
+                                  h->S2, (size_t)h->pitch * h->elem, (size_t)h->Wp * h->elem, rows,
+                                  cudaMemcpyDeviceToDevice, h->stream));
   return BSF_OK;
 }
 

@@ -270,7 +270,7 @@ int bsf_batch_plan(bsf_batch_t b, int B, const bsf_image_desc* descs, int flags)
   BSF_BCUDA(b, cudaMemsetAsync(dst, 0, sizeof(DevStatus) * B, b->stream));
   for (int i = 0; i < B; ++i) {
     cudaError_t e = bsf_launch_steps(descs[i].cov, BSF_COV_C, descs[i].H, descs[i].W, b->n,
-                                     b->step_rule, -1, Lf, dst + i, b->stream);
+                                     b->step_rule, BSF_DIRS_CARTESIAN, -1, Lf, dst + i, b->stream);
     if (e != cudaSuccess) { cudaFree(dst); cudaFree(Lf); return bfail(b, BSF_ECUDA, "steps"); }
   }
   BSF_BCUDA(b, cudaMemcpyAsync(hst.data(), dst, sizeof(DevStatus) * B, cudaMemcpyDeviceToHost, b->stream));

@@ -29,7 +29,7 @@ constexpr int kScanChunkMin = 16;
 
 // Launchers; each returns the launch status (cudaGetLastError()).
 cudaError_t bsf_launch_steps(const float* cov, int cov_kind, int H, int W, int n, int rule,
-                             int R, ushort4* Lf, DevStatus* st, cudaStream_t s);
+                             int dirset, int R, ushort4* Lf, DevStatus* st, cudaStream_t s);
 
 cudaError_t bsf_launch_absmax(const void* img, int dtype, long long ld, int H, int W,
                               DevStatus* st, cudaStream_t s);
@@ -139,6 +139,28 @@ cudaError_t bsf_launch_fold128(const void* G, long long pitch, int Hp, int H, in
 // gcov[c][y][x] = gout[y][x] * jac[c][y][x] (jac planes H * ldj apart; gcov [3][H][W]).
 cudaError_t bsf_launch_jacobian_vjp(const float* gout, long long ldg, const float* jac,
                                     long long ldj, float* gcov, int H, int W, cudaStream_t s);
+
+// Stencil of the second direction set (dirset BSF_DIRS_SECOND: S holds its
+// running sums) or of the pair (BSF_DIRS_PAIR: S the Cartesian running sums,
+// S2 the second set's, same pitch).  prec BSF_FIX64 or BSF_FIX128.
+cudaError_t bsf_launch_stencil_sets(int prec, int n, int dirset, const void* S, const void* S2,
+                                    long long pitch, int R, const float* cov, int cov_kind, int rule,
+                                    int H, int W, int row0, int rows, int q, void* out, int out_dtype,
+                                    long long ldo, DevStatus* st, cudaStream_t s);
+
+// Extension + quantisation of the image band onto the padded domain (no
+// running sum): S[yp][xp] = Q(f~(xp - R, row0 + yp - R)); records max |Q| and
+// overflow like bsf_launch_scan_rows.  Fixed point only.
+cudaError_t bsf_launch_extend(int prec, const void* img, int dtype, long long ld, int H, int W, int R,
+                              int row0, int boundary, int q, void* S, long long pitch, int Hp, int Wp,
+                              DevStatus* st, cudaStream_t s);
+
+// n-fold running sums of the second direction set on S in place (three-phase
+// scans): e1 = (2,1) and e4 = (-2,1) on the whole grid, e2 = (1,2) and
+// e3 = (-1,2) on each row parity.  agg holds bsf_second_scan_elems elements.
+size_t bsf_second_scan_elems(int n, int Hp, int Wp, int chunk);
+cudaError_t bsf_launch_scans_second(int prec, int n, void* S, long long pitch, int Hp, int Wp, int chunk,
+                                    void* agg, cudaStream_t s);
 
 // Algorithm 1's split of a field: min over pixels of the condition-2 bound
 // (floored at zero) into *min_bits (device, double bits), then the isotropic

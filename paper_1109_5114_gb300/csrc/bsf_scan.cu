@@ -236,6 +236,29 @@ __device__ __forceinline__ void zero_rows_transfer(T* s, long long m) {
   if constexpr (NF >= 2) s[1] += bsf_mul_int(s[0], m);
 }
 
+// Rows yl of [lo, hi) where the line x = A + B yl lies inside [0, Wp) (the
+// interval shrinks to empty when there are none); B in -2..2.
+__device__ __forceinline__ int floor_div_pos(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+template <int B>
+__device__ __forceinline__ void line_rows(int A, int Wp, int& lo, int& hi) {
+  if constexpr (B == 0) {
+    if (A < 0 || A >= Wp) hi = lo;
+  } else if constexpr (B == 1) {
+    lo = max(lo, -A);
+    hi = min(hi, Wp - A);
+  } else if constexpr (B == -1) {
+    lo = max(lo, A - Wp + 1);
+    hi = min(hi, A + 1);
+  } else if constexpr (B > 0) {  // A + B yl >= 0 and <= Wp - 1
+    lo = max(lo, -floor_div_pos(A, B));
+    hi = min(hi, floor_div_pos(Wp - 1 - A, B) + 1);
+  } else {                       // A - |B| yl <= Wp - 1 and >= 0
+    lo = max(lo, -floor_div_pos(Wp - 1 - A, -B));
+    hi = min(hi, floor_div_pos(A, -B) + 1);
+  }
+  if (hi < lo) hi = lo;
+}
+
 template <typename T, int NF, int SKEW, bool REV>
 __device__ __forceinline__ void vscan_agg_body(const T* __restrict__ S, long long pitch, int Hp,
                                                int Wp, int umin, int Nu, int ch,
@@ -246,17 +269,10 @@ __device__ __forceinline__ void vscan_agg_body(const T* __restrict__ S, long lon
   const int y0 = c * ch, y1 = min(y0 + ch, Hp);
   // in scan order yl the line sits at column x = A + B yl; only the rows with
   // 0 <= x < Wp hold data (the rest of the line is zero)
-  const int A = REV ? u + SKEW * (Hp - 1) : u, B = REV ? -SKEW : SKEW;
+  const int A = REV ? u + SKEW * (Hp - 1) : u;
+  constexpr int B = REV ? -SKEW : SKEW;
   int lo = y0, hi = y1;
-  if (B == 0) {
-    if (A < 0 || A >= Wp) hi = lo;
-  } else if (B == 1) {
-    lo = max(lo, -A);
-    hi = min(hi, Wp - A);
-  } else {
-    lo = max(lo, A - Wp + 1);
-    hi = min(hi, A + 1);
-  }
+  line_rows<B>(A, Wp, lo, hi);
   T s[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) s[f] = 0;
@@ -309,17 +325,11 @@ __device__ __forceinline__ void vscan_apply_body(T* __restrict__ S, long long pi
   const int u = umin + ui;
   const int y0 = c * ch, y1 = min(y0 + ch, Hp);
   // the rows [glo, ghi) (scan order) where the line holds data: column x = A + B yl
-  const int A = REV ? u + SKEW * (Hp - 1) : u, B = REV ? -SKEW : SKEW;
+  const int A = REV ? u + SKEW * (Hp - 1) : u;
+  constexpr int B = REV ? -SKEW : SKEW;
   int glo = 0, ghi = Hp;
-  if (B == 0) {
-    if (A < 0 || A >= Wp) return;
-  } else if (B == 1) {
-    glo = max(0, -A);
-    ghi = min(Hp, Wp - A);
-  } else {
-    glo = max(0, A - Wp + 1);
-    ghi = min(Hp, A + 1);
-  }
+  line_rows<B>(A, Wp, glo, ghi);
+  if (glo >= ghi) return;
   const int lo = max(y0, glo), hi = min(y1, ghi);
   if (lo >= hi) return;  // nothing of this line in this chunk
   // carried-in state: the line is zero before its first chunk with data
@@ -609,8 +619,8 @@ template <typename T, int NF, int SKEW, bool REV>
 cudaError_t launch_v_t(T* S, long long pitch, int Hp, int Wp, int ch, T* agg, T* carry,
                        cudaStream_t s) {
   // u = x - SKEW * y ranges over [umin, umin + Nu)
-  const int umin = SKEW == 1 ? -(Hp - 1) : 0;
-  const int Nu = SKEW == 0 ? Wp : Wp + Hp - 1;
+  const int umin = SKEW > 0 ? -SKEW * (Hp - 1) : 0;
+  const int Nu = Wp + (SKEW < 0 ? -SKEW : SKEW) * (Hp - 1);
   const int nchunks = (Hp + ch - 1) / ch;
   const int threads = 128;
   dim3 grid((Nu + threads - 1) / threads, nchunks);
@@ -846,4 +856,157 @@ cudaError_t bsf_launch_batch_vscan(int n, int skew, const BatchImage* imgs, cons
   else if (n == 3) batch_vscan_n<3>(skew, imgs, starts, B, total, s);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Second direction set (Section 2.3, Algorithm 3, step 2): running sums along
+// e1 = (2,1), e2 = (1,2), e3 = (-1,2), e4 = (-2,1).  No direction runs along
+// a row, so the extension and quantisation get a pass of their own
+// (k_extend); e1 and e4 step one row down and 2 columns across (skew +2 and
+// -2 of the three-phase scan); e2 and e3 step two rows down and one column
+// across, so each row parity is a grid of its own (pitch 2p) on which they
+// are skew +1 and -1 scans; both parities run in one launch (blockIdx.z).
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename T, typename In>
+__global__ void __launch_bounds__(256)
+k_extend(const In* __restrict__ img, long long ld, int H, int W, int R, int row0, int boundary,
+         float scale_f, int q, T* __restrict__ S, long long pitch, int Wp, DevStatus* st) {
+  const int yp = blockIdx.x;  // padded row (grid x: up to 2^31 - 1 rows)
+  const int xp = blockIdx.y * 256 + threadIdx.x;
+  bool yvalid;
+  const int ys = bsf_map_index(row0 + yp - R, H, boundary, yvalid);
+  float amax = 0.f;
+  bool ok = true;
+  if (xp < Wp) {
+    T v = (T)0;
+    bool xvalid;
+    const int xs = bsf_map_index(xp - R, W, boundary, xvalid);
+    if (yvalid && xvalid) v = quantize_one<T, In>(img[(long long)ys * ld + xs], q, scale_f, ok, amax);
+    S[(long long)yp * pitch + xp] = v;
+  }
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  const bool bad = __any_sync(0xffffffffu, !ok);
+  if ((threadIdx.x & 31) == 0) {
+    bsf_atomic_max_pos_float(&st->max_absq_bits, amax);
+    if (bad) bsf_set_error(st, BSF_EOVERFLOW);
+  }
+}
+
+template <typename T>
+cudaError_t launch_extend_t(const void* img, int dtype, long long ld, int H, int W, int R, int row0,
+                            int boundary, int q, T* S, long long pitch, int Hp, int Wp, DevStatus* st,
+                            cudaStream_t s) {
+  const float scale = ldexpf(1.f, q);
+  const dim3 grid(Hp, (Wp + 255) / 256);
+  switch (dtype) {
+    case BSF_U8:
+      k_extend<T, uint8_t><<<grid, 256, 0, s>>>((const uint8_t*)img, ld, H, W, R, row0, boundary, scale, q,
+                                                S, pitch, Wp, st);
+      break;
+    case BSF_F32:
+      k_extend<T, float><<<grid, 256, 0, s>>>((const float*)img, ld, H, W, R, row0, boundary, scale, q, S,
+                                              pitch, Wp, st);
+      break;
+    case BSF_F64:
+      k_extend<T, double><<<grid, 256, 0, s>>>((const double*)img, ld, H, W, R, row0, boundary, scale, q,
+                                               S, pitch, Wp, st);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// One row parity of a grid scanned two rows per step: rows par, par + 2, ...
+struct ParityGrid {
+  int Hs, umin, Nu;
+};
+template <int SKEW>
+__device__ __forceinline__ ParityGrid parity_grid(int Hp, int Wp, int par) {
+  ParityGrid g;
+  g.Hs = (Hp - par + 1) / 2;
+  g.umin = SKEW > 0 ? -(g.Hs - 1) : 0;
+  g.Nu = Wp + g.Hs - 1;
+  return g;
+}
+
+template <typename T, int NF, int SKEW>
+__global__ void __launch_bounds__(128)
+k_vscan_agg_par(const T* __restrict__ S, long long pitch, int Hp, int Wp, int ch, T* __restrict__ agg,
+                long long agg_stride) {
+  const int par = blockIdx.z;
+  const ParityGrid g = parity_grid<SKEW>(Hp, Wp, par);
+  if (g.Hs <= 0) return;
+  vscan_agg_body<T, NF, SKEW, false>(S + par * pitch, 2 * pitch, g.Hs, Wp, g.umin, g.Nu, ch,
+                                     agg + par * agg_stride, blockIdx.x, blockIdx.y);
+}
+
+template <typename T, int NF, int SKEW>
+__global__ void __launch_bounds__(128)
+k_vscan_apply_par(T* __restrict__ S, long long pitch, int Hp, int Wp, int ch, const T* __restrict__ agg,
+                  long long agg_stride) {
+  const int par = blockIdx.z;
+  const ParityGrid g = parity_grid<SKEW>(Hp, Wp, par);
+  if (g.Hs <= 0) return;
+  vscan_apply_body<T, NF, SKEW, false>(S + par * pitch, 2 * pitch, g.Hs, Wp, g.umin, g.Nu, ch,
+                                       agg + par * agg_stride, blockIdx.x, blockIdx.y);
+}
+
+template <typename T, int NF, int SKEW>
+cudaError_t launch_par_t(T* S, long long pitch, int Hp, int Wp, int ch, T* agg, cudaStream_t s) {
+  const int Hs0 = (Hp + 1) / 2;  // rows of parity 0 (the larger)
+  const int Nu0 = Wp + Hs0 - 1;
+  const int nch = (Hs0 + ch - 1) / ch;
+  const long long stride = (long long)nch * NF * Nu0;
+  dim3 grid((Nu0 + 127) / 128, nch, Hp > 1 ? 2 : 1);
+  k_vscan_agg_par<T, NF, SKEW><<<grid, 128, 0, s>>>(S, pitch, Hp, Wp, ch, agg, stride);
+  k_vscan_apply_par<T, NF, SKEW><<<grid, 128, 0, s>>>(S, pitch, Hp, Wp, ch, agg, stride);
+  return cudaGetLastError();
+}
+
+template <typename T, int NF>
+cudaError_t launch_second_t(T* S, long long pitch, int Hp, int Wp, int ch, T* agg, cudaStream_t s) {
+  cudaError_t e;
+  // the n folds of each direction are inside each scan; order: e1, e2, e3, e4
+  if ((e = launch_v_t<T, NF, 2, false>(S, pitch, Hp, Wp, ch, agg, nullptr, s)) != cudaSuccess) return e;
+  if ((e = launch_par_t<T, NF, 1>(S, pitch, Hp, Wp, ch, agg, s)) != cudaSuccess) return e;
+  if ((e = launch_par_t<T, NF, -1>(S, pitch, Hp, Wp, ch, agg, s)) != cudaSuccess) return e;
+  return launch_v_t<T, NF, -2, false>(S, pitch, Hp, Wp, ch, agg, nullptr, s);
+}
+
+}  // namespace
+
+cudaError_t bsf_launch_extend(int prec, const void* img, int dtype, long long ld, int H, int W, int R,
+                              int row0, int boundary, int q, void* S, long long pitch, int Hp, int Wp,
+                              DevStatus* st, cudaStream_t s) {
+  if (prec == BSF_FIX64)
+    return launch_extend_t<uint64_t>(img, dtype, ld, H, W, R, row0, boundary, q, (uint64_t*)S, pitch, Hp,
+                                     Wp, st, s);
+  if (prec == BSF_FIX128)
+    return launch_extend_t<u128>(img, dtype, ld, H, W, R, row0, boundary, q, (u128*)S, pitch, Hp, Wp, st,
+                                 s);
+  return cudaErrorInvalidValue;
+}
+
+size_t bsf_second_scan_elems(int n, int Hp, int Wp, int chunk) {
+  // skew +-2 on the whole grid: nchunks x n x (Wp + 2 (Hp - 1)); the parity
+  // grids need 2 x ceil(Hs0 / chunk) x n x (Wp + Hs0 - 1), Hs0 = ceil(Hp / 2)
+  const size_t full = (size_t)((Hp + chunk - 1) / chunk) * n * ((size_t)Wp + 2 * (size_t)(Hp - 1));
+  const int Hs0 = (Hp + 1) / 2;
+  const size_t par = 2 * (size_t)((Hs0 + chunk - 1) / chunk) * n * ((size_t)Wp + Hs0 - 1);
+  return full > par ? full : par;
+}
+
+cudaError_t bsf_launch_scans_second(int prec, int n, void* S, long long pitch, int Hp, int Wp, int chunk,
+                                    void* agg, cudaStream_t s) {
+  switch (prec * 10 + n) {
+    case 11: return launch_second_t<uint64_t, 1>((uint64_t*)S, pitch, Hp, Wp, chunk, (uint64_t*)agg, s);
+    case 12: return launch_second_t<uint64_t, 2>((uint64_t*)S, pitch, Hp, Wp, chunk, (uint64_t*)agg, s);
+    case 13: return launch_second_t<uint64_t, 3>((uint64_t*)S, pitch, Hp, Wp, chunk, (uint64_t*)agg, s);
+    case 21: return launch_second_t<u128, 1>((u128*)S, pitch, Hp, Wp, chunk, (u128*)agg, s);
+    case 22: return launch_second_t<u128, 2>((u128*)S, pitch, Hp, Wp, chunk, (u128*)agg, s);
+    case 23: return launch_second_t<u128, 3>((u128*)S, pitch, Hp, Wp, chunk, (u128*)agg, s);
+    default: return cudaErrorInvalidValue;
+  }
 }

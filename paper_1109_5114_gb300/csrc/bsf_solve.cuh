@@ -113,6 +113,110 @@ __device__ __forceinline__ bool pixel_steps(float C11, float C12, float C22, int
 }
 
 // ---------------------------------------------------------------------------
+// The second box spline beta'_a (Section 2.3): boxes along the grid vectors
+// e_1 = (2, 1), e_2 = (1, 2), e_3 = (-1, 2), e_4 = (-2, 1), |e_k|^2 = 5, with
+// covariance (n/12) sum_k A_k e_k e_k^T / 5.  With M = (12/n) C, carried
+// times 3: P3 = 4 M11 - M22 = 3 (A1 + A4), Q3 = 4 M22 - M11 = 3 (A2 + A3),
+// m3 = 7.5 M12 = 3 (A1 + A2 - A3 - A4); the family is
+//   3A = (T, (P3 + Q3 + m3)/2 - T, (Q3 - P3 - m3)/2 + T, P3 - T),
+// feasible iff P3, Q3 >= 0 and |m3| <= P3 + Q3 (beyond: clamped, flag 1).
+// The kurtosis sum_k A_k^2 u_k u_k^T of Section 2.3 has, along the family,
+// the stationarity cubic V^3 + p V + q = 0 with T = P3/2 + m3/4 + V,
+//   p = (50 (P3^2 + Q3^2) + 32 (P3 - Q3)^2 + 43 m3^2) / 400 > 0,
+//   q = m3 (P3 - Q3) (P3 + Q3) / 32,
+// solved like the Cartesian one: two Newton steps from -q/p.  A holds 3A_k.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ Solved solve_scales_k(float C11, float C12, float C22, float B) {
+  Solved r;
+  r.flags = 0;
+  if (!(isfinite(C11) && isfinite(C12) && isfinite(C22))) {
+    r.flags |= 2;
+    C11 = 0.f; C12 = 0.f; C22 = 0.f;
+  }
+  const float c11 = fmaxf(C11, 0.f), c22 = fmaxf(C22, 0.f);
+  const float m11 = __fmul_rn(B, c11), m22 = __fmul_rn(B, c22), m12 = __fmul_rn(B, C12);
+  float P3 = __fsub_rn(__fmul_rn(4.f, m11), m22);
+  float Q3 = __fsub_rn(__fmul_rn(4.f, m22), m11);
+  float m3 = __fmul_rn(7.5f, m12);
+  if (P3 < 0.f) { P3 = 0.f; r.flags |= 1; }
+  if (Q3 < 0.f) { Q3 = 0.f; r.flags |= 1; }
+  const float S3 = __fadd_rn(P3, Q3);
+  if (fabsf(m3) > S3) { m3 = copysignf(S3, m3); r.flags |= 1; }
+  const float dPQ = __fsub_rn(P3, Q3);
+  const float p = __fdiv_rn(
+      __fadd_rn(__fadd_rn(__fmul_rn(50.f, __fadd_rn(__fmul_rn(P3, P3), __fmul_rn(Q3, Q3))),
+                          __fmul_rn(32.f, __fmul_rn(dPQ, dPQ))),
+                __fmul_rn(43.f, __fmul_rn(m3, m3))),
+      400.f);
+  const float q = __fmul_rn(__fmul_rn(__fmul_rn(m3, dPQ), S3), 0.03125f);
+  float v = (p > 0.f) ? __fdiv_rn(-q, p) : 0.f;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const float v2 = __fmul_rn(v, v);
+    const float h = __fadd_rn(__fmul_rn(__fadd_rn(v2, p), v), q);
+    const float dh = __fadd_rn(__fmul_rn(3.f, v2), p);
+    if (dh > 0.f) v = __fsub_rn(v, __fdiv_rn(h, dh));
+  }
+  float T = __fadd_rn(__fadd_rn(__fmul_rn(0.5f, P3), __fmul_rn(0.25f, m3)), v);
+  const float half = __fmul_rn(0.5f, __fadd_rn(S3, m3));
+  T = fminf(fmaxf(T, fmaxf(__fmul_rn(0.5f, __fadd_rn(dPQ, m3)), 0.f)), fminf(P3, half));
+  r.A[0] = fmaxf(T, 0.f);
+  r.A[1] = fmaxf(__fsub_rn(half, T), 0.f);
+  r.A[2] = fmaxf(__fadd_rn(__fmul_rn(0.5f, __fsub_rn(__fsub_rn(Q3, P3), m3)), T), 0.f);
+  r.A[3] = fmaxf(__fsub_rn(P3, T), 0.f);
+  return r;
+}
+
+// Largest |offset| of the taps of beta'_a: along e_k the offsets run from
+// -n(L+1)/2 to n(L-1)/2 units of e_k.
+__device__ __forceinline__ int tap_reach_k(const int L[4], int n) {
+  int lo[4], hi[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) { lo[k] = -(n * (L[k] + 1)) / 2; hi[k] = (n * (L[k] - 1)) / 2; }
+  const int xr = max(-(2 * lo[0] + lo[1] - hi[2] - 2 * hi[3]), 2 * hi[0] + hi[1] - lo[2] - 2 * lo[3]);
+  const int yr = max(-(lo[0] + 2 * lo[1] + 2 * lo[2] + lo[3]), hi[0] + 2 * hi[1] + 2 * hi[2] + hi[3]);
+  return max(xr, yr);
+}
+
+__device__ __forceinline__ bool pixel_steps_k(float C11, float C12, float C22, int n, int rule,
+                                              int R, int L[4], int& flags, int& reach) {
+  Solved sv = solve_scales_k(C11, C12, C22, scale_of_order(n));
+  flags = sv.flags;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float a = __fdiv_rn(sv.A[k], 15.f);  // A / |e_k|^2 from 3A
+    const float lam = (rule == BSF_STEP_D1_PAPER) ? __fsqrt_rn(a) : __fsqrt_rn(__fadd_rn(1.f, a));
+    L[k] = round_step(lam, n);
+  }
+  reach = tap_reach_k(L, n);
+  if (R >= 0 && reach > R) {
+    L[0] = L[1] = L[2] = L[3] = 1;
+    reach = tap_reach_k(L, n);
+    return false;
+  }
+  return true;
+}
+
+// Algorithm 2's sector: beta'_a where its elongation bound is the larger one,
+// i.e. |C11 - C22| < 3 |C12| < 6 |C11 - C22| (|C11 - C22| rounded once to
+// float64; 3|C12| and 2|C11 - C22| are exact there).
+__device__ __forceinline__ bool use_second_set(float C11, float C12, float C22) {
+  const double d = fabs(__dsub_rn((double)C11, (double)C22));
+  const double a = fabs((double)C12);
+  return d < 3.0 * a && a < 2.0 * d;
+}
+
+// Direction sets of the integer-step filter (BSF_DIRS_*): steps of one pixel
+// for the set the context uses; `second` says which set the pixel takes.
+__device__ __forceinline__ bool pixel_steps_set(int dirset, float C11, float C12, float C22, int n,
+                                                int rule, int R, int L[4], int& flags, int& reach,
+                                                bool& second) {
+  second = dirset == BSF_DIRS_SECOND || (dirset == BSF_DIRS_PAIR && use_second_set(C11, C12, C22));
+  return second ? pixel_steps_k(C11, C12, C22, n, rule, R, L, flags, reach)
+                : pixel_steps(C11, C12, C22, n, rule, R, L, flags, reach);
+}
+
+// ---------------------------------------------------------------------------
 // Float32 elementary functions for the log-parameter fields, written out as
 // fixed sequences of IEEE round-to-nearest operations (no contraction), so
 // that any IEEE float32 implementation of the same steps gives the same bits.

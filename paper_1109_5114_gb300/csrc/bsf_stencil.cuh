@@ -1,0 +1,179 @@
+// Per-pixel finite differences on the running sums (Section 1.1: the 16-tap
+// finite-difference mesh of the BoxFilter algorithm, generalised to order n,
+// whose mesh grows to (n+1)^4 taps -- Section 2.1 counts 2^N points per
+// order, two per box distribution).
+//
+// For pixel p with integer steps L_k and centring c_k = n (L_k - 1)/2:
+//   acc = sum_{t in {0..n}^4} prod_k (-1)^t_k C(n, t_k) S(p + sum_k (c_k - t_k L_k) d_k)
+// evaluated exactly modulo 2^b as the nested order-n backward differences
+// along d1, d2, d3, d4 (innermost first), then
+//   out = RN32(RN32(acc) 2^-q) / RN32(D)  or  RN64(RN64(acc) 2^-q) / RN64(D),
+//   D = prod_k L_k^n.
+// One thread per output pixel; a warp covers 32 consecutive pixels of a row,
+// so each tap is a coalesced row segment of S whenever neighbouring pixels
+// share their steps (the covariance field is smooth).  The second direction
+// set of Section 2.3 (Table 1's mesh of Algorithm 3) is the same stencil
+// along e1 = (2,1), e2 = (1,2), e3 = (-1,2), e4 = (-2,1).
+//
+// Shared by the kernels of bsf_stencil.cu (first direction set, batches) and
+// bsf_stencil_second.cu (second set, and the pair of Algorithm 2).
+#pragma once
+
+#include <type_traits>
+
+#include "bsf_solve.cuh"
+
+namespace {
+
+// Nested order-n differences.  Taps are addressed by 32-bit element indices
+// into S (the padded domain holds fewer than 2^31 elements); level LVL applies
+// the difference along direction LVL-1 (stride s[LVL-1] elements) to level
+// LVL-1, and level 0 loads one element.
+template <typename T, int NF, int LVL>
+__device__ __forceinline__ T comb(const T* __restrict__ S, int idx, const int* s) {
+  if constexpr (LVL == 0) {
+    return bsf_load(S + idx);
+  } else {
+    const int sk = s[LVL - 1];
+    const T v0 = comb<T, NF, LVL - 1>(S, idx, s);
+    const T v1 = comb<T, NF, LVL - 1>(S, idx - sk, s);
+    if constexpr (NF == 1) {
+      return v0 - v1;
+    } else if constexpr (NF == 2) {
+      const T v2 = comb<T, NF, LVL - 1>(S, idx - 2 * sk, s);
+      return (v0 + v2) - (v1 + v1);
+    } else {
+      const T v2 = comb<T, NF, LVL - 1>(S, idx - 2 * sk, s);
+      const T v3 = comb<T, NF, LVL - 1>(S, idx - 3 * sk, s);
+      const T a = v1 - v2;
+      return (v0 - v3) - (a + a + a);
+    }
+  }
+}
+
+template <typename T> __device__ __forceinline__ float to_f32(T acc, T D);
+template <> __device__ __forceinline__ float to_f32<uint64_t>(uint64_t acc, uint64_t D) {
+  (void)D;
+  return bsf_rn32_i64((long long)acc);
+}
+template <> __device__ __forceinline__ float to_f32<u128>(u128 acc, u128 D) {
+  (void)D;
+  return bsf_rn32((i128)acc);
+}
+template <typename T> __device__ __forceinline__ double to_f64(T acc);
+template <> __device__ __forceinline__ double to_f64<uint64_t>(uint64_t acc) {
+  return __ll2double_rn((long long)acc);
+}
+template <> __device__ __forceinline__ double to_f64<u128>(u128 acc) { return bsf_rn64((i128)acc); }
+
+template <typename T> __device__ __forceinline__ float mass_f32(T D);
+template <> __device__ __forceinline__ float mass_f32<uint64_t>(uint64_t D) { return bsf_rn32_u64(D); }
+template <> __device__ __forceinline__ float mass_f32<u128>(u128 D) { return bsf_rn32_u(D); }
+template <typename T> __device__ __forceinline__ double mass_f64(T D);
+template <> __device__ __forceinline__ double mass_f64<uint64_t>(uint64_t D) { return __ull2double_rn(D); }
+template <> __device__ __forceinline__ double mass_f64<u128>(u128 D) { return bsf_rn64_u(D); }
+
+// Resident blocks per SM requested from the register allocator: enough warps
+// to cover the latency of the (n+1)^4 gathers.
+template <typename T, int NF> struct StencilOcc {
+  static constexpr int value = sizeof(T) == 8 ? (NF == 1 ? 6 : NF == 2 ? 4 : 1) : (NF == 1 ? 4 : NF == 2 ? 2 : 1);
+};
+
+// The step solve of bsf_solve.cuh runs here, per pixel, so its arithmetic
+// overlaps the gathers of other warps and no step field goes through HBM.
+// DS (BSF_DIRS_*): the direction set.  BSF_DIRS_CARTESIAN takes the taps
+// from S along d1..d4; BSF_DIRS_SECOND from S along e1 = (2,1), e2 = (1,2),
+// e3 = (-1,2), e4 = (-2,1); BSF_DIRS_PAIR chooses per pixel between S
+// (Cartesian running sums) and S2 (running sums of the second set), which
+// share one pitch.
+template <typename T, int NF, typename Out, int DS = BSF_DIRS_CARTESIAN>
+__device__ __forceinline__ void stencil_d1_body(const T* __restrict__ S, const T* __restrict__ S2,
+                                                long long pitch, int R,
+                                                const float* __restrict__ cov, int kind, int rule, int H,
+                                                int W, int row0, int rows, float scale_f,
+                                                double scale_d, Out* __restrict__ out,
+                                                long long ldo, DevStatus* st, int bx, int by) {
+  // pixel (x, row0 + y) of an H x W image; rows [row0, row0 + rows) are
+  // filtered from running sums whose padded row 0 is image row row0 - R
+  const int x = bx * 32 + threadIdx.x;
+  const int y = by * blockDim.y + threadIdx.y;
+  if (x >= W || y >= rows) return;
+  const long long HW = (long long)H * W, i = (long long)(row0 + y) * W + x;
+  int L[4], flags, reach;
+  float C11, C12, C22;
+  bsf_solve::load_cov(cov, kind, HW, i, C11, C12, C22);
+  bool second = false;
+  bool in_reach;
+  if constexpr (DS == BSF_DIRS_CARTESIAN)
+    in_reach = bsf_solve::pixel_steps(C11, C12, C22, NF, rule, R, L, flags, reach);
+  else
+    in_reach = bsf_solve::pixel_steps_set(DS, C11, C12, C22, NF, rule, R, L, flags, reach, second);
+  {  // rare-event counters, aggregated per warp
+    const unsigned act = __activemask();
+    const unsigned mc = __ballot_sync(act, flags & 1), mb = __ballot_sync(act, flags & 2),
+                   mr = __ballot_sync(act, !in_reach);
+    if ((mc | mb | mr) && (threadIdx.x & 31) == __ffs(act) - 1) {
+      if (mc) atomicAdd(&st->clamp_count, (unsigned)__popc(mc));
+      if (mb) { atomicAdd(&st->bad_count, (unsigned)__popc(mb)); bsf_set_error(st, BSF_ECOV); }
+      if (mr) { atomicAdd(&st->range_count, (unsigned)__popc(mr)); bsf_set_error(st, BSF_ERANGE); }
+    }
+  }
+  const int L1 = L[0], L2 = L[1], L3 = L[2], L4w = L[3];
+  // element strides of d1 = (1,0), d2 = (1,1), d3 = (0,1), d4 = (-1,1), or
+  // of e1 = (2,1), e2 = (1,2), e3 = (-1,2), e4 = (-2,1)
+  const int p32 = (int)pitch;
+  int e1 = 1, e2 = p32 + 1, e3 = p32, e4 = p32 - 1;
+  const T* Sp = S;
+  if constexpr (DS != BSF_DIRS_CARTESIAN) {
+    if (second) {
+      e1 = p32 + 2; e2 = 2 * p32 + 1; e3 = 2 * p32 - 1; e4 = p32 - 2;
+      if constexpr (DS == BSF_DIRS_PAIR) Sp = S2;
+    }
+  }
+  const int c1 = NF * (L1 - 1) / 2, c2 = NF * (L2 - 1) / 2, c3 = NF * (L3 - 1) / 2,
+            c4 = NF * (L4w - 1) / 2;
+  const int base = (y + R) * p32 + (x + R) + c1 * e1 + c2 * e2 + c3 * e3 + c4 * e4;
+  const int s[4] = {L1 * e1, L2 * e2, L3 * e3, L4w * e4};
+  const T acc = comb<T, NF, 4>(Sp, base, s);
+
+  if constexpr (IsFixed<T>::value) {
+    // D = prod_k L_k^n (exact) and the bound max|Q| * D < 2^(b-1) that makes
+    // the modular accumulator equal the true one (checked in float32 with a
+    // margin far above its rounding: |acc| <= D max|Q| and max|Q| <= bound + 1/2)
+    T D = 1;
+    const T D1 = (T)(unsigned)(L1 * L2) * (T)(unsigned)(L3 * L4w);
+    const float Df1 = (float)(L1 * L2) * (float)(L3 * L4w);
+    float Df = Df1;
+#pragma unroll
+    for (int j = 0; j < NF; ++j) D *= D1;
+#pragma unroll
+    for (int j = 1; j < NF; ++j) Df *= Df1;
+    const float maxq = __uint_as_float(st->max_absq_bits) + 1.f;
+    const float lim = bsf_pow2_f32(ElemBits<T>::value - 1);
+    if (maxq * Df * 1.0001f >= lim) {
+      atomicAdd(&st->overflow_count, 1u);
+      bsf_set_error(st, BSF_EOVERFLOW);
+    }
+    if constexpr (sizeof(Out) == 4) {
+      const float xa = __fmul_rn(to_f32<T>(acc, D), scale_f);
+      out[(long long)(y) * ldo + x] = __fdiv_rn(xa, mass_f32<T>(D));
+    } else {
+      const double xa = __dmul_rn(to_f64<T>(acc), scale_d);
+      out[(long long)(y) * ldo + x] = __ddiv_rn(xa, mass_f64<T>(D));
+    }
+  } else {
+    // floating-point precision variants: acc / prod L^n
+    double Dd = 1.0;
+    const double D1 = (double)(L1 * L2) * (double)(L3 * L4w);
+#pragma unroll
+    for (int j = 0; j < NF; ++j) Dd *= D1;
+    double a;
+    if constexpr (std::is_same<T, double>::value) a = acc;
+    else a = (double)acc.hi + (double)acc.lo;
+    const double v = a / Dd;
+    if constexpr (sizeof(Out) == 4) out[(long long)(y) * ldo + x] = __double2float_rn(v);
+    else out[(long long)(y) * ldo + x] = v;
+  }
+}
+
+}  // namespace

@@ -8,8 +8,10 @@ using namespace bsf_solve;
 
 // rule BSF_STEP_D2: Lf holds floor(lambda~) (capped at 65535) and the mass is
 // that of the interpolated kernels (prod_k M_k, times 2^40).
+// dirset (BSF_DIRS_*): the direction set of the integer-step rules; with
+// BSF_DIRS_PAIR bit 15 of L1 marks the pixels that take the second set.
 __global__ void k_steps(const float* __restrict__ cov, int kind, int H, int W, int n, int rule,
-                        int R, ushort4* __restrict__ Lf, DevStatus* st) {
+                        int dirset, int R, ushort4* __restrict__ Lf, DevStatus* st) {
   const long long HW = (long long)H * W;
   int my_reach = 0;
   float my_mass = 1.f;
@@ -29,11 +31,13 @@ __global__ void k_steps(const float* __restrict__ cov, int kind, int H, int W, i
         L[k] = min(Hq[k] >> 9, 65535);
       }
     } else {
-      if (!pixel_steps(C11, C12, C22, n, rule, R, L, flags, reach)) ++my_range;
+      bool second;
+      if (!pixel_steps_set(dirset, C11, C12, C22, n, rule, R, L, flags, reach, second)) ++my_range;
       // prod L^n in float32 (a bound for the choice of q; the stencil checks exactly)
       const float m1 = (float)(L[0] * L[1]) * (float)(L[2] * L[3]);
       mass = m1;
       for (int j = 1; j < n; ++j) mass *= m1;
+      if (dirset == BSF_DIRS_PAIR && second) L[0] |= 0x8000;
     }
     my_reach = max(my_reach, reach);
     my_mass = fmaxf(my_mass, mass);
@@ -97,12 +101,13 @@ int grid_for(long long work, int threads) {
 }  // namespace
 
 cudaError_t bsf_launch_steps(const float* cov, int cov_kind, int H, int W, int n, int rule,
-                             int R, ushort4* Lf, DevStatus* st, cudaStream_t s) {
+                             int dirset, int R, ushort4* Lf, DevStatus* st, cudaStream_t s) {
   if (cov_kind != BSF_COV_C && cov_kind != BSF_COV_LOGSIG_THETA_LOGRHO) return cudaErrorInvalidValue;
-  if (rule == BSF_STEP_D2 && n > 2) return cudaErrorInvalidValue;
+  if (rule == BSF_STEP_D2 && (n > 2 || dirset != BSF_DIRS_CARTESIAN)) return cudaErrorInvalidValue;
+  if (dirset < BSF_DIRS_CARTESIAN || dirset > BSF_DIRS_PAIR) return cudaErrorInvalidValue;
   const int threads = 256;
-  k_steps<<<grid_for((long long)H * W, threads), threads, 0, s>>>(cov, cov_kind, H, W, n, rule, R,
-                                                                  Lf, st);
+  k_steps<<<grid_for((long long)H * W, threads), threads, 0, s>>>(cov, cov_kind, H, W, n, rule,
+                                                                  dirset, R, Lf, st);
   return cudaGetLastError();
 }
 

@@ -12,13 +12,14 @@ def torch_mod():
 
 
 def run_gpu(img, cov, n, boundary, q, precision=1, out_dtype=np.float32, max_reach=-1,
-            step_rule=0, want_S=False, want_steps=False):
-    """Forward filter on cuda:0; returns dict(out, R, q, info[, S, L])."""
+            step_rule=0, want_S=False, want_steps=False, directions=0):
+    """Forward filter on cuda:0; returns dict(out, R, q, info[, S, L]).  With
+    directions = BSF_DIRS_PAIR, S is the pair (first set's, second set's)."""
     torch = torch_mod()
     from paper_1109_5114_gb300 import bsf
     H, W = img.shape
     f = bsf.BoxSplineFilter(H, W, n, boundary, max_reach=max_reach, precision=precision,
-                            frac_bits=q, step_rule=step_rule)
+                            frac_bits=q, step_rule=step_rule, directions=directions)
     ti = torch.from_numpy(np.ascontiguousarray(img)).cuda()
     tc = torch.from_numpy(np.ascontiguousarray(cov, dtype=np.float32)).cuda()
     tdt = torch.float32 if np.dtype(out_dtype) == np.float32 else torch.float64
@@ -28,15 +29,21 @@ def run_gpu(img, cov, n, boundary, q, precision=1, out_dtype=np.float32, max_rea
     info = f.info()
     res = dict(out=out.cpu().numpy(), R=info.R, q=info.frac_bits, info=info, status=st)
     if want_steps:
-        res["L"] = f.steps().cpu().numpy().astype(np.int64) & 0xFFFF
+        L = f.steps().cpu().numpy().astype(np.int64) & 0xFFFF
+        res["L"] = L & 0x7FFF if directions == 2 else L
+        if directions == 2:
+            res["second"] = (L[0] & 0x8000) != 0
     if want_S:
         raw, inf = f.preintegrated()
         raw = raw.cpu().numpy()
+        sets = 2 if directions == 2 else 1
         if inf.elem_bytes == 8:
-            res["S"] = raw.view(np.uint64).reshape(inf.Hp, inf.Wp)
+            S = raw.view(np.uint64).reshape(sets, inf.Hp, inf.Wp)
+            S = [S[i] for i in range(sets)]
         else:
-            v = raw.view(np.uint64).reshape(inf.Hp, inf.Wp, 2)
-            res["S"] = (v[..., 0].copy(), v[..., 1].copy())
+            v = raw.view(np.uint64).reshape(sets, inf.Hp, inf.Wp, 2)
+            S = [(v[i, ..., 0].copy(), v[i, ..., 1].copy()) for i in range(sets)]
+        res["S"] = S[0] if sets == 1 else tuple(S)
     f.close()
     return res
 
@@ -50,6 +57,12 @@ def oracle_S(img, n, boundary, q, R, bits):
     fq = quantize(img, q, as_object=(bits == 128))
     fe = kernels.extend_image(fq, R, boundary)
     return modular.preintegrate(fe, n, bits)
+
+
+def oracle_S_second(img, n, boundary, q, R, bits):
+    from oracle import knight
+    fq = quantize(img, q, as_object=(bits == 128))
+    return knight.preintegrate_k(kernels.extend_image(fq, R, boundary), n, bits)
 
 
 def oracle_steps(cov, n, rule="corrected"):
