@@ -283,6 +283,48 @@ def run_gpu(args):
                   "R": tp.info().R, "passes": 2}
     tp.close()
 
+    # ---- the second direction set (Algorithm 3) and the pair (Algorithm 2) --
+    # same workload; each its own context (plan, running sums, stencil)
+    def time_dirs(directions):
+        g = bsf.BoxSplineFilter(H, W, ORDER, "symmetric", precision=1, frac_bits=-1, value_bound=vmax,
+                                directions=directions)
+        g.set_option(bsf.BSF_OPT_SCAN_MODE, bsf.BSF_SCAN_THREE_PHASE)
+        o = torch.empty_like(d_out)
+        g.plan(d_cov)
+        for _ in range(args.warmup):
+            flush.zero_()
+            g.filter(d_img, d_cov, out=o)
+        torch.cuda.synchronize()
+        g.set_profiling(True)
+        g.read_profile()
+        for _ in range(args.steps):
+            flush.zero_()
+            g.filter(d_img, d_cov, out=o)
+        pr = g.read_profile()
+        g.set_profiling(False)
+        es = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ee = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        barrier(world)
+        t0 = time.time()
+        for i in range(args.steps):
+            flush.zero_()
+            es[i].record(stream)
+            g.filter(d_img, d_cov, out=o)
+            ee[i].record(stream)
+        torch.cuda.synchronize()
+        clk.mark(t0, time.time())
+        barrier(world)
+        ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(es, ee)), world)
+        if g.status() != 0:
+            raise RuntimeError(f"device status (directions {directions})")
+        gi = g.info()
+        g.close()
+        return {"ms_per_step": round(ms / args.steps, 5), "R": gi.R, "clamped_px": gi.clamp_count,
+                "phases_ms": {k: round(v / max(c, 1), 5) for k, (v, c) in pr.items() if c}}, ms
+
+    second, second_ms = time_dirs(bsf.BSF_DIRS_SECOND)
+    pair, pair_ms = time_dirs(bsf.BSF_DIRS_PAIR)
+
     # ---- forward + backward (image gradient of <out, gout>) ---------------
     gen = torch.Generator(device="cuda").manual_seed(0)
     d_gout = torch.randn((H, W), generator=gen, device="cuda", dtype=torch.float32)
@@ -364,6 +406,9 @@ def run_gpu(args):
     fp64_form["speedup_of_fixed_point"] = round(value / fp64_form["value"], 3)
     algorithm1["value"] = round(world * px * args.steps / (tp_ms * 1e-3) / 1e6, 2)
     algorithm1["unit"] = UNIT
+    for d, ms in ((second, second_ms), (pair, pair_ms)):
+        d["value"] = round(world * px * args.steps / (ms * 1e-3) / 1e6, 2)
+        d["unit"] = UNIT
     fb_value = world * px * args.steps / (fb_ms * 1e-3) / 1e6
     e2e_value = world * px * args.steps / (e2e_ms * 1e-3) / 1e6
 
@@ -414,6 +459,8 @@ def run_gpu(args):
         "gpu_launches": launches,
         "fp64_form": fp64_form,
         "algorithm1": algorithm1,
+        "algorithm3_second_set": second,
+        "algorithm2_pair": pair,
         "fwd_bwd": {"value": round(fb_value, 2), "unit": UNIT,
                     "ms_per_step": round(fb_ms / args.steps, 5),
                     "phases_ms": {k: round(ms / max(c, 1), 5) for k, (ms, c) in prof_fb.items() if c}},
@@ -433,7 +480,7 @@ def run_gpu(args):
 
 
 KERNEL_SOURCES = {
-    "stencil": ["bsf_stencil.cu", "bsf_solve.cuh", "bsf_device.cuh", "bsf_internal.h"],
+    "stencil": ["bsf_stencil.cu", "bsf_stencil.cuh", "bsf_solve.cuh", "bsf_device.cuh", "bsf_internal.h"],
     "stencil_d2": ["bsf_continuous.cuh", "bsf_continuous128.cu", "bsf_solve.cuh", "bsf_device.cuh",
                    "bsf_internal.h"],
 }

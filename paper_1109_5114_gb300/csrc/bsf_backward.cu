@@ -15,6 +15,7 @@
 // sums wrap modulo 2^64, and gimg = RN32(acc) 2^-qg.
 #include <cstring>
 
+#include "bsf_reduce.cuh"
 #include "bsf_solve.cuh"
 
 namespace {
@@ -27,8 +28,8 @@ __global__ void k_gabsmax(const float* __restrict__ g, long long ld, int H, int 
     const long long y = i / W, x = i - y * W;
     m = fmaxf(m, fabsf(g[y * ld + x]));  // NaN is ignored here; the weights check it
   }
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) bsf_atomic_max_pos_float(&st->max_absg_bits, m);
+  m = bsf_block_reduce(m, [](float a, float b) { return fmaxf(a, b); });
+  if (threadIdx.x == 0) bsf_atomic_max_pos_float(&st->max_absg_bits, m);
 }
 
 // qg from the float32 bits of max|gout|: 54 - ceil(log2 m), clamped to [0, 100]

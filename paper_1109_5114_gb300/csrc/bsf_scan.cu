@@ -209,11 +209,24 @@ __device__ __forceinline__ void scan_rows_body(const In* __restrict__ img, long 
         return q_;
       },
       [&](int xp, T val) { row[xp] = val; });
+  // one atomic per block on the status word (per-warp atomics on one word
+  // serialise)
+  __shared__ float s_amax[kRowThreads / 32];
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
   for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   const bool bad = __any_sync(0xffffffffu, !all_ok);
+  __syncthreads();
   if (lane == 0) {
-    bsf_atomic_max_pos_float(&st->max_absq_bits, amax);
-    if (bad) bsf_set_error(st, BSF_EOVERFLOW);
+    s_amax[threadIdx.x >> 5] = amax;
+    if (bad) s_bad = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = s_amax[0];
+    for (int w = 1; w < kRowThreads / 32; ++w) m = fmaxf(m, s_amax[w]);
+    if (m > 0.f) bsf_atomic_max_pos_float(&st->max_absq_bits, m);
+    if (s_bad) bsf_set_error(st, BSF_EOVERFLOW);
   }
 }
 
@@ -869,28 +882,45 @@ cudaError_t bsf_launch_batch_vscan(int n, int skew, const BatchImage* imgs, cons
 // ---------------------------------------------------------------------------
 namespace {
 
+// One block per padded row; the block's maximum |Q| goes to the status word
+// with one atomic (a per-warp atomic on that one word serialises).
 template <typename T, typename In>
 __global__ void __launch_bounds__(256)
 k_extend(const In* __restrict__ img, long long ld, int H, int W, int R, int row0, int boundary,
          float scale_f, int q, T* __restrict__ S, long long pitch, int Wp, DevStatus* st) {
-  const int yp = blockIdx.x;  // padded row (grid x: up to 2^31 - 1 rows)
-  const int xp = blockIdx.y * 256 + threadIdx.x;
+  const int yp = blockIdx.x;
   bool yvalid;
   const int ys = bsf_map_index(row0 + yp - R, H, boundary, yvalid);
+  const In* src = img + (long long)ys * ld;
+  T* row = S + (long long)yp * pitch;
   float amax = 0.f;
   bool ok = true;
-  if (xp < Wp) {
+  for (int xp = threadIdx.x; xp < Wp; xp += 256) {
     T v = (T)0;
     bool xvalid;
     const int xs = bsf_map_index(xp - R, W, boundary, xvalid);
-    if (yvalid && xvalid) v = quantize_one<T, In>(img[(long long)ys * ld + xs], q, scale_f, ok, amax);
-    S[(long long)yp * pitch + xp] = v;
+    if (yvalid && xvalid) {
+      bool ok1;
+      float ax;
+      v = quantize_one<T, In>(src[xs], q, scale_f, ok1, ax);
+      ok &= ok1;
+      amax = fmaxf(amax, ax);
+    }
+    row[xp] = v;
   }
+  __shared__ float s_max[8];
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
   for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-  const bool bad = __any_sync(0xffffffffu, !ok);
-  if ((threadIdx.x & 31) == 0) {
-    bsf_atomic_max_pos_float(&st->max_absq_bits, amax);
-    if (bad) bsf_set_error(st, BSF_EOVERFLOW);
+  __syncthreads();
+  if (!ok) s_bad = 1;
+  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = amax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = s_max[0];
+    for (int w = 1; w < 8; ++w) m = fmaxf(m, s_max[w]);
+    if (m > 0.f) bsf_atomic_max_pos_float(&st->max_absq_bits, m);
+    if (s_bad) bsf_set_error(st, BSF_EOVERFLOW);
   }
 }
 
@@ -899,7 +929,7 @@ cudaError_t launch_extend_t(const void* img, int dtype, long long ld, int H, int
                             int boundary, int q, T* S, long long pitch, int Hp, int Wp, DevStatus* st,
                             cudaStream_t s) {
   const float scale = ldexpf(1.f, q);
-  const dim3 grid(Hp, (Wp + 255) / 256);
+  const int grid = Hp;
   switch (dtype) {
     case BSF_U8:
       k_extend<T, uint8_t><<<grid, 256, 0, s>>>((const uint8_t*)img, ld, H, W, R, row0, boundary, scale, q,

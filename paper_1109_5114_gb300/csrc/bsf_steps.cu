@@ -1,5 +1,6 @@
 // Step-field kernel (plan and diagnostics) and the value reduction used by
 // automatic q.  The per-pixel solve itself is in bsf_solve.cuh.
+#include "bsf_reduce.cuh"
 #include "bsf_solve.cuh"
 
 namespace {
@@ -88,8 +89,9 @@ __global__ void k_absmax(const In* __restrict__ img, long long ld, int H, int W,
     const double v = fabs((double)img[y * ld + x]);
     m = (v > m || v != v) ? v : m;  // NaN propagates (fails the later bound)
   }
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) bsf_atomic_max_pos_double(&st->max_absf_bits, m);
+  // NaN propagates through the block (fmax would drop it)
+  m = bsf_block_reduce(m, [](double a, double b) { return (a != a || b != b) ? a + b : fmax(a, b); });
+  if (threadIdx.x == 0) bsf_atomic_max_pos_double(&st->max_absf_bits, m);
 }
 
 int grid_for(long long work, int threads) {

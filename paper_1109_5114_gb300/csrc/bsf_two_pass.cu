@@ -11,6 +11,7 @@
 //   t = |tan(phi) - 1/tan(phi)| / 2,
 //   (e + 1)/(e - 1) = (1 + t)/sqrt(1 + t^2) = (1 + 1/t)/sqrt(1 + 1/t^2),
 //   bound = (C11 + C22 - (e + 1)/(e - 1) root) / 2   (factor 1 when C12 = 0).
+#include "bsf_reduce.cuh"
 #include "bsf_solve.cuh"
 
 namespace {
@@ -70,8 +71,8 @@ __global__ void k_cond2_upper(const float* __restrict__ cov, int kind, long long
     cond2_interval(C11, C12, C22, lo, hi);
     m = fminf(m, hi == hi ? fmaxf(hi, 0.f) : __int_as_float(0x7f800000));
   }
-  for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) atomicMin(upper_bits, __float_as_uint(m));
+  m = bsf_block_reduce(m, [](float a, float b) { return fminf(a, b); });
+  if (threadIdx.x == 0) atomicMin(upper_bits, __float_as_uint(m));
 }
 
 // Pass 2: the float64 bound of the pixels whose interval reaches below that
@@ -89,8 +90,8 @@ __global__ void k_cond2_min(const float* __restrict__ cov, int kind, long long H
     cond2_interval(C11, C12, C22, lo, hi);
     if (!(fmaxf(lo, 0.f) > U)) m = fmin(m, fmax(cond2_bound(C11, C12, C22), 0.0));
   }
-  for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) atomicMin(min_bits, (unsigned long long)__double_as_longlong(m));
+  m = bsf_block_reduce(m, [](double a, double b) { return fmin(a, b); });
+  if (threadIdx.x == 0) atomicMin(min_bits, (unsigned long long)__double_as_longlong(m));
 }
 
 // iso = (s2, 0, s2), res = (C11 - s2, C12, C22 - s2) in float32,
