@@ -316,7 +316,11 @@ def _scan_k128(S: U128, ex: int, ey: int) -> None:
 
 def preintegrate_k(fq_ext: np.ndarray, n: int, bits: int = 64):
     """n-fold running sums along e_1..e_4 (Algorithm 3, step 2, without the
-    factor sqrt(5), which the normalisation absorbs), mod 2^bits."""
+    factor sqrt(5), which the normalisation absorbs), mod 2^bits (bits=32:
+    the mod-2^64 sums reduced, as in modular.preintegrate)."""
+    if bits == 32:
+        with np.errstate(over="ignore"):
+            return (preintegrate_k(fq_ext, n, 64) & U64(0xFFFFFFFF)).astype(np.uint32)
     if bits == 64:
         if fq_ext.dtype == object:
             S = np.vectorize(lambda v: int(v) & MASK64, otypes=[object])(fq_ext).astype(U64)
@@ -337,7 +341,12 @@ def preintegrate_k(fq_ext: np.ndarray, n: int, bits: int = 64):
 
 
 def taps_k(S, Lfield: np.ndarray, n: int, R: int, H: int, W: int, bits: int = 64):
-    """acc(p) = sum_t prod_k (-1)^t_k C(n, t_k) S(p + sum_k (c_k - t_k L_k) e_k)."""
+    """acc(p) = sum_t prod_k (-1)^t_k C(n, t_k) S(p + sum_k (c_k - t_k L_k) e_k)
+    (bits=32: mod 2^32, read as a signed 32-bit value)."""
+    if bits == 32:
+        with np.errstate(over="ignore"):
+            acc = taps_k(np.asarray(S).astype(U64), Lfield, n, R, H, W, 64)
+        return (acc.view(U64) & U64(0xFFFFFFFF)).astype(np.uint32).view(np.int32).astype(np.int64)
     yy, xx = np.mgrid[0:H, 0:W]
     L = Lfield.astype(np.int64)
     c = (n * (L - 1)) // 2

@@ -134,8 +134,14 @@ def preintegrate(fq_ext: np.ndarray, n: int, bits: int = 64):
     """n-fold running sums along every direction, mod 2^bits.
 
     fq_ext: integer image on the padded domain (int64 or Python ints).
-    Returns a uint64 array (bits=64) or a U128 (bits=128).
+    Returns a uint64 array (bits=64), a uint32 array (bits=32) or a U128
+    (bits=128).  Mod 2^32 the sums are the mod-2^64 sums reduced (reduction
+    mod 2^32 is a ring homomorphism of Z/2^64), which is how bits=32 is
+    computed.
     """
+    if bits == 32:
+        with np.errstate(over="ignore"):
+            return (preintegrate(fq_ext, n, 64) & U64(0xFFFFFFFF)).astype(np.uint32)
     if bits == 64:
         if fq_ext.dtype == object:
             S = np.vectorize(lambda v: int(v) & MASK64, otypes=[object])(fq_ext).astype(U64)
@@ -171,8 +177,13 @@ def tap_weights(n: int):
 def taps(S, Lfield: np.ndarray, n: int, R: int, H: int, W: int, bits: int = 64):
     """Signed exact accumulators acc[H][W] from the running sums S.
 
-    Returns int64 (bits=64) or object (bits=128) arrays.
+    Returns int64 (bits=64, and bits=32: the accumulator mod 2^32 read as a
+    signed 32-bit value) or object (bits=128) arrays.
     """
+    if bits == 32:   # the same combination mod 2^32
+        with np.errstate(over="ignore"):
+            acc = taps(np.asarray(S).astype(U64), Lfield, n, R, H, W, 64)
+        return (acc.view(U64) & U64(0xFFFFFFFF)).astype(np.uint32).view(np.int32).astype(np.int64)
     yy, xx = np.mgrid[0:H, 0:W]
     L = Lfield.astype(np.int64)
     c = (n * (L - 1)) // 2
