@@ -75,12 +75,19 @@ extern "C" {
 #define BSF_F64  2
 
 /* precision of the running sums */
+#define BSF_FIX     0       /* modular fixed point of the narrowest of 32, 64, 128 bits that
+                               holds the bound, chosen at each pre-integration (see
+                               bsf_set_precision) */
 #define BSF_FIX64   1       /* uint64 modular fixed point (8 B per element) */
 #define BSF_FIX128  2       /* uint128 modular fixed point (16 B per element) */
 #define BSF_F64ACC  3       /* precision study: float64 running sums (8 B) */
 #define BSF_F32KAHAN 4      /* precision study: compensated float32 running sums, each
                                element an unevaluated sum hi + lo of two float32 added
                                with error-free transformations (8 B) */
+#define BSF_FIX32   5       /* uint32 modular fixed point (4 B per element): forward
+                               filtering with integer steps only (no backward, no
+                               BSF_STEP_D2, no batches); the vertical sums always use the
+                               three-phase scan */
 
 /* covariance field encodings */
 #define BSF_COV_C   0       /* (C11, C12, C22) in px^2 */
@@ -192,12 +199,22 @@ int bsf_set_stream(bsf_t h, void* stream);
  * bits of the fixed-point input.  BSF_F64ACC / BSF_F32KAHAN keep the image
  * values as they are (q is ignored) and are not exact: the n-fold sums grow
  * like prod_k (extent^n / n!) and their rounding is not cancelled by the
- * differences (forward only).  frac_bits in [0, 62] (BSF_FIX64) or [0, 100] (BSF_FIX128)
- * fixes q; -1 chooses the largest q (at most b - 28) with
+ * differences (forward only).  frac_bits in [0, 30] (BSF_FIX32), [0, 62]
+ * (BSF_FIX64 and BSF_FIX) or [0, 100] (BSF_FIX128) fixes q; -1 chooses the
+ * largest q (at most 30 for 32 bits, b - 28 otherwise) with
  * (max|f| 2^q) * max prod L^n < 2^(b-2), from the value bound (see
  * bsf_set_value_bound; uint8 images use 255; float images without a declared
  * bound are reduced on the device, which synchronises) and the mass bound of
- * the last plan.  Errors: BSF_EINVAL. */
+ * the last plan.
+ * BSF_FIX chooses b at every pre-integration, from the same bounds: with a
+ * fixed q, the narrowest b in {32, 64, 128} with (max|f| 2^q + 1/2) mass <
+ * 2^(b-2); with automatic q, the narrowest b whose automatic q reaches
+ * q_t = 0 for uint8 images (exact) and q_t = 25 - ceil(log2 max|f|)
+ * otherwise (quantisation below half a float32 ulp of the largest value).
+ * 32 bits only for the forward filter with integer steps; the continuous
+ * steps choose between 64 and 128; the backward needs the pre-integration
+ * to have come out 64-bit (else BSF_EINVAL).  bsf_get_info reports the
+ * element size taken.  Errors: BSF_EINVAL. */
 int bsf_set_precision(bsf_t h, int mode, int frac_bits);
 
 /* Declare max |f| of the images to come (used by automatic q; no sync). */

@@ -13,7 +13,8 @@ struct bsf_ctx {
   int H = 0, W = 0, N = 4, n = 1, boundary = BSF_SYMMETRIC;
   int R = -1;               // padding; -1 until known
   bool R_fixed = false;     // given at create
-  int precision = BSF_FIX64;
+  int precision = BSF_FIX64;       // element type of the running sums in use
+  bool prec_auto = false;          // BSF_FIX: the width is chosen per pre-integration
   int frac_req = -1;        // requested q (-1 = automatic)
   int q = -1;               // q of the current pre-integration
   int step_rule = BSF_STEP_D1;
@@ -72,7 +73,7 @@ struct bsf_ctx {
   // the whole host-buffer call as a CUDA graph, replayed while its key holds
   cudaStream_t s_cap = nullptr;
   cudaGraphExec_t hgraph = nullptr;
-  long long hkey[16] = {};
+  long long hkey[18] = {};
 
   // Algorithm 1 (bsf_filter_two_pass): the two fields, the first pass's
   // output and the minimum of the condition-2 bound
@@ -112,8 +113,13 @@ int cuda_fail(bsf_t h, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
   } while (0)
 
-size_t elem_bytes_of(int precision) { return precision == BSF_FIX128 ? 16 : 8; }
-bool is_fixed(int precision) { return precision == BSF_FIX64 || precision == BSF_FIX128; }
+size_t elem_bytes_of(int precision) {
+  return precision == BSF_FIX128 ? 16 : (precision == BSF_FIX32 ? 4 : 8);
+}
+bool is_fixed(int precision) {
+  return precision == BSF_FIX32 || precision == BSF_FIX64 || precision == BSF_FIX128;
+}
+int elem_bits(int precision) { return precision == BSF_FIX128 ? 128 : (precision == BSF_FIX32 ? 32 : 64); }
 
 void free_workspace(bsf_t h) {
   if (h->S) cudaFree(h->S);
@@ -233,6 +239,11 @@ int d2_min_reach(int n) { return n == 2 ? 9 : 6; }
 int check_d2(bsf_t h) {
   if (h->n > 2) return fail(h, BSF_EINVAL, "continuous steps need n <= 2");
   if (!is_fixed(h->precision)) return fail(h, BSF_EINVAL, "continuous steps need fixed point");
+  if (h->precision == BSF_FIX32) {
+    if (!h->prec_auto) return fail(h, BSF_EINVAL, "continuous steps need 64 or 128 bits");
+    h->precision = BSF_FIX64;  // BSF_FIX: chosen again at the pre-integration, 64 bits at least
+    h->have_S = false;
+  }
   if (h->R >= 0 && h->R < d2_min_reach(h->n))
     return fail(h, BSF_EINVAL, "padding R = %d below %d, the reach of continuous identity steps",
                 h->R, d2_min_reach(h->n));
@@ -279,12 +290,11 @@ int run_steps(bsf_t h, const float* cov, int cov_kind, bool sync_plan) {
 
 // Choose q for this pre-integration.
 int resolve_q(bsf_t h, const void* img, int dtype, long long ld) {
-  const int b = h->precision == BSF_FIX128 ? 128 : 64;
   if (!is_fixed(h->precision)) {  // floating-point sums hold the values themselves
     h->q = 0;
     return BSF_OK;
   }
-  if (h->frac_req >= 0) {
+  if (h->frac_req >= 0 && !h->prec_auto) {
     h->q = h->frac_req;
     return BSF_OK;
   }
@@ -308,9 +318,34 @@ int resolve_q(bsf_t h, const void* img, int dtype, long long ld) {
   const double mass = h->plan_mass > 1.0 ? h->plan_mass : 1.0;
   const double lv = std::log2(vmax > 1e-300 ? vmax : 1e-300);
   const double lm = std::log2(mass);
-  int q = (int)std::floor((b - 2) - lv - lm) - 1;
-  if (h->step_rule == BSF_STEP_D2) q -= 2;  // derivative sums reach 3 max|Q| mass
-  if (q > b - 28) q = b - 28;
+  auto auto_q = [&](int b) {
+    int q = (int)std::floor((b - 2) - lv - lm) - 1;
+    if (h->step_rule == BSF_STEP_D2) q -= 2;  // derivative sums reach 3 max|Q| mass
+    const int qcap = b == 32 ? 30 : b - 28;
+    if (q > qcap) q = qcap;
+    return q;
+  };
+  if (h->prec_auto) {
+    // the narrowest element that holds the bound (BSF_FIX)
+    static const int widths[3] = {BSF_FIX32, BSF_FIX64, BSF_FIX128};
+    const int qt = dtype == BSF_U8 ? 0 : 25 - (int)std::ceil(lv);
+    int pick = BSF_FIX128;
+    for (int w : widths) {
+      if (w == BSF_FIX32 && h->step_rule == BSF_STEP_D2) continue;  // continuous steps: 64 / 128 bits
+      const int b = elem_bits(w);
+      const bool fits = h->frac_req >= 0
+                            ? std::log2((vmax * std::ldexp(1.0, h->frac_req) + 0.5) * mass) < b - 2
+                            : auto_q(b) >= (qt > 0 ? qt : 0);
+      if (fits) { pick = w; break; }
+    }
+    if (pick != h->precision) h->have_S = false;
+    h->precision = pick;
+    if (h->frac_req >= 0) {
+      h->q = h->frac_req;
+      return BSF_OK;
+    }
+  }
+  int q = auto_q(elem_bits(h->precision));
   if (q < 0) q = 0;
   h->q = q;
   return BSF_OK;
@@ -327,8 +362,8 @@ int preintegrate_impl(bsf_t h, const void* img, int dtype, long long ld, int row
   if (h->dirset != BSF_DIRS_CARTESIAN && !is_fixed(h->precision))
     return fail(h, BSF_EINVAL, "the second direction set needs fixed point");
   int rc;
+  if ((rc = resolve_q(h, img, dtype, ld))) return rc;  // may choose the element (BSF_FIX)
   if ((rc = ensure_workspace(h))) return rc;
-  if ((rc = resolve_q(h, img, dtype, ld))) return rc;
   if ((rc = reset_counters(h, false, true))) return rc;
   const int Hb = rows + 2 * h->R;  // padded rows of the band
   cudaError_t e;
@@ -364,7 +399,7 @@ int preintegrate_impl(bsf_t h, const void* img, int dtype, long long ld, int row
   const int phases[3] = {BSF_PHASE_D3, BSF_PHASE_D2, BSF_PHASE_D4};
   for (int i = 0; i < 3; ++i) {
     PhaseTimer t(h, phases[i]);
-    if (h->scan_mode == BSF_SCAN_LOOKBACK && is_fixed(h->precision))
+    if (h->scan_mode == BSF_SCAN_LOOKBACK && is_fixed(h->precision) && h->precision != BSF_FIX32)
       e = bsf_launch_vscan_lb(h->precision, h->n, skews[i], false, h->short_tiles != 0, h->S, h->pitch,
                               Hb, h->Wp, h->agg, h->carry, h->sync_words, h->wait_limit,
                               h->test_unpublished, h->st, h->stream);
@@ -449,13 +484,16 @@ int bsf_set_stream(bsf_t h, void* stream) {
 
 int bsf_set_precision(bsf_t h, int mode, int frac_bits) {
   if (!h) return BSF_EINVAL;
-  if (mode != BSF_FIX64 && mode != BSF_FIX128 && mode != BSF_F64ACC && mode != BSF_F32KAHAN)
+  if (mode != BSF_FIX && mode != BSF_FIX32 && mode != BSF_FIX64 && mode != BSF_FIX128 &&
+      mode != BSF_F64ACC && mode != BSF_F32KAHAN)
     return fail(h, BSF_EINVAL, "bad precision mode %d", mode);
-  const int qmax = mode == BSF_FIX64 ? 62 : 100;
+  const int qmax = mode == BSF_FIX32 ? 30 : (mode == BSF_FIX64 || mode == BSF_FIX ? 62 : 100);
   if (frac_bits < -1 || frac_bits > qmax)
     return fail(h, BSF_EINVAL, "frac_bits %d outside [-1, %d]", frac_bits, qmax);
-  if (mode != h->precision) h->have_S = false;
-  h->precision = mode;
+  const int eff = mode == BSF_FIX ? (is_fixed(h->precision) ? h->precision : BSF_FIX64) : mode;
+  if (eff != h->precision) h->have_S = false;
+  h->precision = eff;
+  h->prec_auto = mode == BSF_FIX;
   h->frac_req = frac_bits;
   return BSF_OK;
 }
@@ -724,11 +762,11 @@ int bsf_filter_host(bsf_t h, const void* img, int dtype, long long ld, const flo
   if (plan || !q_known || h->profiling) {
     if ((rc = enqueue_host_filter(h, img, dtype, ld, cov, cov_kind, out, out_dtype, ldo, plan))) return rc;
   } else {
-    if ((rc = ensure_workspace(h))) return rc;
     if ((rc = resolve_q(h, nullptr, dtype, ld))) return rc;  // host arithmetic only here
-    const long long key[16] = {(long long)img, (long long)cov, (long long)out, dtype, ld, ldo, out_dtype,
+    if ((rc = ensure_workspace(h))) return rc;
+    const long long key[18] = {(long long)img, (long long)cov, (long long)out, dtype, ld, ldo, out_dtype,
                                cov_kind, h->host_bands, h->step_rule, h->precision, h->q, h->R,
-                               (long long)h->S, h->pitch, h->scan_chunk};
+                               (long long)h->S, h->pitch, h->scan_chunk, h->dirset, (long long)h->S2};
     if (!h->hgraph || std::memcmp(key, h->hkey, sizeof key) != 0) {
       if (h->hgraph) {
         cudaGraphExecDestroy(h->hgraph);

@@ -72,10 +72,12 @@ __device__ __forceinline__ f32x2 operator-(f32x2 a, f32x2 b) { return a + (-b); 
 __device__ __forceinline__ f32x2& operator+=(f32x2& a, f32x2 b) { a = a + b; return a; }
 
 template <typename T> struct ElemBits;
+template <> struct ElemBits<uint32_t> { static constexpr int value = 32; };
 template <> struct ElemBits<uint64_t> { static constexpr int value = 64; };
 template <> struct ElemBits<u128> { static constexpr int value = 128; };
 
 template <typename T> struct IsFixed { static constexpr bool value = false; };
+template <> struct IsFixed<uint32_t> { static constexpr bool value = true; };
 template <> struct IsFixed<uint64_t> { static constexpr bool value = true; };
 template <> struct IsFixed<u128> { static constexpr bool value = true; };
 
@@ -94,6 +96,7 @@ template <> __device__ __forceinline__ f32x2 bsf_load<f32x2>(const f32x2* p) {
   const float2 v = __ldg(reinterpret_cast<const float2*>(p));
   return f32x2(v.x, v.y);
 }
+template <> __device__ __forceinline__ uint32_t bsf_load<uint32_t>(const uint32_t* p) { return __ldg(p); }
 template <> __device__ __forceinline__ uint64_t bsf_load<uint64_t>(const uint64_t* p) {
   return __ldg(reinterpret_cast<const unsigned long long*>(p));
 }
@@ -108,6 +111,9 @@ template <> __device__ __forceinline__ double bsf_shfl_up<double>(double v, int 
 }
 template <> __device__ __forceinline__ f32x2 bsf_shfl_up<f32x2>(f32x2 v, int d) {
   return f32x2(__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d));
+}
+template <> __device__ __forceinline__ uint32_t bsf_shfl_up<uint32_t>(uint32_t v, int d) {
+  return __shfl_up_sync(0xffffffffu, v, d);
 }
 template <> __device__ __forceinline__ uint64_t bsf_shfl_up<uint64_t>(uint64_t v, int d) {
   return __shfl_up_sync(0xffffffffu, (unsigned long long)v, d);
@@ -125,6 +131,9 @@ template <> __device__ __forceinline__ double bsf_shfl_idx<double>(double v, int
 template <> __device__ __forceinline__ f32x2 bsf_shfl_idx<f32x2>(f32x2 v, int src) {
   return f32x2(__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src));
 }
+template <> __device__ __forceinline__ uint32_t bsf_shfl_idx<uint32_t>(uint32_t v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
 template <> __device__ __forceinline__ uint64_t bsf_shfl_idx<uint64_t>(uint64_t v, int src) {
   return __shfl_sync(0xffffffffu, (unsigned long long)v, src);
 }
@@ -140,6 +149,12 @@ template <> __device__ __forceinline__ u128 bsf_shfl_idx<u128>(u128 v, int src) 
 // (exact for float inputs).  ok = false when |x| does not fit the element.
 // ----------------------------------------------------------------------------
 template <typename T> __device__ __forceinline__ T bsf_round_to_elem(double x, bool& ok);
+
+template <> __device__ __forceinline__ uint32_t bsf_round_to_elem<uint32_t>(double x, bool& ok) {
+  // |x| < 2^31 - 1 keeps the rounded value inside int32
+  ok = fabs(x) < 2147483647.0;
+  return ok ? (uint32_t)__double2int_rn(x) : 0u;
+}
 
 template <> __device__ __forceinline__ uint64_t bsf_round_to_elem<uint64_t>(double x, bool& ok) {
   // |x| < 2^63 - 1024 keeps the rounded value inside int64

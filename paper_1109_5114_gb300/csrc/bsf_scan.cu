@@ -662,6 +662,9 @@ cudaError_t bsf_launch_scan_rows(int prec, int n, const void* img, int dtype, lo
 #define BSF_ROWS(T, NF) \
   return launch_rows_t<T, NF>(img, dtype, ld, H, W, R, row0, boundary, q, (T*)S, pitch, Hp, Wp, st, s)
   switch (prec * 10 + n) {
+    case 51: BSF_ROWS(uint32_t, 1);
+    case 52: BSF_ROWS(uint32_t, 2);
+    case 53: BSF_ROWS(uint32_t, 3);
     case 11: BSF_ROWS(uint64_t, 1);
     case 12: BSF_ROWS(uint64_t, 2);
     case 13: BSF_ROWS(uint64_t, 3);
@@ -768,6 +771,9 @@ cudaError_t bsf_launch_vscan(int prec, int n, int skew, bool reverse, void* S, l
                  : launch_v_skew<T, NF, false>(skew, (T*)S, pitch, Hp, Wp, chunk, (T*)agg,       \
                                                (T*)carry, s)
   switch (prec * 10 + n) {
+    case 51: BSF_V(uint32_t, 1);
+    case 52: BSF_V(uint32_t, 2);
+    case 53: BSF_V(uint32_t, 3);
     case 11: BSF_V(uint64_t, 1);
     case 12: BSF_V(uint64_t, 2);
     case 13: BSF_V(uint64_t, 3);
@@ -1010,6 +1016,9 @@ cudaError_t launch_second_t(T* S, long long pitch, int Hp, int Wp, int ch, T* ag
 cudaError_t bsf_launch_extend(int prec, const void* img, int dtype, long long ld, int H, int W, int R,
                               int row0, int boundary, int q, void* S, long long pitch, int Hp, int Wp,
                               DevStatus* st, cudaStream_t s) {
+  if (prec == BSF_FIX32)
+    return launch_extend_t<uint32_t>(img, dtype, ld, H, W, R, row0, boundary, q, (uint32_t*)S, pitch, Hp,
+                                     Wp, st, s);
   if (prec == BSF_FIX64)
     return launch_extend_t<uint64_t>(img, dtype, ld, H, W, R, row0, boundary, q, (uint64_t*)S, pitch, Hp,
                                      Wp, st, s);
@@ -1031,6 +1040,9 @@ size_t bsf_second_scan_elems(int n, int Hp, int Wp, int chunk) {
 cudaError_t bsf_launch_scans_second(int prec, int n, void* S, long long pitch, int Hp, int Wp, int chunk,
                                     void* agg, cudaStream_t s) {
   switch (prec * 10 + n) {
+    case 51: return launch_second_t<uint32_t, 1>((uint32_t*)S, pitch, Hp, Wp, chunk, (uint32_t*)agg, s);
+    case 52: return launch_second_t<uint32_t, 2>((uint32_t*)S, pitch, Hp, Wp, chunk, (uint32_t*)agg, s);
+    case 53: return launch_second_t<uint32_t, 3>((uint32_t*)S, pitch, Hp, Wp, chunk, (uint32_t*)agg, s);
     case 11: return launch_second_t<uint64_t, 1>((uint64_t*)S, pitch, Hp, Wp, chunk, (uint64_t*)agg, s);
     case 12: return launch_second_t<uint64_t, 2>((uint64_t*)S, pitch, Hp, Wp, chunk, (uint64_t*)agg, s);
     case 13: return launch_second_t<uint64_t, 3>((uint64_t*)S, pitch, Hp, Wp, chunk, (uint64_t*)agg, s);

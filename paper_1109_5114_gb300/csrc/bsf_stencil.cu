@@ -43,6 +43,9 @@ cudaError_t bsf_launch_stencil_d1(int prec, int n, const void* S, long long pitc
   return launch_t<T, NF>((const T*)S, pitch, R, cov, cov_kind, rule, H, W, row0, rows, q, out, out_dtype, \
                          ldo, st, s)
   switch (prec * 10 + n) {
+    case 51: BSF_ST(uint32_t, 1);
+    case 52: BSF_ST(uint32_t, 2);
+    case 53: BSF_ST(uint32_t, 3);
     case 11: BSF_ST(uint64_t, 1);
     case 12: BSF_ST(uint64_t, 2);
     case 13: BSF_ST(uint64_t, 3);

@@ -52,6 +52,10 @@ __device__ __forceinline__ T comb(const T* __restrict__ S, int idx, const int* s
 }
 
 template <typename T> __device__ __forceinline__ float to_f32(T acc, T D);
+template <> __device__ __forceinline__ float to_f32<uint32_t>(uint32_t acc, uint32_t D) {
+  (void)D;
+  return __int2float_rn((int)acc);
+}
 template <> __device__ __forceinline__ float to_f32<uint64_t>(uint64_t acc, uint64_t D) {
   (void)D;
   return bsf_rn32_i64((long long)acc);
@@ -61,22 +65,25 @@ template <> __device__ __forceinline__ float to_f32<u128>(u128 acc, u128 D) {
   return bsf_rn32((i128)acc);
 }
 template <typename T> __device__ __forceinline__ double to_f64(T acc);
+template <> __device__ __forceinline__ double to_f64<uint32_t>(uint32_t acc) { return (double)(int)acc; }
 template <> __device__ __forceinline__ double to_f64<uint64_t>(uint64_t acc) {
   return __ll2double_rn((long long)acc);
 }
 template <> __device__ __forceinline__ double to_f64<u128>(u128 acc) { return bsf_rn64((i128)acc); }
 
 template <typename T> __device__ __forceinline__ float mass_f32(T D);
+template <> __device__ __forceinline__ float mass_f32<uint32_t>(uint32_t D) { return __uint2float_rn(D); }
 template <> __device__ __forceinline__ float mass_f32<uint64_t>(uint64_t D) { return bsf_rn32_u64(D); }
 template <> __device__ __forceinline__ float mass_f32<u128>(u128 D) { return bsf_rn32_u(D); }
 template <typename T> __device__ __forceinline__ double mass_f64(T D);
+template <> __device__ __forceinline__ double mass_f64<uint32_t>(uint32_t D) { return (double)D; }
 template <> __device__ __forceinline__ double mass_f64<uint64_t>(uint64_t D) { return __ull2double_rn(D); }
 template <> __device__ __forceinline__ double mass_f64<u128>(u128 D) { return bsf_rn64_u(D); }
 
 // Resident blocks per SM requested from the register allocator: enough warps
 // to cover the latency of the (n+1)^4 gathers.
 template <typename T, int NF> struct StencilOcc {
-  static constexpr int value = sizeof(T) == 8 ? (NF == 1 ? 6 : NF == 2 ? 4 : 1) : (NF == 1 ? 4 : NF == 2 ? 2 : 1);
+  static constexpr int value = sizeof(T) <= 8 ? (NF == 1 ? 6 : NF == 2 ? 4 : 1) : (NF == 1 ? 4 : NF == 2 ? 2 : 1);
 };
 
 // The step solve of bsf_solve.cuh runs here, per pixel, so its arithmetic

@@ -1,6 +1,6 @@
 // Stencil kernels of the second direction set (BSF_DIRS_SECOND: Algorithm 3's
 // beta'_a with integer steps) and of the pair switched per pixel by sector
-// (BSF_DIRS_PAIR: Algorithm 2).  Fixed point only.
+// (BSF_DIRS_PAIR: Algorithm 2).  Fixed point only (32, 64 and 128 bits).
 #include "bsf_stencil.cuh"
 
 namespace {
@@ -54,7 +54,12 @@ cudaError_t bsf_launch_stencil_sets(int prec, int n, int dirset, const void* S, 
                                     int H, int W, int row0, int rows, int q, void* out, int out_dtype,
                                     long long ldo, DevStatus* st, cudaStream_t s) {
   if (dirset == BSF_DIRS_PAIR && !S2) return cudaErrorInvalidValue;
-  if (prec == BSF_FIX64) {
+  if (prec == BSF_FIX32) {
+    if (dirset == BSF_DIRS_SECOND)
+      return launch_sets_n<uint32_t, BSF_DIRS_SECOND>(n, S, S2, pitch, R, cov, cov_kind, rule, H, W, row0, rows, q, out, out_dtype, ldo, st, s);
+    if (dirset == BSF_DIRS_PAIR)
+      return launch_sets_n<uint32_t, BSF_DIRS_PAIR>(n, S, S2, pitch, R, cov, cov_kind, rule, H, W, row0, rows, q, out, out_dtype, ldo, st, s);
+  } else if (prec == BSF_FIX64) {
     if (dirset == BSF_DIRS_SECOND)
       return launch_sets_n<uint64_t, BSF_DIRS_SECOND>(n, S, S2, pitch, R, cov, cov_kind, rule, H, W, row0, rows, q, out, out_dtype, ldo, st, s);
     if (dirset == BSF_DIRS_PAIR)

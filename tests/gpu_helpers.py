@@ -37,7 +37,10 @@ def run_gpu(img, cov, n, boundary, q, precision=1, out_dtype=np.float32, max_rea
         raw, inf = f.preintegrated()
         raw = raw.cpu().numpy()
         sets = 2 if directions == 2 else 1
-        if inf.elem_bytes == 8:
+        if inf.elem_bytes == 4:
+            S = raw.view(np.uint32).reshape(sets, inf.Hp, inf.Wp)
+            S = [S[i] for i in range(sets)]
+        elif inf.elem_bytes == 8:
             S = raw.view(np.uint64).reshape(sets, inf.Hp, inf.Wp)
             S = [S[i] for i in range(sets)]
         else:
