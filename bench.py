@@ -325,6 +325,47 @@ def run_gpu(args):
     second, second_ms = time_dirs(bsf.BSF_DIRS_SECOND)
     pair, pair_ms = time_dirs(bsf.BSF_DIRS_PAIR)
 
+    # ---- 8-bit image, small kernels: what 32-bit running sums buy ---------
+    # (the blob image as uint8, sigma 1..3 px, rho 1..3, n = 2: the bound
+    # 255 x max prod L^n stays below 2^31, so BSF_FIX takes 32 bits)
+    import workloads as wl
+    u8 = torch.from_numpy(wl.blob_image_u8(H, W, seed=0)).cuda()
+    cov_s = torch.from_numpy(wl.diagonal_ramp_cov_field(H, W, sigma_hi=3.0, rho_hi=3.0)).cuda()
+    small = {"workload": f"{H}x{W} uint8 blob image, sigma 1-3 px, rho 1-3, n={ORDER}"}
+    outs = {}
+    for name, prec in (("fix_auto", bsf.BSF_FIX), ("fix64", bsf.BSF_FIX64)):
+        g = bsf.BoxSplineFilter(H, W, ORDER, "symmetric", precision=prec, frac_bits=-1)
+        g.set_option(bsf.BSF_OPT_SCAN_MODE, bsf.BSF_SCAN_THREE_PHASE)
+        o = torch.empty((H, W), dtype=torch.float32, device="cuda")
+        g.plan(cov_s)
+        for _ in range(args.warmup):
+            flush.zero_()
+            g.filter(u8, cov_s, out=o)
+        torch.cuda.synchronize()
+        es = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ee = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        barrier(world)
+        t0 = time.time()
+        for i in range(args.steps):
+            flush.zero_()
+            es[i].record(stream)
+            g.filter(u8, cov_s, out=o)
+            ee[i].record(stream)
+        torch.cuda.synchronize()
+        clk.mark(t0, time.time())
+        barrier(world)
+        ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(es, ee)), world)
+        if g.status() != 0:
+            raise RuntimeError(f"device status ({name})")
+        gi = g.info()
+        small[name] = {"ms_per_step": round(ms / args.steps, 5), "elem_bytes": gi.elem_bytes,
+                       "frac_bits": gi.frac_bits,
+                       "value": round(world * H * W * args.steps / (ms * 1e-3) / 1e6, 2), "unit": UNIT}
+        outs[name] = o
+        g.close()
+    # both are exact integer pipelines; they differ only where q differs
+    small["max_abs_diff"] = float((outs["fix_auto"] - outs["fix64"]).abs().max())
+
     # ---- forward + backward (image gradient of <out, gout>) ---------------
     gen = torch.Generator(device="cuda").manual_seed(0)
     d_gout = torch.randn((H, W), generator=gen, device="cuda", dtype=torch.float32)
@@ -461,6 +502,7 @@ def run_gpu(args):
         "algorithm1": algorithm1,
         "algorithm3_second_set": second,
         "algorithm2_pair": pair,
+        "u8_small_kernels": small,
         "fwd_bwd": {"value": round(fb_value, 2), "unit": UNIT,
                     "ms_per_step": round(fb_ms / args.steps, 5),
                     "phases_ms": {k: round(ms / max(c, 1), 5) for k, (ms, c) in prof_fb.items() if c}},
