@@ -327,15 +327,18 @@ def run_gpu(args):
 
     # ---- 8-bit image, small kernels: what 32-bit running sums buy ---------
     # (the blob image as uint8, sigma 1..3 px, rho 1..3, n = 2: the bound
-    # 255 x max prod L^n stays below 2^31, so BSF_FIX takes 32 bits)
+    # 255 x max prod L^n stays below 2^31, so BSF_FIX takes 32 bits), and
+    # what the fused tiles buy against the global passes
     import workloads as wl
     u8 = torch.from_numpy(wl.blob_image_u8(H, W, seed=0)).cuda()
     cov_s = torch.from_numpy(wl.diagonal_ramp_cov_field(H, W, sigma_hi=3.0, rho_hi=3.0)).cuda()
     small = {"workload": f"{H}x{W} uint8 blob image, sigma 1-3 px, rho 1-3, n={ORDER}"}
     outs = {}
-    for name, prec in (("fix_auto", bsf.BSF_FIX), ("fix64", bsf.BSF_FIX64)):
+    for name, prec, tiles in (("fix_auto", bsf.BSF_FIX, 1), ("fix_auto_global_passes", bsf.BSF_FIX, 0),
+                              ("fix64", bsf.BSF_FIX64, 1), ("fix64_global_passes", bsf.BSF_FIX64, 0)):
         g = bsf.BoxSplineFilter(H, W, ORDER, "symmetric", precision=prec, frac_bits=-1)
         g.set_option(bsf.BSF_OPT_SCAN_MODE, bsf.BSF_SCAN_THREE_PHASE)
+        g.set_option(bsf.BSF_OPT_TILES, tiles)
         o = torch.empty((H, W), dtype=torch.float32, device="cuda")
         g.plan(cov_s)
         for _ in range(args.warmup):

@@ -135,7 +135,8 @@ extern "C" {
 #define BSF_PHASE_BWD_FOLD    8  /* backward: extension adjoint + output */
 #define BSF_PHASE_SECOND      9  /* BSF_DIRS_SECOND / _PAIR: extension + quantisation, then the
                                     running sums along e1..e4 (nine kernels) */
-#define BSF_NUM_PHASES        10
+#define BSF_PHASE_TILES      10  /* the fused tile filter (BSF_OPT_TILES): one kernel */
+#define BSF_NUM_PHASES        11
 
 /* options of bsf_set_option */
 #define BSF_OPT_SCAN_MODE    1  /* value BSF_SCAN_THREE_PHASE (default) or BSF_SCAN_LOOKBACK */
@@ -152,6 +153,15 @@ extern "C" {
 #define BSF_OPT_HOST_BANDS   7  /* row bands of bsf_filter_host's overlapped transfers, 1..32 (default 4) */
 #define BSF_OPT_DIRECTIONS   8  /* direction set of the integer-step filter (BSF_DIRS_*); changing
                                    it drops the plan (the next call plans again) */
+#define BSF_OPT_TILES        9  /* 1 (default): bsf_filter / bsf_filter_rows with an image run as one
+                                   fused kernel of restarted tiles whenever a tile of at least
+                                   64 x 64 outputs plus the padding R on each side fits in shared
+                                   memory (Cartesian set, BSF_STEP_D1 / _PAPER, BSF_FIX32/64/128,
+                                   BSF_F64ACC): each block pre-integrates its own window in
+                                   shared memory, and no running sums are kept (a later
+                                   bsf_filter with img NULL, or bsf_copy_preintegrated, needs
+                                   bsf_preintegrate); same results as the global passes in fixed
+                                   point.  0: always the global passes */
 #define BSF_SCAN_LOOKBACK     0 /* single pass, decoupled look-back between blocks */
 #define BSF_SCAN_THREE_PHASE  1 /* reduce / carry / rescan; no block waits on another
                                    (measured faster on GB300 for 2048^2, n = 2) */

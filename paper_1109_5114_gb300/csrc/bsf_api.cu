@@ -19,6 +19,8 @@ struct bsf_ctx {
   int q = -1;               // q of the current pre-integration
   int step_rule = BSF_STEP_D1;
   int dirset = BSF_DIRS_CARTESIAN;  // direction set (BSF_OPT_DIRECTIONS)
+  int tiles = 1;                    // BSF_OPT_TILES
+  int max_smem = 0;                 // opt-in shared memory per block (bytes)
   bool has_bound = false;
   double value_bound = 0.0;
   cudaStream_t stream = nullptr;
@@ -551,6 +553,10 @@ int bsf_set_option(bsf_t h, int option, long long value) {
         h->steps_current = false;
       }
       return BSF_OK;
+    case BSF_OPT_TILES:
+      if (value != 0 && value != 1) return fail(h, BSF_EINVAL, "bad tiles option %lld", value);
+      h->tiles = (int)value;
+      return BSF_OK;
     case BSF_OPT_HOST_BANDS:
       if (value < 1 || value > bsf_ctx::kHostBands) return fail(h, BSF_EINVAL, "bad band count %lld", value);
       h->host_bands = (int)value;
@@ -596,6 +602,35 @@ static int filter_impl(bsf_t h, const void* img, int dtype, long long ld, const 
     if ((rc = run_steps(h, cov, cov_kind, true))) return rc;
   }
   if ((rc = reset_counters(h, true, false))) return rc;
+  // one fused kernel of restarted tiles, when a tile fits in shared memory
+  if (img && h->tiles && !jac && h->dirset == BSF_DIRS_CARTESIAN && h->step_rule != BSF_STEP_D2 &&
+      h->precision != BSF_F32KAHAN && h->R >= 0) {
+    if (dtype != BSF_U8 && dtype != BSF_F32 && dtype != BSF_F64)
+      return fail(h, BSF_EINVAL, "bad image dtype %d", dtype);
+    if (ld < h->W) return fail(h, BSF_EINVAL, "ld %lld < W %d", ld, h->W);
+    if ((rc = resolve_q(h, img, dtype, ld))) return rc;  // may choose the element (BSF_FIX)
+    if (!h->max_smem) {
+      int v = 0;
+      BSF_CUDA(h, cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+      h->max_smem = v;
+    }
+    const int TT = h->precision == BSF_F32KAHAN ? 0 : bsf_tile_size(h->precision, h->R, h->max_smem);
+    if (TT > 0) {
+      if ((rc = reset_counters(h, false, true))) return rc;
+      cudaError_t e;
+      {
+        PhaseTimer t(h, BSF_PHASE_TILES);
+        e = bsf_launch_tiles(h->precision, h->n, img, dtype, ld, h->H, h->W, h->R, h->boundary, row0, rows, TT,
+                             h->q, cov, cov_kind, h->step_rule, out, out_dtype, ldo, h->st, h->stream);
+      }
+      if (e != cudaSuccess) return cuda_fail(h, e, "tile filter");
+      h->have_S = false;  // no running sums are kept
+      h->last_cov = cov;
+      h->last_kind = cov_kind;
+      h->steps_current = false;
+      return BSF_OK;
+    }
+  }
   if (img) {
     if ((rc = preintegrate_impl(h, img, dtype, ld, row0, rows))) return rc;
   } else if (!h->have_S || h->S_R != h->R || h->S_elem != h->elem || h->S_row0 != row0 ||

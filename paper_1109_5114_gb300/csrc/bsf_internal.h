@@ -162,6 +162,16 @@ size_t bsf_second_scan_elems(int n, int Hp, int Wp, int chunk);
 cudaError_t bsf_launch_scans_second(int prec, int n, void* S, long long pitch, int Hp, int Wp, int chunk,
                                     void* agg, cudaStream_t s);
 
+// Tile-restarted pre-integration fused with the stencil (one launch,
+// Cartesian set, integer steps): bsf_tile_size gives the tile side T (a
+// multiple of 32) for this element precision and padding within max_smem
+// bytes of shared memory per block, or 0 when no tile of at least 64 fits.
+// prec BSF_FIX32/64/128 or BSF_F64ACC.  Outputs rows [row0, row0 + rows).
+int bsf_tile_size(int prec, int R, int max_smem);
+cudaError_t bsf_launch_tiles(int prec, int n, const void* img, int dtype, long long ld, int H, int W, int R,
+                             int boundary, int row0, int rows, int TT, int q, const float* cov, int cov_kind,
+                             int rule, void* out, int out_dtype, long long ldo, DevStatus* st, cudaStream_t s);
+
 // Algorithm 1's split of a field: min over pixels of the condition-2 bound
 // (floored at zero) into *min_bits (device, double bits), then the isotropic
 // field s2 I and the residual C - s2 I (float32 [3][H][W], BSF_COV_C),

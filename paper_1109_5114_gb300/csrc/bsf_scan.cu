@@ -26,6 +26,7 @@
 #include <type_traits>
 
 #include "bsf_device.cuh"
+#include "bsf_quantize.cuh"
 
 namespace {
 
@@ -43,39 +44,6 @@ namespace {
 // states.
 // ---------------------------------------------------------------------------
 constexpr int kRowThreads = 256;
-
-template <typename T, typename In>
-__device__ __forceinline__ T quantize_one(In fv, int q, float scale_f, bool& ok, float& ax) {
-  if constexpr (!IsFixed<T>::value) {  // floating-point variants: the values themselves
-    ok = true;
-    ax = 0.f;
-    if constexpr (std::is_same<T, double>::value) {
-      return (double)fv;
-    } else if constexpr (sizeof(In) <= 4) {
-      return f32x2((float)fv, 0.f);
-    } else {  // float64 input: hi + lo carries its 48 leading bits
-      const float h = __double2float_rn(fv);
-      return f32x2(h, __double2float_rn(fv - (double)h));
-    }
-  } else if constexpr (sizeof(In) == 1) {
-    ok = true;
-    ax = (float)fv * scale_f;
-    return (T)fv << q;
-  } else if constexpr (sizeof(In) == 4) {
-    // f 2^q is exact in float32 (a power-of-two scaling of a finite value
-    // that stays finite); below 2^63 the conversion rounds it half to even
-    const float x = __fmul_rn(fv, scale_f);
-    ax = fabsf(x);
-    ok = true;
-    if (ax < 2147483648.f) return (T)(long long)__float2int_rn(x);  // 32-bit conversion suffices
-    if (ax < 9223372036854775808.f) return (T)(long long)__float2ll_rn(x);
-    return bsf_quantize_f32<T>(fv, q, ok);  // large or non-finite: integer path
-  } else {
-    const double xq = (double)fv * (double)scale_f;
-    ax = __double2float_ru(fabs(xq));
-    return bsf_round_to_elem<T>(xq, ok);
-  }
-}
 
 // C(a, j) for j = 0, 1, 2 (the folds n <= 3 need no more)
 __device__ __forceinline__ long long binom_small(long long a, int j) {

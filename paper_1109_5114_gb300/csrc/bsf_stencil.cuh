@@ -29,22 +29,24 @@ namespace {
 // into S (the padded domain holds fewer than 2^31 elements); level LVL applies
 // the difference along direction LVL-1 (stride s[LVL-1] elements) to level
 // LVL-1, and level 0 loads one element.
-template <typename T, int NF, int LVL>
+// SH: S lies in shared memory (plain loads) instead of global memory.
+template <typename T, int NF, int LVL, bool SH = false>
 __device__ __forceinline__ T comb(const T* __restrict__ S, int idx, const int* s) {
   if constexpr (LVL == 0) {
-    return bsf_load(S + idx);
+    if constexpr (SH) return S[idx];
+    else return bsf_load(S + idx);
   } else {
     const int sk = s[LVL - 1];
-    const T v0 = comb<T, NF, LVL - 1>(S, idx, s);
-    const T v1 = comb<T, NF, LVL - 1>(S, idx - sk, s);
+    const T v0 = comb<T, NF, LVL - 1, SH>(S, idx, s);
+    const T v1 = comb<T, NF, LVL - 1, SH>(S, idx - sk, s);
     if constexpr (NF == 1) {
       return v0 - v1;
     } else if constexpr (NF == 2) {
-      const T v2 = comb<T, NF, LVL - 1>(S, idx - 2 * sk, s);
+      const T v2 = comb<T, NF, LVL - 1, SH>(S, idx - 2 * sk, s);
       return (v0 + v2) - (v1 + v1);
     } else {
-      const T v2 = comb<T, NF, LVL - 1>(S, idx - 2 * sk, s);
-      const T v3 = comb<T, NF, LVL - 1>(S, idx - 3 * sk, s);
+      const T v2 = comb<T, NF, LVL - 1, SH>(S, idx - 2 * sk, s);
+      const T v3 = comb<T, NF, LVL - 1, SH>(S, idx - 3 * sk, s);
       const T a = v1 - v2;
       return (v0 - v3) - (a + a + a);
     }
@@ -86,6 +88,65 @@ template <typename T, int NF> struct StencilOcc {
   static constexpr int value = sizeof(T) <= 8 ? (NF == 1 ? 6 : NF == 2 ? 4 : 1) : (NF == 1 ? 4 : NF == 2 ? 2 : 1);
 };
 
+// Rare-event counters of the step solve (clamped, non-finite, out of
+// reach), aggregated over the active lanes of the warp.
+__device__ __forceinline__ void count_pixel_flags(int flags, bool in_reach, DevStatus* st) {
+  const unsigned act = __activemask();
+  const unsigned mc = __ballot_sync(act, flags & 1), mb = __ballot_sync(act, flags & 2),
+                 mr = __ballot_sync(act, !in_reach);
+  if ((mc | mb | mr) && (threadIdx.x & 31) == __ffs(act) - 1) {
+    if (mc) atomicAdd(&st->clamp_count, (unsigned)__popc(mc));
+    if (mb) { atomicAdd(&st->bad_count, (unsigned)__popc(mb)); bsf_set_error(st, BSF_ECOV); }
+    if (mr) { atomicAdd(&st->range_count, (unsigned)__popc(mr)); bsf_set_error(st, BSF_ERANGE); }
+  }
+}
+
+// The output rule of one pixel from its exact accumulator: D = prod_k L_k^n
+// and out = RN(RN(acc) 2^-q) / RN(D) (fixed point), or acc / D (floating-
+// point variants).  maxq bounds max|Q| + 1 over the kernel's support: the
+// bound max|Q| * D < 2^(b-1), which makes the modular accumulator equal the
+// true one, is checked in float32 with a margin far above its rounding
+// (|acc| <= D max|Q|).
+template <typename T, int NF, typename Out>
+__device__ __forceinline__ void finish_pixel(T acc, const int* L, float maxq, float scale_f, double scale_d,
+                                             Out* __restrict__ o, DevStatus* st) {
+  const int L1 = L[0], L2 = L[1], L3 = L[2], L4w = L[3];
+  if constexpr (IsFixed<T>::value) {
+    T D = 1;
+    const T D1 = (T)(unsigned)(L1 * L2) * (T)(unsigned)(L3 * L4w);
+    const float Df1 = (float)(L1 * L2) * (float)(L3 * L4w);
+    float Df = Df1;
+#pragma unroll
+    for (int j = 0; j < NF; ++j) D *= D1;
+#pragma unroll
+    for (int j = 1; j < NF; ++j) Df *= Df1;
+    const float lim = bsf_pow2_f32(ElemBits<T>::value - 1);
+    if (maxq * Df * 1.0001f >= lim) {
+      atomicAdd(&st->overflow_count, 1u);
+      bsf_set_error(st, BSF_EOVERFLOW);
+    }
+    if constexpr (sizeof(Out) == 4) {
+      const float xa = __fmul_rn(to_f32<T>(acc, D), scale_f);
+      *o = __fdiv_rn(xa, mass_f32<T>(D));
+    } else {
+      const double xa = __dmul_rn(to_f64<T>(acc), scale_d);
+      *o = __ddiv_rn(xa, mass_f64<T>(D));
+    }
+  } else {
+    // floating-point precision variants: acc / prod L^n
+    double Dd = 1.0;
+    const double D1 = (double)(L1 * L2) * (double)(L3 * L4w);
+#pragma unroll
+    for (int j = 0; j < NF; ++j) Dd *= D1;
+    double a;
+    if constexpr (std::is_same<T, double>::value) a = acc;
+    else a = (double)acc.hi + (double)acc.lo;
+    const double v = a / Dd;
+    if constexpr (sizeof(Out) == 4) *o = __double2float_rn(v);
+    else *o = v;
+  }
+}
+
 // The step solve of bsf_solve.cuh runs here, per pixel, so its arithmetic
 // overlaps the gathers of other warps and no step field goes through HBM.
 // DS (BSF_DIRS_*): the direction set.  BSF_DIRS_CARTESIAN takes the taps
@@ -115,16 +176,7 @@ __device__ __forceinline__ void stencil_d1_body(const T* __restrict__ S, const T
     in_reach = bsf_solve::pixel_steps(C11, C12, C22, NF, rule, R, L, flags, reach);
   else
     in_reach = bsf_solve::pixel_steps_set(DS, C11, C12, C22, NF, rule, R, L, flags, reach, second);
-  {  // rare-event counters, aggregated per warp
-    const unsigned act = __activemask();
-    const unsigned mc = __ballot_sync(act, flags & 1), mb = __ballot_sync(act, flags & 2),
-                   mr = __ballot_sync(act, !in_reach);
-    if ((mc | mb | mr) && (threadIdx.x & 31) == __ffs(act) - 1) {
-      if (mc) atomicAdd(&st->clamp_count, (unsigned)__popc(mc));
-      if (mb) { atomicAdd(&st->bad_count, (unsigned)__popc(mb)); bsf_set_error(st, BSF_ECOV); }
-      if (mr) { atomicAdd(&st->range_count, (unsigned)__popc(mr)); bsf_set_error(st, BSF_ERANGE); }
-    }
-  }
+  count_pixel_flags(flags, in_reach, st);
   const int L1 = L[0], L2 = L[1], L3 = L[2], L4w = L[3];
   // element strides of d1 = (1,0), d2 = (1,1), d3 = (0,1), d4 = (-1,1), or
   // of e1 = (2,1), e2 = (1,2), e3 = (-1,2), e4 = (-2,1)
@@ -142,45 +194,8 @@ __device__ __forceinline__ void stencil_d1_body(const T* __restrict__ S, const T
   const int base = (y + R) * p32 + (x + R) + c1 * e1 + c2 * e2 + c3 * e3 + c4 * e4;
   const int s[4] = {L1 * e1, L2 * e2, L3 * e3, L4w * e4};
   const T acc = comb<T, NF, 4>(Sp, base, s);
-
-  if constexpr (IsFixed<T>::value) {
-    // D = prod_k L_k^n (exact) and the bound max|Q| * D < 2^(b-1) that makes
-    // the modular accumulator equal the true one (checked in float32 with a
-    // margin far above its rounding: |acc| <= D max|Q| and max|Q| <= bound + 1/2)
-    T D = 1;
-    const T D1 = (T)(unsigned)(L1 * L2) * (T)(unsigned)(L3 * L4w);
-    const float Df1 = (float)(L1 * L2) * (float)(L3 * L4w);
-    float Df = Df1;
-#pragma unroll
-    for (int j = 0; j < NF; ++j) D *= D1;
-#pragma unroll
-    for (int j = 1; j < NF; ++j) Df *= Df1;
-    const float maxq = __uint_as_float(st->max_absq_bits) + 1.f;
-    const float lim = bsf_pow2_f32(ElemBits<T>::value - 1);
-    if (maxq * Df * 1.0001f >= lim) {
-      atomicAdd(&st->overflow_count, 1u);
-      bsf_set_error(st, BSF_EOVERFLOW);
-    }
-    if constexpr (sizeof(Out) == 4) {
-      const float xa = __fmul_rn(to_f32<T>(acc, D), scale_f);
-      out[(long long)(y) * ldo + x] = __fdiv_rn(xa, mass_f32<T>(D));
-    } else {
-      const double xa = __dmul_rn(to_f64<T>(acc), scale_d);
-      out[(long long)(y) * ldo + x] = __ddiv_rn(xa, mass_f64<T>(D));
-    }
-  } else {
-    // floating-point precision variants: acc / prod L^n
-    double Dd = 1.0;
-    const double D1 = (double)(L1 * L2) * (double)(L3 * L4w);
-#pragma unroll
-    for (int j = 0; j < NF; ++j) Dd *= D1;
-    double a;
-    if constexpr (std::is_same<T, double>::value) a = acc;
-    else a = (double)acc.hi + (double)acc.lo;
-    const double v = a / Dd;
-    if constexpr (sizeof(Out) == 4) out[(long long)(y) * ldo + x] = __double2float_rn(v);
-    else out[(long long)(y) * ldo + x] = v;
-  }
+  finish_pixel<T, NF, Out>(acc, L, __uint_as_float(st->max_absq_bits) + 1.f, scale_f, scale_d,
+                           out + (long long)(y) * ldo + x, st);
 }
 
 }  // namespace

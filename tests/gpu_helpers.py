@@ -20,6 +20,8 @@ def run_gpu(img, cov, n, boundary, q, precision=1, out_dtype=np.float32, max_rea
     H, W = img.shape
     f = bsf.BoxSplineFilter(H, W, n, boundary, max_reach=max_reach, precision=precision,
                             frac_bits=q, step_rule=step_rule, directions=directions)
+    if want_S:  # the fused tiles keep no running sums
+        f.set_option(bsf.BSF_OPT_TILES, 0)
     ti = torch.from_numpy(np.ascontiguousarray(img)).cuda()
     tc = torch.from_numpy(np.ascontiguousarray(cov, dtype=np.float32)).cuda()
     tdt = torch.float32 if np.dtype(out_dtype) == np.float32 else torch.float64

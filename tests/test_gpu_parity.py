@@ -214,6 +214,7 @@ def test_scan_modes_agree_bit_exact(prec):
     outs = []
     for mode in (bsf.BSF_SCAN_LOOKBACK, bsf.BSF_SCAN_THREE_PHASE):
         f = bsf.BoxSplineFilter(H, W, n, "symmetric", precision=prec, frac_bits=4)
+        f.set_option(bsf.BSF_OPT_TILES, 0)  # the global passes keep their running sums
         f.set_option(bsf.BSF_OPT_SCAN_MODE, mode)
         out = f.filter(torch.from_numpy(img).cuda(), torch.from_numpy(cov).cuda())
         raw, _ = f.preintegrated()
@@ -237,6 +238,7 @@ def test_bounded_wait_times_out_and_context_stays_usable():
     cov = _cov(H, W, seed=3)
     f = bsf.BoxSplineFilter(H, W, n, "symmetric", frac_bits=20)
     ti, tc = torch.from_numpy(img).cuda(), torch.from_numpy(cov).cuda()
+    f.set_option(bsf.BSF_OPT_TILES, 0)  # the waits are in the global look-back scans
     f.set_option(bsf.BSF_OPT_SCAN_MODE, bsf.BSF_SCAN_LOOKBACK)
     f.set_option(bsf.BSF_OPT_WAIT_LIMIT, 2000)
     f.set_option(bsf.BSF_OPT_TEST_UNPUBLISHED, 1)
