@@ -20,6 +20,8 @@ backward  the adjoint of the integer-step filter with respect to the image.
 continuous  the continuous-step filter (interpolated taps, Section 2.3) and
           the derivative of its output with respect to the covariance field.
 two_pass  Algorithm 1: an isotropic pass, then the space-variant residual pass.
+sampled   the sampled continuous box spline: the filter of the paper's running
+          sums interpolated by the grid box spline (eq. "interpolation").
 knight    the second box spline beta'_a on the directions (2,1), (1,2), (-1,2),
           (-2,1) (Algorithm 3, Table 1) and the pair switched by sector
           (Algorithm 2).
@@ -27,4 +29,4 @@ knight    the second box spline beta'_a on the directions (2,1), (1,2), (-1,2),
 Parity status of each function is stated in its docstring; "parity unpinned"
 marks a function with no independent pin.
 """
-from . import params, kernels, modular, gaussian, backward, continuous, two_pass, knight  # noqa: F401
+from . import params, kernels, modular, gaussian, backward, continuous, two_pass, knight, sampled  # noqa: F401
