@@ -234,6 +234,10 @@ int check_cov_kind(bsf_t h, int cov_kind) {
   return BSF_OK;
 }
 
+// Smallest padding of the sampled box spline's taps (lambda = 1 on every
+// direction).
+constexpr int kSampledMinPad = 4;
+
 // Smallest padding of the continuous-step taps (identity steps): samples at
 // -3..1 (n = 2) or -2..1 (n = 1) along every direction.
 int d2_min_reach(int n) { return n == 2 ? 9 : 6; }
@@ -282,6 +286,7 @@ int run_steps(bsf_t h, const float* cov, int cov_kind, bool sync_plan) {
       // the solve ran unbounded: every tap of this field fits this R
       int R = reach > 3 * h->n ? reach : 3 * h->n;
       if (h->step_rule == BSF_STEP_D2 && R < d2_min_reach(h->n)) R = d2_min_reach(h->n);
+      if (h->step_rule == BSF_STEP_SAMPLED && R < kSampledMinPad) R = kSampledMinPad;
       h->R = widen && h->R > R ? h->R : R;
     }
     h->planned = true;
@@ -333,7 +338,8 @@ int resolve_q(bsf_t h, const void* img, int dtype, long long ld) {
     const int qt = dtype == BSF_U8 ? 0 : 25 - (int)std::ceil(lv);
     int pick = BSF_FIX128;
     for (int w : widths) {
-      if (w == BSF_FIX32 && h->step_rule == BSF_STEP_D2) continue;  // continuous steps: 64 / 128 bits
+      if (w == BSF_FIX32 && (h->step_rule == BSF_STEP_D2 || h->step_rule == BSF_STEP_SAMPLED))
+        continue;  // continuous steps: 64 / 128 bits
       const int b = elem_bits(w);
       const bool fits = h->frac_req >= 0
                             ? std::log2((vmax * std::ldexp(1.0, h->frac_req) + 0.5) * mass) < b - 2
@@ -510,8 +516,9 @@ int bsf_set_value_bound(bsf_t h, double max_abs) {
 
 int bsf_set_step_rule(bsf_t h, int rule) {
   if (!h) return BSF_EINVAL;
-  if (rule != BSF_STEP_D1 && rule != BSF_STEP_D1_PAPER && rule != BSF_STEP_D2)
+  if (rule != BSF_STEP_D1 && rule != BSF_STEP_D1_PAPER && rule != BSF_STEP_D2 && rule != BSF_STEP_SAMPLED)
     return fail(h, BSF_EINVAL, "bad step rule %d", rule);
+  if (rule == BSF_STEP_SAMPLED && h->n != 1) return fail(h, BSF_EINVAL, "the sampled box spline is of order 1");
   if (rule == BSF_STEP_D2 && h->n > 2) return fail(h, BSF_EINVAL, "continuous steps need n <= 2");
   if (rule != h->step_rule) h->planned = false;  // the mass bound differs between rules
   h->step_rule = rule;
@@ -585,8 +592,20 @@ static int filter_impl(bsf_t h, const void* img, int dtype, long long ld, const 
     const int rc = check_d2(h);
     if (rc) return rc;
   }
+  if (h->step_rule == BSF_STEP_SAMPLED) {
+    if (h->precision != BSF_FIX64 && h->precision != BSF_FIX128) {
+      if (!(h->prec_auto && h->precision == BSF_FIX32))
+        return fail(h, BSF_EINVAL, "the sampled box spline needs BSF_FIX64 or BSF_FIX128");
+      h->precision = BSF_FIX64;  // BSF_FIX: chosen again at the pre-integration, 64 bits at least
+      h->have_S = false;
+    }
+    if (jac) return fail(h, BSF_EINVAL, "the sampled box spline has no Jacobian");
+    if (h->R >= 0 && h->R < kSampledMinPad)
+      return fail(h, BSF_EINVAL, "padding R = %d below %d, the reach of the sampled taps", h->R, kSampledMinPad);
+  }
   if (h->dirset != BSF_DIRS_CARTESIAN) {
-    if (h->step_rule == BSF_STEP_D2) return fail(h, BSF_EINVAL, "the second direction set: integer steps only");
+    if (h->step_rule == BSF_STEP_D2 || h->step_rule == BSF_STEP_SAMPLED)
+      return fail(h, BSF_EINVAL, "the second direction set: integer steps only");
     if (!is_fixed(h->precision)) return fail(h, BSF_EINVAL, "the second direction set needs fixed point");
   }
   if (out_dtype != BSF_F32 && out_dtype != BSF_F64) return fail(h, BSF_EINVAL, "bad out dtype %d", out_dtype);
@@ -603,7 +622,8 @@ static int filter_impl(bsf_t h, const void* img, int dtype, long long ld, const 
   }
   if ((rc = reset_counters(h, true, false))) return rc;
   // one fused kernel of restarted tiles, when a tile fits in shared memory
-  if (img && h->tiles && !jac && h->dirset == BSF_DIRS_CARTESIAN && h->step_rule != BSF_STEP_D2 &&
+  if (img && h->tiles && !jac && h->dirset == BSF_DIRS_CARTESIAN &&
+      (h->step_rule == BSF_STEP_D1 || h->step_rule == BSF_STEP_D1_PAPER) &&
       h->precision != BSF_F32KAHAN && h->R >= 0) {
     if (dtype != BSF_U8 && dtype != BSF_F32 && dtype != BSF_F64)
       return fail(h, BSF_EINVAL, "bad image dtype %d", dtype);
@@ -644,6 +664,9 @@ static int filter_impl(bsf_t h, const void* img, int dtype, long long ld, const 
       e = bsf_launch_stencil_d2(h->precision, h->n, jac ? 1 : 0, h->S, h->pitch, h->R, cov, cov_kind,
                                 h->H, h->W, row0, rows, h->S_q, out, out_dtype, ldo, jac, ldj,
                                 (long long)rows * ldj, nullptr, 0, h->st, h->stream);
+    else if (h->step_rule == BSF_STEP_SAMPLED)
+      e = bsf_launch_stencil_sampled(h->precision, h->S, h->pitch, h->R, cov, cov_kind, h->H, h->W, row0,
+                                     rows, h->S_q, out, out_dtype, ldo, h->st, h->stream);
     else if (h->dirset == BSF_DIRS_CARTESIAN)
       e = bsf_launch_stencil_d1(h->precision, h->n, h->S, h->pitch, h->R, cov, cov_kind,
                                 h->step_rule, h->H, h->W, row0, rows, h->S_q, out, out_dtype, ldo,
@@ -693,6 +716,9 @@ static cudaError_t stencil_band(bsf_t h, const float* cov, int cov_kind, int y0,
     return bsf_launch_stencil_d2(h->precision, h->n, 0, S, h->pitch, h->R, cov, cov_kind, h->H, h->W,
                                  y0, rows, h->S_q, out, out_dtype, ldo, nullptr, 0, 0, nullptr, 0,
                                  h->st, h->stream);
+  if (h->step_rule == BSF_STEP_SAMPLED)
+    return bsf_launch_stencil_sampled(h->precision, S, h->pitch, h->R, cov, cov_kind, h->H, h->W, y0, rows,
+                                      h->S_q, out, out_dtype, ldo, h->st, h->stream);
   return bsf_launch_stencil_d1(h->precision, h->n, S, h->pitch, h->R, cov, cov_kind, h->step_rule,
                                h->H, h->W, y0, rows, h->S_q, out, out_dtype, ldo, h->st, h->stream);
 }
@@ -852,7 +878,8 @@ int bsf_filter_two_pass(bsf_t h, const void* img, int dtype, long long ld, const
   if (!h) return BSF_EINVAL;
   if (!img || !cov || !out) return fail(h, BSF_EINVAL, "NULL img, cov or out");
   if (!(frac > 0.0 && frac < 1.0)) return fail(h, BSF_EINVAL, "frac must lie in (0, 1)");
-  if (h->step_rule == BSF_STEP_D2) return fail(h, BSF_EINVAL, "two passes: integer steps only");
+  if (h->step_rule == BSF_STEP_D2 || h->step_rule == BSF_STEP_SAMPLED)
+    return fail(h, BSF_EINVAL, "two passes: integer steps only");
   int rc = check_cov_kind(h, cov_kind);
   if (rc) return rc;
   const size_t HW = (size_t)h->H * h->W;
@@ -966,7 +993,8 @@ int bsf_filter_backward_rows(bsf_t h, const float* gout, long long ldg, const fl
   if (!h) return BSF_EINVAL;
   int rc = check_cov_kind(h, cov_kind);
   if (rc) return rc;
-  if (h->step_rule == BSF_STEP_D2) return fail(h, BSF_EINVAL, "band backward: integer steps only");
+  if (h->step_rule == BSF_STEP_D2 || h->step_rule == BSF_STEP_SAMPLED)
+    return fail(h, BSF_EINVAL, "band backward: integer steps only");
   if (h->dirset != BSF_DIRS_CARTESIAN) return fail(h, BSF_EINVAL, "backward: Cartesian direction set only");
   if (!gout || !cov || !acc) return fail(h, BSF_EINVAL, "NULL gout, cov or acc");
   if (ldg < h->W || lda < h->W) return fail(h, BSF_EINVAL, "leading dimension < W");
@@ -1084,6 +1112,7 @@ int bsf_filter_backward(bsf_t h, const float* gout, long long ldg, const float* 
   int rc = check_cov_kind(h, cov_kind);
   if (rc) return rc;
   if (h->dirset != BSF_DIRS_CARTESIAN) return fail(h, BSF_EINVAL, "backward: Cartesian direction set only");
+  if (h->step_rule == BSF_STEP_SAMPLED) return fail(h, BSF_EINVAL, "the sampled box spline: forward only");
   if (h->step_rule == BSF_STEP_D2) {
     if (!gout || !cov) return fail(h, BSF_EINVAL, "NULL gout or cov");
     if (ldg < h->W || (gimg && ldgi < h->W)) return fail(h, BSF_EINVAL, "leading dimension < W");

@@ -172,6 +172,12 @@ cudaError_t bsf_launch_tiles(int prec, int n, const void* img, int dtype, long l
                              int boundary, int row0, int rows, int TT, int q, const float* cov, int cov_kind,
                              int rule, void* out, int out_dtype, long long ldo, DevStatus* st, cudaStream_t s);
 
+// The sampled continuous box spline (BSF_STEP_SAMPLED): stencil on the
+// Cartesian order-1 running sums S.  prec BSF_FIX64 or BSF_FIX128.
+cudaError_t bsf_launch_stencil_sampled(int prec, const void* S, long long pitch, int R, const float* cov,
+                                       int cov_kind, int H, int W, int row0, int rows, int q, void* out,
+                                       int out_dtype, long long ldo, DevStatus* st, cudaStream_t s);
+
 // Algorithm 1's split of a field: min over pixels of the condition-2 bound
 // (floored at zero) into *min_bits (device, double bits), then the isotropic
 // field s2 I and the residual C - s2 I (float32 [3][H][W], BSF_COV_C),

@@ -113,6 +113,40 @@ __device__ __forceinline__ bool pixel_steps(float C11, float C12, float C22, int
 }
 
 // ---------------------------------------------------------------------------
+// Sampled continuous box spline (BSF_STEP_SAMPLED, order 1): lambda_k =
+// a_k / |d_k| = sqrt(A_k / |d_k|^2), quantised to Lq_k = max(1, RNE(512
+// lambda_k)).  The taps lie within sum lambda |d|_inf / 2 of the pixel and
+// the interpolation reaches one sample left, right and up, two down:
+// reach = max(ceil(Sx / 512), ceil(Sy / 512)) / 2 + 3, Sx = Lq1 + Lq2 + Lq4,
+// Sy = Lq2 + Lq3 + Lq4.  Out of reach: Lq = 512 (lambda = 1), false.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int sampled_reach(const int Lq[4]) {
+  const long long sx = (long long)Lq[0] + Lq[1] + Lq[3], sy = (long long)Lq[1] + Lq[2] + Lq[3];
+  const long long cx = (sx + 511) >> 9, cy = (sy + 511) >> 9;
+  const long long r = (cx > cy ? cx : cy) / 2 + 3;
+  return r > (1 << 30) ? (1 << 30) : (int)r;
+}
+
+__device__ __forceinline__ bool pixel_steps_sampled(float C11, float C12, float C22, int R, int Lq[4],
+                                                    int& flags, int& reach) {
+  Solved sv = solve_scales(C11, C12, C22, 12.f);
+  flags = sv.flags;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float a = (k & 1) ? __fmul_rn(sv.A[k], 0.5f) : sv.A[k];  // A / |d_k|^2
+    const float lam = fminf(__fsqrt_rn(a), 4194304.f);               // keeps 512 lambda in int range
+    Lq[k] = max(__float2int_rn(__fmul_rn(lam, 512.f)), 1);
+  }
+  reach = sampled_reach(Lq);
+  if (R >= 0 && reach > R) {
+    Lq[0] = Lq[1] = Lq[2] = Lq[3] = 512;
+    reach = sampled_reach(Lq);
+    return false;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
 // The second box spline beta'_a (Section 2.3): boxes along the grid vectors
 // e_1 = (2, 1), e_2 = (1, 2), e_3 = (-1, 2), e_4 = (-2, 1), |e_k|^2 = 5, with
 // covariance (n/12) sum_k A_k e_k e_k^T / 5.  With M = (12/n) C, carried
