@@ -325,6 +325,44 @@ def run_gpu(args):
     second, second_ms = time_dirs(bsf.BSF_DIRS_SECOND)
     pair, pair_ms = time_dirs(bsf.BSF_DIRS_PAIR)
 
+    # ---- the sampled continuous box spline (order 1, the paper's mesh) -----
+    gs = bsf.BoxSplineFilter(H, W, 1, "symmetric", precision=1, frac_bits=-1, value_bound=vmax,
+                             step_rule=bsf.BSF_STEP_SAMPLED)
+    gs.set_option(bsf.BSF_OPT_SCAN_MODE, bsf.BSF_SCAN_THREE_PHASE)
+    o_s = torch.empty_like(d_out)
+    gs.plan(d_cov)
+    for _ in range(args.warmup):
+        flush.zero_()
+        gs.filter(d_img, d_cov, out=o_s)
+    torch.cuda.synchronize()
+    gs.set_profiling(True)
+    gs.read_profile()
+    for _ in range(args.steps):
+        flush.zero_()
+        gs.filter(d_img, d_cov, out=o_s)
+    pr_s = gs.read_profile()
+    gs.set_profiling(False)
+    es = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ee = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(world)
+    t0 = time.time()
+    for i in range(args.steps):
+        flush.zero_()
+        es[i].record(stream)
+        gs.filter(d_img, d_cov, out=o_s)
+        ee[i].record(stream)
+    torch.cuda.synchronize()
+    clk.mark(t0, time.time())
+    barrier(world)
+    ms_s = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(es, ee)), world)
+    if gs.status() != 0:
+        raise RuntimeError("device status (sampled box spline)")
+    sampled = {"ms_per_step": round(ms_s / args.steps, 5), "n": 1, "R": gs.info().R,
+               "frac_bits": gs.info().frac_bits,
+               "value": round(world * H * W * args.steps / (ms_s * 1e-3) / 1e6, 2), "unit": UNIT,
+               "phases_ms": {k: round(v / max(c, 1), 5) for k, (v, c) in pr_s.items() if c}}
+    gs.close()
+
     # ---- 8-bit image, small kernels: what 32-bit running sums buy ---------
     # (the blob image as uint8, sigma 1..3 px, rho 1..3, n = 2: the bound
     # 255 x max prod L^n stays below 2^31, so BSF_FIX takes 32 bits), and
@@ -506,6 +544,7 @@ def run_gpu(args):
         "algorithm3_second_set": second,
         "algorithm2_pair": pair,
         "u8_small_kernels": small,
+        "sampled_box_spline": sampled,
         "fwd_bwd": {"value": round(fb_value, 2), "unit": UNIT,
                     "ms_per_step": round(fb_ms / args.steps, 5),
                     "phases_ms": {k: round(ms / max(c, 1), 5) for k, (ms, c) in prof_fb.items() if c}},
