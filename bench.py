@@ -834,6 +834,81 @@ def run_diff(args):
     }
 
 
+def run_single(args):
+    """One filter configuration on its own (few launches, for profiling and
+    for its own throughput): tiles4096 (8-bit 4096^2 blob image, sigma 1-3 px,
+    rho 1-3, n = 2, automatic width, fused tiles), sampled2048 (the benchmark's
+    image and field, n = 1, the sampled continuous box spline), pair2048 (the
+    benchmark's image and field, n = 2, both direction sets switched by
+    sector)."""
+    import torch
+    import workloads as wl
+    from paper_1109_5114_gb300 import bsf
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if args.workload == "tiles4096":
+        h = w = 4096
+        img = torch.from_numpy(wl.blob_image_u8(h, w, seed=0)).cuda()
+        cov = torch.from_numpy(wl.diagonal_ramp_cov_field(h, w, sigma_hi=3.0, rho_hi=3.0)).cuda()
+        f = bsf.BoxSplineFilter(h, w, 2, "symmetric", precision=bsf.BSF_FIX, frac_bits=-1)
+        desc = "4096x4096 uint8 blob image, sigma 1-3 px, rho 1-3, n=2, automatic width, fused tiles"
+    else:
+        h, w = H, W
+        im, cv = make_inputs()
+        img, cov = torch.from_numpy(im).cuda(), torch.from_numpy(cv).cuda()
+        vmax = float(np.abs(im).max())
+        if args.workload == "sampled2048":
+            f = bsf.BoxSplineFilter(h, w, 1, "symmetric", frac_bits=-1, value_bound=vmax,
+                                    step_rule=bsf.BSF_STEP_SAMPLED)
+            desc = WORKLOAD.replace("n=2 (81 taps)", "n=1") + "; sampled continuous box spline"
+        else:
+            f = bsf.BoxSplineFilter(h, w, 2, "symmetric", frac_bits=-1, value_bound=vmax,
+                                    directions=bsf.BSF_DIRS_PAIR)
+            desc = WORKLOAD + "; both direction sets, switched per pixel"
+    f.set_option(bsf.BSF_OPT_SCAN_MODE, bsf.BSF_SCAN_THREE_PHASE)
+    f.plan(cov)
+    out = torch.empty((h, w), dtype=torch.float32, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        flush.zero_()
+        f.filter(img, cov, out=out)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local).__enter__()
+    es = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ee = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(world)
+    t0 = time.time()
+    for i in range(args.steps):
+        flush.zero_()
+        es[i].record(stream)
+        f.filter(img, cov, out=out)
+        ee[i].record(stream)
+    torch.cuda.synchronize()
+    clk.mark(t0, time.time())
+    clk.__exit__(None, None, None)
+    barrier(world)
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(es, ee)), world)
+    if f.status() != 0:
+        raise RuntimeError("device status")
+    info = f.info()
+    f.close()
+    if rank != 0:
+        return None
+    return {"metric": METRIC, "value": round(world * h * w * args.steps / (ms * 1e-3) / 1e6, 2), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms / args.steps, 5), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": f"u{8 * info.elem_bytes}", "data": "synthetic",
+            "config": {"workload": desc, "H": h, "W": w, "R": info.R, "frac_bits": info.frac_bits,
+                       "l2": "flushed before every timed step (256 MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "clocks": clk.summary()}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -846,9 +921,11 @@ def main():
                     help="rows of the workload each --impl reference step filters")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="spacevariant2048",
-                    choices=["spacevariant2048", "batch64", "diff8x1024"],
+                    choices=["spacevariant2048", "batch64", "diff8x1024", "tiles4096", "sampled2048",
+                             "pair2048"],
                     help="spacevariant2048: the benchmark line; batch64: the batched form; "
-                         "diff8x1024: continuous steps with the parameter gradient")
+                         "diff8x1024: continuous steps with the parameter gradient; "
+                         "tiles4096, sampled2048, pair2048: one configuration each (run_single)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "bsf":
         args.warmup = 3
@@ -858,6 +935,8 @@ def main():
         line = run_batch(args)
     elif args.workload == "diff8x1024":
         line = run_diff(args)
+    elif args.workload in ("tiles4096", "sampled2048", "pair2048"):
+        line = run_single(args)
     else:
         line = run_gpu(args)
     if line is not None:

@@ -150,7 +150,7 @@ extern "C" {
 #define BSF_OPT_SCAN_MODE    1  /* value BSF_SCAN_THREE_PHASE (default) or BSF_SCAN_LOOKBACK */
 #define BSF_OPT_WAIT_LIMIT   2  /* polls a block may spend waiting for a predecessor
                                    (default 1048576, >= 0); past it: BSF_ETIMEOUT */
-#define BSF_OPT_SCAN_CHUNK   4  /* rows per chunk of the three-phase scan, 16..4096 (default 64) */
+#define BSF_OPT_SCAN_CHUNK   4  /* rows per chunk of the three-phase scan, 16..4096 (default 48) */
 #define BSF_OPT_SCAN_SHORT_TILES 5  /* 1 = look-back tiles of half the rows (16 for uint64) */
 #define BSF_OPT_TEST_UNPUBLISHED 3  /* failure injection for tests: 1 = the look-back
                                        scan's first chunk never marks its results

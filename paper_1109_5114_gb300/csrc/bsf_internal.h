@@ -24,7 +24,7 @@ struct DevStatus {
 
 // Default and smallest chunk height (rows per chunk) of the three-phase
 // vertical running sums; workspace is sized for the smallest.
-constexpr int kScanChunk = 64;
+constexpr int kScanChunk = 48;
 constexpr int kScanChunkMin = 16;
 
 // Launchers; each returns the launch status (cudaGetLastError()).

@@ -22,6 +22,9 @@
 
 #include "bsf_internal.h"
 
+// rows per chunk of the vertical sums here (the static array is sized for it)
+constexpr int kNoallocChunk = 64;
+
 namespace {
 
 constexpr size_t kScratchBytes = 24u << 20;
@@ -68,7 +71,7 @@ extern "C" int bsf_filter_noalloc(const void* img, int dtype, long long ld, int 
   // carve the scratch: status | S [Hp][pitch] | agg | carry
   const long long Hp = (long long)H + 2LL * reach, Wp = (long long)W + 2LL * reach;
   const long long pitch = round_up((size_t)Wp, 32);
-  const long long nchunks = (Hp + kScanChunk - 1) / kScanChunk;
+  const long long nchunks = (Hp + kNoallocChunk - 1) / kNoallocChunk;
   const size_t off_S = round_up(sizeof(DevStatus), 256);
   const size_t scan_bytes = (size_t)nchunks * n * (size_t)(Wp + Hp - 1) * 8;
   const size_t off_agg = off_S + round_up((size_t)pitch * Hp * 8, 256);
@@ -94,7 +97,7 @@ extern "C" int bsf_filter_noalloc(const void* img, int dtype, long long ld, int 
     return BSF_ECUDA;
   const int skews[3] = {0, 1, -1};
   for (int i = 0; i < 3; ++i)
-    if (bsf_launch_vscan(BSF_FIX64, n, skews[i], false, S, pitch, (int)Hp, (int)Wp, kScanChunk, agg, carry, s) !=
+    if (bsf_launch_vscan(BSF_FIX64, n, skews[i], false, S, pitch, (int)Hp, (int)Wp, kNoallocChunk, agg, carry, s) !=
         cudaSuccess)
       return BSF_ECUDA;
   if (bsf_launch_stencil_d1(BSF_FIX64, n, S, pitch, reach, cov, BSF_COV_C, BSF_STEP_D1, H, W, 0, H, frac_bits, out,
