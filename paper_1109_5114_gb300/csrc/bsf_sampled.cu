@@ -9,9 +9,8 @@
 //
 // lambda_k = a_k / |d_k| from the minimum-kurtosis scales (the continuous
 // beta_a has covariance C exactly), quantised to Lq_k = max(1, RNE(512
-// lambda_k)).  Every tap then lies on the grid of 2^-10; the samples around
-// it (seven of a 3 x 3 block) get integer weights beta_b * 2^23
-// (bsf_grid_box_spline.h), so
+// lambda_k)).  Every tap then lies on the grid of 2^-10; the nine samples
+// around it get integer weights beta_b * 2^23 (bsf_grid_box_spline.h), so
 //   acc = sum_t (-1)^|t| sum_samples w S   (exact, modulo 2^b),
 //   out = RN(RN(acc) 2^(13 - q)) / RN(prod Lq)
 // since prod lambda = prod Lq / 2^36.  |acc| <= 2^23 prod lambda max|Q|,
@@ -49,10 +48,16 @@ k_stencil_sampled(const T* __restrict__ S, long long pitch, int R, const float* 
     const int Zx = X0 + o1 + o2 - o4, Zy = Y0 + o2 + o3 + o4;
     const int U = Zx & 1023, V = Zy & 1023;
     const int tri = V <= U ? (U + V <= 1024 ? 0 : 1) : (U + V >= 1024 ? 2 : 3);
-    // the seven samples (zx + i1, zy + i2), i1 in {-1, 0, 1}, i2 in
-    // {-2, -1, 0}, whose weights do not vanish on this triangle
+    int w[9];
+    grid_box_spline_weights(tri, U, V, w);
+    // samples (zx + i1, zy + i2), i1 in {-1, 0, 1}, i2 in {-2, -1, 0}
     const int base = (Zy >> 10) * p32 + (Zx >> 10);
-    const T f = grid_box_spline_tap<T>(tri, U, V, base, p32, [&](int i) { return bsf_load(S + i); });
+    T f = (T)0;
+#pragma unroll
+    for (int i1 = -1; i1 <= 1; ++i1)
+#pragma unroll
+      for (int i2 = -2; i2 <= 0; ++i2)
+        f += (T)(unsigned)w[(i1 + 1) * 3 + (i2 + 2)] * bsf_load(S + base + i2 * p32 + i1);
     const int par = __popc(t) & 1;
     acc = par ? acc - f : acc + f;
   }

@@ -13,25 +13,24 @@ HEADER = os.path.join(os.path.dirname(__file__), "..", "paper_1109_5114_gb300", 
 
 
 def _weights():
-    """{tri: {(c1, c2): weight expression}} parsed from the generated code
-    (cells left out of a triangle's branch have weight zero there)."""
+    """{tri: [expr for w[0..8]]} parsed from the header's switch."""
     text = open(HEADER).read()
     out, tri = {}, None
     for line in text.splitlines():
         m = re.match(r"\s*(case (\d)|default):", line)
         if m:
             tri = int(m.group(2)) if m.group(2) else 3
-            out[tri] = {}
+            out[tri] = [None] * 9
             continue
-        m = re.match(r"\s*f \+= \(T\)\(unsigned\)\((.*)\) \* load\(.*\);  // cell \((-?\d), (-?\d)\)", line)
+        m = re.match(r"\s*w\[(\d)\] = (.*);", line)
         if m and tri is not None:
-            out[tri][(int(m.group(2)), int(m.group(3)))] = m.group(1)
+            out[tri][int(m.group(1))] = m.group(2)
     return out
 
 
 def test_generated_weights_equal_the_exact_box_spline():
     W = _weights()
-    assert sorted(W) == [0, 1, 2, 3] and all(len(v) == 7 for v in W.values())
+    assert sorted(W) == [0, 1, 2, 3] and all(None not in v for v in W.values())
     rng = random.Random(0)
     for _ in range(400):
         U, V = rng.randrange(0, 1024), rng.randrange(0, 1024)
@@ -39,7 +38,6 @@ def test_generated_weights_equal_the_exact_box_spline():
         env = {"U": U, "V": V, "UU": U * U, "UV": U * V, "VV": V * V}
         for i1 in (-1, 0, 1):
             for i2 in (-2, -1, 0):
-                expr = W[tri].get((-i1, -i2))
-                got = eval(expr, {}, env) if expr else 0  # noqa: S307 (integer expression)
+                got = eval(W[tri][(i1 + 1) * 3 + (i2 + 2)], {}, env)  # noqa: S307 (integer expression)
                 want = sp.beta(Fr(-i1) + Fr(U, 1024), Fr(-i2) + Fr(V, 1024), (Fr(1),) * 4) * (1 << sp.WEIGHT_BITS)
                 assert got == want, (U, V, i1, i2)
