@@ -164,8 +164,10 @@ extern "C" {
 #define BSF_OPT_TILES        9  /* 1 (default): bsf_filter / bsf_filter_rows with an image run as one
                                    fused kernel of restarted tiles whenever a tile of at least
                                    64 x 64 outputs plus the padding R on each side fits in shared
-                                   memory (Cartesian set, BSF_STEP_D1 / _PAPER, BSF_FIX32/64/128,
-                                   BSF_F64ACC): each block pre-integrates its own window in
+                                   memory (BSF_STEP_D1 / _PAPER; the Cartesian set in every
+                                   precision, the second set and the pair in fixed point, the
+                                   pair with two windows per block): each block pre-integrates
+                                   its own window in
                                    shared memory, and no running sums are kept (a later
                                    bsf_filter with img NULL, or bsf_copy_preintegrated, needs
                                    bsf_preintegrate); same results as the global passes in fixed

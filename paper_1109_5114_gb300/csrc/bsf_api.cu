@@ -622,9 +622,8 @@ static int filter_impl(bsf_t h, const void* img, int dtype, long long ld, const 
   }
   if ((rc = reset_counters(h, true, false))) return rc;
   // one fused kernel of restarted tiles, when a tile fits in shared memory
-  if (img && h->tiles && !jac && h->dirset == BSF_DIRS_CARTESIAN &&
-      (h->step_rule == BSF_STEP_D1 || h->step_rule == BSF_STEP_D1_PAPER) &&
-      h->precision != BSF_F32KAHAN && h->R >= 0) {
+  if (img && h->tiles && !jac && (h->step_rule == BSF_STEP_D1 || h->step_rule == BSF_STEP_D1_PAPER) &&
+      h->R >= 0 && (h->dirset == BSF_DIRS_CARTESIAN || is_fixed(h->precision))) {
     if (dtype != BSF_U8 && dtype != BSF_F32 && dtype != BSF_F64)
       return fail(h, BSF_EINVAL, "bad image dtype %d", dtype);
     if (ld < h->W) return fail(h, BSF_EINVAL, "ld %lld < W %d", ld, h->W);
@@ -634,14 +633,14 @@ static int filter_impl(bsf_t h, const void* img, int dtype, long long ld, const 
       BSF_CUDA(h, cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
       h->max_smem = v;
     }
-    const int TT = h->precision == BSF_F32KAHAN ? 0 : bsf_tile_size(h->precision, h->R, h->max_smem);
+    const int TT = bsf_tile_size(h->precision, h->R, h->max_smem, h->dirset == BSF_DIRS_PAIR ? 2 : 1);
     if (TT > 0) {
       if ((rc = reset_counters(h, false, true))) return rc;
       cudaError_t e;
       {
         PhaseTimer t(h, BSF_PHASE_TILES);
-        e = bsf_launch_tiles(h->precision, h->n, img, dtype, ld, h->H, h->W, h->R, h->boundary, row0, rows, TT,
-                             h->q, cov, cov_kind, h->step_rule, out, out_dtype, ldo, h->st, h->stream);
+        e = bsf_launch_tiles(h->precision, h->n, h->dirset, img, dtype, ld, h->H, h->W, h->R, h->boundary, row0, rows,
+                             TT, h->q, cov, cov_kind, h->step_rule, out, out_dtype, ldo, h->st, h->stream);
       }
       if (e != cudaSuccess) return cuda_fail(h, e, "tile filter");
       h->have_S = false;  // no running sums are kept

@@ -163,13 +163,16 @@ cudaError_t bsf_launch_scans_second(int prec, int n, void* S, long long pitch, i
                                     void* agg, cudaStream_t s);
 
 // Tile-restarted pre-integration fused with the stencil (one launch,
-// Cartesian set, integer steps): bsf_tile_size gives the tile side T (a
+// integer steps, any direction set; the second set and the pair in fixed
+// point): bsf_tile_size gives the tile side T (a
 // multiple of 32) for this element precision and padding within max_smem
 // bytes of shared memory per block, or 0 when no tile of at least 64 fits.
-// prec BSF_FIX32/64/128 or BSF_F64ACC.  Outputs rows [row0, row0 + rows).
-int bsf_tile_size(int prec, int R, int max_smem);
-cudaError_t bsf_launch_tiles(int prec, int n, const void* img, int dtype, long long ld, int H, int W, int R,
-                             int boundary, int row0, int rows, int TT, int q, const float* cov, int cov_kind,
+// prec BSF_FIX32/64/128, BSF_F64ACC or BSF_F32KAHAN.  Outputs rows
+// [row0, row0 + rows).
+// windows: 2 for the pair of direction sets (two windows per block), else 1.
+int bsf_tile_size(int prec, int R, int max_smem, int windows);
+cudaError_t bsf_launch_tiles(int prec, int n, int dirset, const void* img, int dtype, long long ld, int H, int W,
+                             int R, int boundary, int row0, int rows, int TT, int q, const float* cov, int cov_kind,
                              int rule, void* out, int out_dtype, long long ldo, DevStatus* st, cudaStream_t s);
 
 // The sampled continuous box spline (BSF_STEP_SAMPLED): stencil on the

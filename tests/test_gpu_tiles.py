@@ -104,10 +104,11 @@ def test_large_padding_takes_the_global_passes():
     np.testing.assert_array_equal(out, modular.filter_modular(img, cov, 2, 2, q=12, R=info.R))
 
 
-@pytest.mark.parametrize("n,bound", [(1, 1e-8), (2, 1e-3)])
-def test_restarted_float64_sums_stay_accurate(n, bound):
-    # float64 running sums over a whole 1024^2 image lose most digits for
-    # n = 2; restarted per tile they are bounded by the window (P ~ 90):
+@pytest.mark.parametrize("n,bound,precision", [(1, 1e-8, 3), (2, 1e-3, 3), (1, 1e-5, 4)])
+def test_restarted_float_sums_stay_accurate(n, bound, precision):
+    # float64 (precision 3) or compensated float32 (precision 4) running
+    # sums over a whole 1024^2 image lose most digits for n = 2; restarted per
+    # tile they are bounded by the window (P ~ 90):
     # about P^(4n) / 2^(2n) max|f|, whose float64 rounding, over (n+1)^4 taps
     # with weights up to 2^(4(n-1)), is ~1e-11 (n = 1) and ~1e-5 (n = 2) of
     # the mass
@@ -115,8 +116,8 @@ def test_restarted_float64_sums_stay_accurate(n, bound):
     img = wl.blob_image(H, W, seed=7).astype(np.float32)
     cov = _cov(H, W, seed=8, smax=2.0)
     exact, info, _, _ = _run(img, cov, n, 2, 30, precision=1, out64=True)
-    tiled, _, st, prof = _run(img, cov, n, 2, -1, precision=3, tiles=1, out64=True)
-    glob, _, _, _ = _run(img, cov, n, 2, -1, precision=3, tiles=0, out64=True)
+    tiled, _, st, prof = _run(img, cov, n, 2, -1, precision=precision, tiles=1, out64=True)
+    glob, _, _, _ = _run(img, cov, n, 2, -1, precision=precision, tiles=0, out64=True)
     assert prof["tiles"][1] == 1
     scale = np.abs(exact).max()
     e_tiled = np.abs(tiled - exact).max() / scale
@@ -138,3 +139,38 @@ def test_overflow_in_a_tile_is_reported():
     assert f.read_profile()["tiles"][1] == 1
     assert f.status() == bsf.BSF_EOVERFLOW
     f.close()
+
+
+@pytest.mark.parametrize("directions,n,precision", [(1, 1, 1), (1, 2, 1), (1, 3, 2), (2, 1, 1), (2, 2, 1),
+                                                    (2, 2, 5), (2, 3, 1)])
+def test_tiles_of_the_second_set_and_the_pair(directions, n, precision):
+    # the fused tiles with the second direction set (its running sums walked
+    # along (2,1), (1,2), (-1,2), (-2,1) in the window) and with the pair
+    # (two windows per block): equal to the global passes and to the oracle
+    import torch
+
+    from oracle import knight as kn
+    from paper_1109_5114_gb300 import bsf
+    H, W = 131, 170
+    img = wl.random_integer_image(H, W, seed=n + 10 * directions, lo=0, hi=255).astype(np.uint8)
+    cov = _cov(H, W, seed=20 + n, smax=1.6 if precision == 5 else 2.2)
+    q = 0 if precision == 5 else 8
+    outs, profs, R = [], [], None
+    for tiles in (1, 0):
+        f = bsf.BoxSplineFilter(H, W, n, "symmetric", precision=precision, frac_bits=q, directions=directions)
+        f.set_option(bsf.BSF_OPT_TILES, tiles)
+        f.set_profiling(True)
+        out = f.filter(torch.from_numpy(img).cuda(), torch.from_numpy(cov).cuda())
+        profs.append(f.read_profile())
+        assert f.status() == 0
+        R = f.info().R
+        outs.append(out.cpu().numpy())
+        f.close()
+    assert profs[0]["tiles"][1] == 1 and profs[1]["tiles"][1] == 0
+    np.testing.assert_array_equal(outs[0], outs[1])
+    bits = {5: 32, 1: 64, 2: 128}[precision]
+    if directions == 1:
+        ref = kn.filter_modular_k(img, cov, n, 2, q=q, bits=bits, R=R)
+    else:
+        ref = kn.algorithm2(img, cov, n, 2, q=q, bits=bits, R=R)[0]
+    np.testing.assert_array_equal(outs[0], ref)
