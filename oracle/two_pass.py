@@ -10,8 +10,8 @@ Proposition 2 (the split) the two filters compose into one of covariance C.
 Delta C must stay within the elongation bound, which gives eq. "condition2"
 on sigma^2; sigma^2 is set to half that bound (Algorithm 1, step 1).
 
-Readings: one global sigma^2 (the space-invariant first pass of Algorithm 1,
-read as in the survey of the method): half the smallest condition-2 bound over
+Readings: one global sigma^2 (the first pass of Algorithm 1 is the
+space-invariant BoxFilter): half the smallest condition-2 bound over
 the field (floored at zero); the bound is written algebraically,
     root = sqrt((C11 - C22)^2 + 4 C12^2),
     tan(phi) = ((C22 - C11) + root) / (2 C12) if C22 >= C11,
