@@ -115,3 +115,67 @@ def test_constant_image_and_steps():
     f = np.full((H, W), 3.0)
     out = sp.filter_sampled(f, cov, kernels.REPLICATE, 10, out_dtype=np.float64, pixels=[(10, 10)])
     assert abs(out[(10, 10)] - 3.0) < 0.05
+
+
+def test_second_set_grid_box_spline():
+    # beta'_b: unit mass, partition of unity over the lattice, symmetric about
+    # its centre (0, 3) under the reflections of the square, zero outside
+    # its octagon (the zonotope of the four steps) and positive inside
+    rng = random.Random(5)
+    for _ in range(12):
+        x = (Fr(rng.randrange(0, 64), 64), Fr(rng.randrange(0, 64), 64))
+        assert sum(sp.beta_k(x[0] - m1, x[1] - m2, ONES) for m1 in range(-4, 5) for m2 in range(-7, 2)) == 1
+    for _ in range(40):
+        a, b = Fr(rng.randrange(-190, 191), 64), Fr(rng.randrange(-190, 191), 64)
+        v = sp.beta_k(a, 3 + b, ONES)
+        for a2, b2 in ((b, a), (-a, b), (a, -b), (-b, -a)):
+            assert sp.beta_k(a2, 3 + b2, ONES) == v
+    # the octagon: |x| + ... ; vertices of sum_k [0, e_k] include (0, 0), (2, 1), (3, 3), (0, 6)
+    assert sp.beta_k(Fr(0), Fr(0), ONES) == 0 and sp.beta_k(Fr(0), Fr(6), ONES) == 0
+    assert sp.beta_k(Fr(0), Fr(3), ONES) > 0 and sp.beta_k(Fr(5, 2), Fr(3), ONES) > 0
+    assert sp.beta_k(Fr(3), Fr(3), ONES) == 0 and sp.beta_k(Fr(-3), Fr(3), ONES) == 0
+
+
+def test_second_set_weights_are_integers_over_491520():
+    rng = random.Random(6)
+    for _ in range(300):
+        x = (Fr(rng.randrange(-192, 193), 64), Fr(rng.randrange(0, 385), 64))
+        assert (sp.beta_k(x[0], x[1], ONES) * sp.WEIGHT_DEN_K).denominator == 1
+
+
+@pytest.mark.parametrize("boundary", [0, 2])
+def test_second_set_paper_route_equals_the_sampled_box_spline(boundary):
+    # Algorithm 3 as printed (running sums along (2,1), (1,2), (-1,2), (-2,1),
+    # interpolation by beta'_b, the 16-tap differences) is exactly the
+    # sampled beta'_a
+    H, W = 7, 8
+    f = synth.random_integer_image(H, W, seed=7, lo=-9, hi=9).astype(np.float64)
+    fq = quantize(f, 0, as_object=True)
+    rng = random.Random(8 + boundary)
+    for _ in range(4):
+        Lq = np.array([rng.randrange(1, 90) for _ in range(4)])
+        R = int(sp.reach_k(Lq)) + 1
+        y, x = rng.randrange(H), rng.randrange(W)
+        a = sp.exact_value_k(fq, Lq, boundary, y, x)
+        assert a == sp.paper_route_value_k(fq, Lq, boundary, y, x, R)
+        sp.accumulator_k(a, Lq)   # integral
+
+
+def test_second_set_covariance():
+    # the continuous beta'_a has covariance sum_k lambda_k^2 e_k e_k^T / 12
+    lam = (Fr(3, 2), Fr(1), Fr(5, 4), Fr(3, 4))
+    h = Fr(1, 6)
+    tx = sum(l * e[0] for l, e in zip(lam, sp._E)) / 2
+    ty = sum(l * e[1] for l, e in zip(lam, sp._E)) / 2
+    mass, m2 = Fr(0), np.zeros((2, 2))
+    for i in range(-33, 34):
+        for j in range(-33, 34):
+            y = (tx + (i + Fr(1, 2)) * h, ty + (j + Fr(1, 2)) * h)
+            b = sp.beta_k(y[0], y[1], lam)
+            if b:
+                mass += b * h * h
+                v = np.array([float(y[0] - tx), float(y[1] - ty)])
+                m2 += float(b * h * h) * np.outer(v, v)
+    want = sum(float(l) ** 2 / 12 * np.outer(e, e) for l, e in zip(lam, sp._E))
+    assert abs(float(mass) - 1) < 2e-3
+    assert np.allclose(m2, want, atol=0.03)
