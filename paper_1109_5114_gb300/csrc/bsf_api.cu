@@ -237,6 +237,7 @@ int check_cov_kind(bsf_t h, int cov_kind) {
 // Smallest padding of the sampled box spline's taps (lambda = 1 on every
 // direction).
 constexpr int kSampledMinPad = 4;
+constexpr int kSampledMinPadSecond = 10;  // the second set's, lambda = (1, 1, 1, 1)
 
 // Smallest padding of the continuous-step taps (identity steps): samples at
 // -3..1 (n = 2) or -2..1 (n = 1) along every direction.
@@ -286,7 +287,10 @@ int run_steps(bsf_t h, const float* cov, int cov_kind, bool sync_plan) {
       // the solve ran unbounded: every tap of this field fits this R
       int R = reach > 3 * h->n ? reach : 3 * h->n;
       if (h->step_rule == BSF_STEP_D2 && R < d2_min_reach(h->n)) R = d2_min_reach(h->n);
-      if (h->step_rule == BSF_STEP_SAMPLED && R < kSampledMinPad) R = kSampledMinPad;
+      if (h->step_rule == BSF_STEP_SAMPLED) {
+        const int minpad = h->dirset == BSF_DIRS_CARTESIAN ? kSampledMinPad : kSampledMinPadSecond;
+        if (R < minpad) R = minpad;
+      }
       h->R = widen && h->R > R ? h->R : R;
     }
     h->planned = true;
@@ -600,12 +604,13 @@ static int filter_impl(bsf_t h, const void* img, int dtype, long long ld, const 
       h->have_S = false;
     }
     if (jac) return fail(h, BSF_EINVAL, "the sampled box spline has no Jacobian");
-    if (h->R >= 0 && h->R < kSampledMinPad)
-      return fail(h, BSF_EINVAL, "padding R = %d below %d, the reach of the sampled taps", h->R, kSampledMinPad);
+    const int minpad = h->dirset == BSF_DIRS_CARTESIAN ? kSampledMinPad : kSampledMinPadSecond;
+    if (h->R >= 0 && h->R < minpad)
+      return fail(h, BSF_EINVAL, "padding R = %d below %d, the reach of the sampled taps", h->R, minpad);
   }
   if (h->dirset != BSF_DIRS_CARTESIAN) {
-    if (h->step_rule == BSF_STEP_D2 || h->step_rule == BSF_STEP_SAMPLED)
-      return fail(h, BSF_EINVAL, "the second direction set: integer steps only");
+    if (h->step_rule == BSF_STEP_D2)
+      return fail(h, BSF_EINVAL, "the second direction set: integer or sampled steps only");
     if (!is_fixed(h->precision)) return fail(h, BSF_EINVAL, "the second direction set needs fixed point");
   }
   if (out_dtype != BSF_F32 && out_dtype != BSF_F64) return fail(h, BSF_EINVAL, "bad out dtype %d", out_dtype);
@@ -664,8 +669,8 @@ static int filter_impl(bsf_t h, const void* img, int dtype, long long ld, const 
                                 h->H, h->W, row0, rows, h->S_q, out, out_dtype, ldo, jac, ldj,
                                 (long long)rows * ldj, nullptr, 0, h->st, h->stream);
     else if (h->step_rule == BSF_STEP_SAMPLED)
-      e = bsf_launch_stencil_sampled(h->precision, h->S, h->pitch, h->R, cov, cov_kind, h->H, h->W, row0,
-                                     rows, h->S_q, out, out_dtype, ldo, h->st, h->stream);
+      e = bsf_launch_stencil_sampled(h->precision, h->dirset, h->S, h->S2, h->pitch, h->R, cov, cov_kind, h->H,
+                                     h->W, row0, rows, h->S_q, out, out_dtype, ldo, h->st, h->stream);
     else if (h->dirset == BSF_DIRS_CARTESIAN)
       e = bsf_launch_stencil_d1(h->precision, h->n, h->S, h->pitch, h->R, cov, cov_kind,
                                 h->step_rule, h->H, h->W, row0, rows, h->S_q, out, out_dtype, ldo,
@@ -715,9 +720,11 @@ static cudaError_t stencil_band(bsf_t h, const float* cov, int cov_kind, int y0,
     return bsf_launch_stencil_d2(h->precision, h->n, 0, S, h->pitch, h->R, cov, cov_kind, h->H, h->W,
                                  y0, rows, h->S_q, out, out_dtype, ldo, nullptr, 0, 0, nullptr, 0,
                                  h->st, h->stream);
-  if (h->step_rule == BSF_STEP_SAMPLED)
-    return bsf_launch_stencil_sampled(h->precision, S, h->pitch, h->R, cov, cov_kind, h->H, h->W, y0, rows,
-                                      h->S_q, out, out_dtype, ldo, h->st, h->stream);
+  if (h->step_rule == BSF_STEP_SAMPLED) {
+    const void* S2 = h->S2 ? static_cast<const char*>(h->S2) + (size_t)y0 * h->pitch * h->elem : nullptr;
+    return bsf_launch_stencil_sampled(h->precision, h->dirset, S, S2, h->pitch, h->R, cov, cov_kind, h->H, h->W,
+                                      y0, rows, h->S_q, out, out_dtype, ldo, h->st, h->stream);
+  }
   return bsf_launch_stencil_d1(h->precision, h->n, S, h->pitch, h->R, cov, cov_kind, h->step_rule,
                                h->H, h->W, y0, rows, h->S_q, out, out_dtype, ldo, h->st, h->stream);
 }

@@ -176,10 +176,11 @@ cudaError_t bsf_launch_tiles(int prec, int n, int dirset, const void* img, int d
                              int rule, void* out, int out_dtype, long long ldo, DevStatus* st, cudaStream_t s);
 
 // The sampled continuous box spline (BSF_STEP_SAMPLED): stencil on the
-// Cartesian order-1 running sums S.  prec BSF_FIX64 or BSF_FIX128.
-cudaError_t bsf_launch_stencil_sampled(int prec, const void* S, long long pitch, int R, const float* cov,
-                                       int cov_kind, int H, int W, int row0, int rows, int q, void* out,
-                                       int out_dtype, long long ldo, DevStatus* st, cudaStream_t s);
+// order-1 running sums S of the direction set (the pair: S Cartesian, S2 the
+// second set's).  prec BSF_FIX64 or BSF_FIX128.
+cudaError_t bsf_launch_stencil_sampled(int prec, int dirset, const void* S, const void* S2, long long pitch, int R,
+                                       const float* cov, int cov_kind, int H, int W, int row0, int rows, int q,
+                                       void* out, int out_dtype, long long ldo, DevStatus* st, cudaStream_t s);
 
 // Algorithm 1's split of a field: min over pixels of the condition-2 bound
 // (floored at zero) into *min_bits (device, double bits), then the isotropic

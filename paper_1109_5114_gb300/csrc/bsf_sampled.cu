@@ -15,29 +15,23 @@
 //   out = RN(RN(acc) 2^(13 - q)) / RN(prod Lq)
 // since prod lambda = prod Lq / 2^36.  |acc| <= 2^23 prod lambda max|Q|,
 // the bound the mass prod Lq 2^-13 enters.
+//
+// The second set (Algorithm 3 as printed: beta'_a, the running sums along
+// e1 = (2,1), e2 = (1,2), e3 = (-1,2), e4 = (-2,1) interpolated by beta'_b):
+// lambda_k = a_k / sqrt(5) quantised to Lq = max(1, RNE(32 lambda)), the taps
+// on the grid of 2^-6, the samples of a 6 x 6 block per tap weighted by
+// beta'_b * 491520 (bsf_knight_box_spline.h), out = RN(RN(acc) 2^(5 - q)) /
+// RN(15 prod Lq).  The pair chooses per pixel by sector.
 #include "bsf_grid_box_spline.h"
+#include "bsf_knight_box_spline.h"
 #include "bsf_stencil.cuh"
 
 namespace {
 
-template <typename T, typename Out>
-__global__ void __launch_bounds__(256, 2)
-k_stencil_sampled(const T* __restrict__ S, long long pitch, int R, const float* __restrict__ cov, int kind,
-                  int H, int W, int row0, int rows, float scale_f, double scale_d, Out* __restrict__ out,
-                  long long ldo, DevStatus* st) {
-  const int x = blockIdx.x * 32 + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= W || y >= rows) return;
-  const long long HW = (long long)H * W, i = (long long)(row0 + y) * W + x;
-  float C11, C12, C22;
-  bsf_solve::load_cov(cov, kind, HW, i, C11, C12, C22);
-  int Lq[4], flags, reach;
-  const bool in_reach = bsf_solve::pixel_steps_sampled(C11, C12, C22, R, Lq, flags, reach);
-  count_pixel_flags(flags, in_reach, st);
-
-  const int p32 = (int)pitch;
-  // the pixel in units of 2^-10 of the padded frame
-  const int X0 = (x + R) << 10, Y0 = (y + R) << 10;
+// Cartesian set: the 16 taps on the 2^-10 grid, nine samples each.
+template <typename T>
+__device__ __forceinline__ T sampled_acc(const T* __restrict__ S, int p32, int x, int y, int R, const int Lq[4]) {
+  const int X0 = (x + R) << 10, Y0 = (y + R) << 10;  // the pixel in units of 2^-10 of the padded frame
   T acc = (T)0;
 #pragma unroll 2
   for (int t = 0; t < 16; ++t) {
@@ -58,13 +52,84 @@ k_stencil_sampled(const T* __restrict__ S, long long pitch, int R, const float* 
 #pragma unroll
       for (int i2 = -2; i2 <= 0; ++i2)
         f += (T)(unsigned)w[(i1 + 1) * 3 + (i2 + 2)] * bsf_load(S + base + i2 * p32 + i1);
-    const int par = __popc(t) & 1;
-    acc = par ? acc - f : acc + f;
+    acc = (__popc(t) & 1) ? acc - f : acc + f;
   }
+  return acc;
+}
 
-  // mass prod Lq (exact in 128 bits) and the bound |acc| <= 2^-13 prod Lq max|Q|
-  const u128 M = (u128)(unsigned)Lq[0] * (unsigned)Lq[1] * (u128)((unsigned long long)(unsigned)Lq[2] * (unsigned)Lq[3]);
-  const float Mf = (float)Lq[0] * (float)Lq[1] * (float)Lq[2] * (float)Lq[3] * 0x1p-13f;
+// Second set: the 16 taps on the 2^-6 grid, the samples of a 6 x 6 block
+// around each (beta'_b lies within [-3, 3] x [0, 6] of a sample), weighted
+// by the table of beta'_b * 491520 folded by its symmetries.
+template <typename T>
+__device__ __forceinline__ T sampled_acc_k(const T* __restrict__ S, int p32, int x, int y, int R, const int Lq[4]) {
+  const int X0 = (x + R) << 6, Y0 = (y + R) << 6;  // units of 2^-6
+  T acc = (T)0;
+#pragma unroll 1
+  for (int t = 0; t < 16; ++t) {
+    // offsets (1 - 2 t_k) Lq_k e_k (units of 2^-6) of e1 = (2,1), e2 = (1,2),
+    // e3 = (-1,2), e4 = (-2,1)
+    const int o1 = (t & 1) ? -Lq[0] : Lq[0], o2 = (t & 2) ? -Lq[1] : Lq[1];
+    const int o3 = (t & 4) ? -Lq[2] : Lq[2], o4 = (t & 8) ? -Lq[3] : Lq[3];
+    const int Zx = X0 + 2 * o1 + o2 - o3 - 2 * o4, Zy = Y0 + o1 + 2 * o2 + 2 * o3 + o4;
+    const int U = Zx & 63, V = Zy & 63;
+    const int base = (Zy >> 6) * p32 + (Zx >> 6);
+    T f = (T)0;
+    // sample (zx + i1, zy + i2): offset from beta'_b's centre (0, 3), units
+    // of 2^-6: (U - 64 i1, V - 64 i2 - 192)
+#pragma unroll
+    for (int i2 = -5; i2 <= 0; ++i2) {
+      const int b2 = V - 64 * i2 - 192;
+#pragma unroll
+      for (int i1 = -2; i1 <= 3; ++i1) {
+        const int b1 = U - 64 * i1;
+        const int ax = b1 < 0 ? -b1 : b1, ay = b2 < 0 ? -b2 : b2;
+        const int a = ax > ay ? ax : ay, b = ax > ay ? ay : ax;
+        if (a <= 192) {
+          const int w = __ldg(&kKnightBoxSpline[a * (a + 1) / 2 + b]);
+          if (w) f += (T)(unsigned)w * bsf_load(S + base + i2 * p32 + i1);
+        }
+      }
+    }
+    acc = (__popc(t) & 1) ? acc - f : acc + f;
+  }
+  return acc;
+}
+
+// DS (BSF_DIRS_*): the Cartesian set on S, the second set on S, or the pair
+// (S Cartesian, S2 the second set's sums), chosen per pixel by sector.
+template <typename T, typename Out, int DS>
+__global__ void __launch_bounds__(256, 2)
+k_stencil_sampled(const T* __restrict__ S, const T* __restrict__ S2, long long pitch, int R,
+                  const float* __restrict__ cov, int kind, int H, int W, int row0, int rows, int q,
+                  Out* __restrict__ out, long long ldo, DevStatus* st) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= W || y >= rows) return;
+  const long long HW = (long long)H * W, i = (long long)(row0 + y) * W + x;
+  float C11, C12, C22;
+  bsf_solve::load_cov(cov, kind, HW, i, C11, C12, C22);
+  const bool second = DS == BSF_DIRS_SECOND ||
+                      (DS == BSF_DIRS_PAIR && bsf_solve::use_second_set(C11, C12, C22));
+  int Lq[4], flags, reach;
+  const bool in_reach = second ? bsf_solve::pixel_steps_sampled_k(C11, C12, C22, R, Lq, flags, reach)
+                               : bsf_solve::pixel_steps_sampled(C11, C12, C22, R, Lq, flags, reach);
+  count_pixel_flags(flags, in_reach, st);
+  const int p32 = (int)pitch;
+  T acc;
+  int e;       // out = RN(RN(acc) 2^(e - q)) / RN(M)
+  u128 M;      // Cartesian: prod Lq, e = 13; second set: 15 prod Lq, e = 5
+  if (DS == BSF_DIRS_CARTESIAN || !second) {
+    acc = sampled_acc<T>(S, p32, x, y, R, Lq);
+    e = 13;
+    M = 1;
+  } else {
+    acc = sampled_acc_k<T>(DS == BSF_DIRS_PAIR ? S2 : S, p32, x, y, R, Lq);
+    e = 5;
+    M = 15;
+  }
+  M *= (u128)(unsigned)Lq[0] * (unsigned)Lq[1] * (u128)((unsigned long long)(unsigned)Lq[2] * (unsigned)Lq[3]);
+  // the bound |acc| <= M 2^-e max|Q| (the weights' sum times prod lambda)
+  const float Mf = bsf_rn32_u(M) * bsf_pow2_f32(-e);
   const float maxq = __uint_as_float(st->max_absq_bits) + 1.f;
   if (maxq * Mf * 1.0001f >= bsf_pow2_f32(ElemBits<T>::value - 1)) {
     atomicAdd(&st->overflow_count, 1u);
@@ -72,44 +137,62 @@ k_stencil_sampled(const T* __restrict__ S, long long pitch, int R, const float* 
   }
   Out* o = out + (long long)y * ldo + x;
   if constexpr (sizeof(Out) == 4) {
-    const float xa = __fmul_rn(to_f32<T>(acc, acc), scale_f);
+    const float xa = __fmul_rn(to_f32<T>(acc, acc), bsf_pow2_f32(e - q));  // q <= 100: normal
     *o = __fdiv_rn(xa, bsf_rn32_u(M));
   } else {
-    const double xa = __dmul_rn(to_f64<T>(acc), scale_d);
+    const double xa = __dmul_rn(to_f64<T>(acc), ldexp(1.0, e - q));
     *o = __ddiv_rn(xa, bsf_rn64_u(M));
   }
 }
 
-template <typename T>
-cudaError_t launch_sampled_t(const T* S, long long pitch, int R, const float* cov, int kind, int H, int W,
-                             int row0, int rows, int q, void* out, int out_dtype, long long ldo, DevStatus* st,
-                             cudaStream_t s) {
+template <typename T, int DS>
+cudaError_t launch_sampled_t(const T* S, const T* S2, long long pitch, int R, const float* cov, int kind, int H,
+                             int W, int row0, int rows, int q, void* out, int out_dtype, long long ldo,
+                             DevStatus* st, cudaStream_t s) {
   dim3 block(32, 8);
   dim3 grid((W + 31) / 32, (rows + 7) / 8);
-  // 2^(13 - q) with q <= 100: normal in float32
-  const float sf = ldexpf(1.f, 13 - q);
-  const double sd = ldexp(1.0, 13 - q);
   if (out_dtype == BSF_F32)
-    k_stencil_sampled<T, float><<<grid, block, 0, s>>>(S, pitch, R, cov, kind, H, W, row0, rows, sf, sd,
-                                                       (float*)out, ldo, st);
+    k_stencil_sampled<T, float, DS><<<grid, block, 0, s>>>(S, S2, pitch, R, cov, kind, H, W, row0, rows, q,
+                                                           (float*)out, ldo, st);
   else if (out_dtype == BSF_F64)
-    k_stencil_sampled<T, double><<<grid, block, 0, s>>>(S, pitch, R, cov, kind, H, W, row0, rows, sf, sd,
-                                                        (double*)out, ldo, st);
+    k_stencil_sampled<T, double, DS><<<grid, block, 0, s>>>(S, S2, pitch, R, cov, kind, H, W, row0, rows, q,
+                                                            (double*)out, ldo, st);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_sampled_d(int dirset, const void* S, const void* S2, long long pitch, int R, const float* cov,
+                             int kind, int H, int W, int row0, int rows, int q, void* out, int out_dtype,
+                             long long ldo, DevStatus* st, cudaStream_t s) {
+  const T* a = (const T*)S;
+  const T* b = (const T*)S2;
+  switch (dirset) {
+    case BSF_DIRS_CARTESIAN:
+      return launch_sampled_t<T, BSF_DIRS_CARTESIAN>(a, b, pitch, R, cov, kind, H, W, row0, rows, q, out, out_dtype,
+                                                     ldo, st, s);
+    case BSF_DIRS_SECOND:
+      return launch_sampled_t<T, BSF_DIRS_SECOND>(a, b, pitch, R, cov, kind, H, W, row0, rows, q, out, out_dtype,
+                                                  ldo, st, s);
+    case BSF_DIRS_PAIR:
+      if (!S2) return cudaErrorInvalidValue;
+      return launch_sampled_t<T, BSF_DIRS_PAIR>(a, b, pitch, R, cov, kind, H, W, row0, rows, q, out, out_dtype, ldo,
+                                                st, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace
 
-cudaError_t bsf_launch_stencil_sampled(int prec, const void* S, long long pitch, int R, const float* cov,
-                                       int cov_kind, int H, int W, int row0, int rows, int q, void* out,
-                                       int out_dtype, long long ldo, DevStatus* st, cudaStream_t s) {
+cudaError_t bsf_launch_stencil_sampled(int prec, int dirset, const void* S, const void* S2, long long pitch, int R,
+                                       const float* cov, int cov_kind, int H, int W, int row0, int rows, int q,
+                                       void* out, int out_dtype, long long ldo, DevStatus* st, cudaStream_t s) {
   if (prec == BSF_FIX64)
-    return launch_sampled_t<uint64_t>((const uint64_t*)S, pitch, R, cov, cov_kind, H, W, row0, rows, q, out,
-                                      out_dtype, ldo, st, s);
+    return launch_sampled_d<uint64_t>(dirset, S, S2, pitch, R, cov, cov_kind, H, W, row0, rows, q, out, out_dtype,
+                                      ldo, st, s);
   if (prec == BSF_FIX128)
-    return launch_sampled_t<u128>((const u128*)S, pitch, R, cov, cov_kind, H, W, row0, rows, q, out, out_dtype,
-                                  ldo, st, s);
+    return launch_sampled_d<u128>(dirset, S, S2, pitch, R, cov, cov_kind, H, W, row0, rows, q, out, out_dtype, ldo,
+                                  st, s);
   return cudaErrorInvalidValue;
 }

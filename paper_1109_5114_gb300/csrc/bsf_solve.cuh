@@ -231,6 +231,39 @@ __device__ __forceinline__ bool pixel_steps_k(float C11, float C12, float C22, i
   return true;
 }
 
+// Sampled continuous box spline of the second set (BSF_STEP_SAMPLED with
+// BSF_DIRS_SECOND / _PAIR, order 1): lambda_k = a_k / sqrt(5) = sqrt(3A_k / 15),
+// quantised to Lq_k = max(1, RNE(32 lambda_k)).  The taps lie within
+// Sx / 64 across and Sy / 64 down of the pixel (Sx = 2 Lq1 + Lq2 + Lq3 +
+// 2 Lq4, Sy = Lq1 + 2 Lq2 + 2 Lq3 + Lq4) and the interpolation reaches two
+// samples left, three right, five up: reach = max(ceil(Sx / 32),
+// ceil(Sy / 32)) / 2 + 7.  Out of reach: Lq = 32 (lambda = 1), false.
+__device__ __forceinline__ int sampled_reach_k(const int Lq[4]) {
+  const long long sx = 2LL * Lq[0] + Lq[1] + Lq[2] + 2LL * Lq[3];
+  const long long sy = (long long)Lq[0] + 2LL * Lq[1] + 2LL * Lq[2] + Lq[3];
+  const long long cx = (sx + 31) >> 5, cy = (sy + 31) >> 5;
+  const long long r = (cx > cy ? cx : cy) / 2 + 7;
+  return r > (1 << 30) ? (1 << 30) : (int)r;
+}
+
+__device__ __forceinline__ bool pixel_steps_sampled_k(float C11, float C12, float C22, int R, int Lq[4],
+                                                      int& flags, int& reach) {
+  Solved sv = solve_scales_k(C11, C12, C22, 12.f);
+  flags = sv.flags;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float lam = fminf(__fsqrt_rn(__fdiv_rn(sv.A[k], 15.f)), 33554432.f);  // 32 lambda in int range
+    Lq[k] = max(__float2int_rn(__fmul_rn(lam, 32.f)), 1);
+  }
+  reach = sampled_reach_k(Lq);
+  if (R >= 0 && reach > R) {
+    Lq[0] = Lq[1] = Lq[2] = Lq[3] = 32;
+    reach = sampled_reach_k(Lq);
+    return false;
+  }
+  return true;
+}
+
 // Algorithm 2's sector: beta'_a where its elongation bound is the larger one,
 // i.e. |C11 - C22| < 3 |C12| < 6 |C11 - C22| (|C11 - C22| rounded once to
 // float64; 3|C12| and 2|C11 - C22| are exact there).

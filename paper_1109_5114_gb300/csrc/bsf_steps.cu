@@ -32,10 +32,15 @@ __global__ void k_steps(const float* __restrict__ cov, int kind, int H, int W, i
         L[k] = min(Hq[k] >> 9, 65535);
       }
     } else if (rule == BSF_STEP_SAMPLED) {
-      if (!pixel_steps_sampled(C11, C12, C22, R, L, flags, reach)) ++my_range;
-      // the bound of |acc|: prod Lq 2^-13 (times max|Q|)
-      mass = (float)L[0] * (float)L[1] * (float)L[2] * (float)L[3] * 0x1p-13f;
-      for (int k = 0; k < 4; ++k) L[k] = min(L[k] >> 9, 65535);  // floor(lambda)
+      const bool second = dirset == BSF_DIRS_SECOND || (dirset == BSF_DIRS_PAIR && use_second_set(C11, C12, C22));
+      const bool ok = second ? pixel_steps_sampled_k(C11, C12, C22, R, L, flags, reach)
+                             : pixel_steps_sampled(C11, C12, C22, R, L, flags, reach);
+      if (!ok) ++my_range;
+      // the bound of |acc|: prod Lq 2^-13 (Cartesian) or 15 prod Lq 2^-5 (second set), times max|Q|
+      mass = (float)L[0] * (float)L[1] * (float)L[2] * (float)L[3] * (second ? 15.f * 0x1p-5f : 0x1p-13f);
+      const int sh = second ? 5 : 9;
+      for (int k = 0; k < 4; ++k) L[k] = min(L[k] >> sh, 65535);  // floor(lambda)
+      if (dirset == BSF_DIRS_PAIR && second) L[0] |= 0x8000;
     } else {
       bool second;
       if (!pixel_steps_set(dirset, C11, C12, C22, n, rule, R, L, flags, reach, second)) ++my_range;
@@ -111,7 +116,7 @@ cudaError_t bsf_launch_steps(const float* cov, int cov_kind, int H, int W, int n
                              int dirset, int R, ushort4* Lf, DevStatus* st, cudaStream_t s) {
   if (cov_kind != BSF_COV_C && cov_kind != BSF_COV_LOGSIG_THETA_LOGRHO) return cudaErrorInvalidValue;
   if (rule == BSF_STEP_D2 && (n > 2 || dirset != BSF_DIRS_CARTESIAN)) return cudaErrorInvalidValue;
-  if (rule == BSF_STEP_SAMPLED && (n != 1 || dirset != BSF_DIRS_CARTESIAN)) return cudaErrorInvalidValue;
+  if (rule == BSF_STEP_SAMPLED && n != 1) return cudaErrorInvalidValue;
   if (dirset < BSF_DIRS_CARTESIAN || dirset > BSF_DIRS_PAIR) return cudaErrorInvalidValue;
   const int threads = 256;
   k_steps<<<grid_for((long long)H * W, threads), threads, 0, s>>>(cov, cov_kind, H, W, n, rule,

@@ -20,13 +20,13 @@ def _lib():
     build.build()
 
 
-def _run(img, cov, boundary, q, precision=1, out64=False):
+def _run(img, cov, boundary, q, precision=1, out64=False, directions=0):
     import torch
 
     from paper_1109_5114_gb300 import bsf
     H, W = img.shape
     f = bsf.BoxSplineFilter(H, W, 1, boundary, precision=precision, frac_bits=q,
-                            step_rule=bsf.BSF_STEP_SAMPLED)
+                            step_rule=bsf.BSF_STEP_SAMPLED, directions=directions)
     out = f.filter(torch.from_numpy(np.ascontiguousarray(img)).cuda(), torch.from_numpy(cov).cuda(),
                    out_dtype=torch.float64 if out64 else torch.float32)
     torch.cuda.synchronize()
@@ -96,8 +96,34 @@ def test_sampled_argument_errors():
         f.backward(torch.ones((16, 16), device="cuda"), cov)
     torch.cuda.synchronize()
     f.close()
-    f = bsf.BoxSplineFilter(16, 16, 1, "symmetric", frac_bits=8, step_rule=bsf.BSF_STEP_SAMPLED,
-                            directions=bsf.BSF_DIRS_PAIR)
+    f = bsf.BoxSplineFilter(16, 16, 1, "symmetric", precision=bsf.BSF_FIX128, frac_bits=8,
+                            step_rule=bsf.BSF_STEP_D2, directions=bsf.BSF_DIRS_PAIR)
     with pytest.raises(bsf.BsfError):
         f.filter(img, cov)
     f.close()
+
+
+@pytest.mark.parametrize("directions,boundary,precision,out64", [(1, 2, 1, False), (1, 0, 2, True),
+                                                                 (2, 2, 1, False), (2, 1, 2, False)])
+def test_sampled_second_set_and_pair_bit_exact(directions, boundary, precision, out64):
+    # Algorithm 3 as printed (beta'_a through the running sums of the second
+    # set interpolated by beta'_b) and Algorithm 2 with both sampled box
+    # splines, against the exact-rational definitions
+    H, W = 15, 18
+    img = wl.blob_image(H, W, seed=directions + boundary, n_blobs=4, sigma_range=(2, 6)).astype(np.float32)
+    rng = np.random.default_rng(30 + directions)
+    phi = rng.uniform(0, np.pi, (H, W))
+    e = rng.uniform(1.0, 4.0, (H, W))
+    s2 = rng.uniform(0.8, 3.0, (H, W))
+    c, sn = np.cos(phi), np.sin(phi)
+    k = 2 * s2 / (1 + e)
+    cov = np.stack([k * (e * c * c + sn * sn), k * (e - 1) * sn * c, k * (e * sn * sn + c * c)]).astype(np.float32)
+    q = 8 if precision == 1 else 30
+    odt = np.float64 if out64 else np.float32
+    got, st, info = _run(img, cov, boundary, q, precision, out64, directions=directions)
+    assert st == 0
+    if directions == 1:
+        ref = sp.filter_sampled_k(img, cov, boundary, q, out_dtype=odt)
+    else:
+        ref = sp.filter_sampled_pair(img, cov, boundary, q, out_dtype=odt)
+    np.testing.assert_array_equal(got, ref)

@@ -41,3 +41,21 @@ def test_generated_weights_equal_the_exact_box_spline():
                 got = eval(W[tri][(i1 + 1) * 3 + (i2 + 2)], {}, env)  # noqa: S307 (integer expression)
                 want = sp.beta(Fr(-i1) + Fr(U, 1024), Fr(-i2) + Fr(V, 1024), (Fr(1),) * 4) * (1 << sp.WEIGHT_BITS)
                 assert got == want, (U, V, i1, i2)
+
+
+KNIGHT_HEADER = os.path.join(os.path.dirname(__file__), "..", "paper_1109_5114_gb300", "csrc",
+                             "bsf_knight_box_spline.h")
+
+
+def test_second_set_table_equals_the_exact_box_spline():
+    text = open(KNIGHT_HEADER).read()
+    body = text[text.index("{") + 1:text.rindex("}")]
+    table = [int(v) for v in body.replace("\n", " ").split(",") if v.strip()]
+    assert len(table) == 193 * 194 // 2
+    rng = random.Random(1)
+    for _ in range(300):
+        a1, a2 = rng.randrange(-200, 201), rng.randrange(-200, 201)   # centred, units of 2^-6
+        a, b = max(abs(a1), abs(a2)), min(abs(a1), abs(a2))
+        got = table[a * (a + 1) // 2 + b] if a <= 192 else 0
+        want = sp.beta_k(Fr(a1, 64), 3 + Fr(a2, 64), (Fr(1),) * 4) * sp.WEIGHT_DEN_K
+        assert got == want, (a1, a2)
