@@ -838,7 +838,8 @@ def run_single(args):
     """One filter configuration on its own (few launches, for profiling and
     for its own throughput): tiles4096 (8-bit 4096^2 blob image, sigma 1-3 px,
     rho 1-3, n = 2, automatic width, fused tiles), sampled2048 (the benchmark's
-    image and field, n = 1, the sampled continuous box spline), pair2048 (the
+    image and field, n = 1, the sampled continuous box spline), sampledsecond2048
+    (the same with the second direction set: Algorithm 3 as printed), pair2048 (the
     benchmark's image and field, n = 2, both direction sets switched by
     sector)."""
     import torch
@@ -865,6 +866,10 @@ def run_single(args):
             f = bsf.BoxSplineFilter(h, w, 1, "symmetric", frac_bits=-1, value_bound=vmax,
                                     step_rule=bsf.BSF_STEP_SAMPLED)
             desc = WORKLOAD.replace("n=2 (81 taps)", "n=1") + "; sampled continuous box spline"
+        elif args.workload == "sampledsecond2048":
+            f = bsf.BoxSplineFilter(h, w, 1, "symmetric", frac_bits=-1, value_bound=vmax,
+                                    step_rule=bsf.BSF_STEP_SAMPLED, directions=bsf.BSF_DIRS_SECOND)
+            desc = WORKLOAD.replace("n=2 (81 taps)", "n=1") + "; the second set's sampled box spline (Algorithm 3)"
         else:
             f = bsf.BoxSplineFilter(h, w, 2, "symmetric", frac_bits=-1, value_bound=vmax,
                                     directions=bsf.BSF_DIRS_PAIR)
@@ -922,10 +927,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="spacevariant2048",
                     choices=["spacevariant2048", "batch64", "diff8x1024", "tiles4096", "sampled2048",
-                             "pair2048"],
+                             "sampledsecond2048", "pair2048"],
                     help="spacevariant2048: the benchmark line; batch64: the batched form; "
                          "diff8x1024: continuous steps with the parameter gradient; "
-                         "tiles4096, sampled2048, pair2048: one configuration each (run_single)")
+                         "tiles4096, sampled2048, sampledsecond2048, pair2048: one configuration each "
+                         "(run_single)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "bsf":
         args.warmup = 3
@@ -935,7 +941,7 @@ def main():
         line = run_batch(args)
     elif args.workload == "diff8x1024":
         line = run_diff(args)
-    elif args.workload in ("tiles4096", "sampled2048", "pair2048"):
+    elif args.workload in ("tiles4096", "sampled2048", "sampledsecond2048", "pair2048"):
         line = run_single(args)
     else:
         line = run_gpu(args)

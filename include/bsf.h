@@ -107,13 +107,18 @@ extern "C" {
 #define BSF_STEP_D2        2  /* continuous steps with interpolated taps (n = 1, 2; fixed
                                  point only): see bsf_filter_jacobian */
 #define BSF_STEP_SAMPLED   3  /* the paper's continuous box spline, sampled (Section 2.3, eq.
-                                 "interpolation"): order n = 1 only, Cartesian set, BSF_FIX64 /
-                                 BSF_FIX128, forward only.  lambda_k = a_k/|d_k| quantised to
-                                 2^-9, Lq_k = max(1, RNE(512 lambda_k)); the running sums are
+                                 "interpolation"): order n = 1 only, BSF_FIX64 / BSF_FIX128,
+                                 forward only.  Cartesian set: lambda_k = a_k/|d_k| quantised
+                                 to 2^-9, Lq_k = max(1, RNE(512 lambda_k)); the running sums are
                                  interpolated at the 16 continuous taps by the grid box spline
                                  of unit steps (nine samples per tap, integer weights over
                                  2^23), so out(p) = sum_m f(m) beta_a(p + tau - m) with
-                                 out = RN(RN(acc) 2^(13-q)) / RN(prod Lq) */
+                                 out = RN(RN(acc) 2^(13-q)) / RN(prod Lq).  BSF_DIRS_SECOND
+                                 (Algorithm 3 as printed): lambda_k = a_k/sqrt(5) quantised to
+                                 2^-5, Lq_k = max(1, RNE(32 lambda_k)), beta'_b interpolation
+                                 (6 x 6 samples per tap, integer weights over 491520),
+                                 out = RN(RN(acc) 2^(5-q)) / RN(15 prod Lq).  BSF_DIRS_PAIR:
+                                 either, per pixel by sector */
 
 /* direction sets (BSF_OPT_DIRECTIONS), Section 2.3 of the paper */
 #define BSF_DIRS_CARTESIAN 0  /* beta_a: d1 = (1,0), d2 = (1,1), d3 = (0,1), d4 = (-1,1) (default) */
