@@ -475,6 +475,32 @@ def run_gpu(args):
     assert np.array_equal(h_out.numpy(), d_out.cpu().numpy())  # same result both ways
     f.close()
 
+    # the host link's own floor for the same bytes: the uploads and the
+    # download as plain copies (one stream each way, overlapped), no filter
+    # work; the e2e figure is compared with it
+    d_img_l = torch.empty(h_img.shape, dtype=h_img.dtype, device="cuda")
+    d_cov_l = torch.empty(h_cov.shape, dtype=h_cov.dtype, device="cuda")
+    h_out_l = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def link_step():
+        with torch.cuda.stream(up):
+            d_img_l.copy_(h_img, non_blocking=True)
+            d_cov_l.copy_(h_cov, non_blocking=True)
+        with torch.cuda.stream(down):
+            h_out_l.copy_(d_out, non_blocking=True)
+        torch.cuda.synchronize()
+
+    for _ in range(2):
+        link_step()
+    link_ms = 0.0
+    for _ in range(5):
+        t0 = time.perf_counter()
+        link_step()
+        link_ms += (time.perf_counter() - t0) * 1e3
+    link_ms /= 5
+    del d_img_l, d_cov_l
+
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -537,7 +563,10 @@ def run_gpu(args):
                    "R": info.R, "l2": "flushed before every timed step (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms / args.steps, 5),
+                "link_floor_ms": round(link_ms, 5),
+                "link_floor_note": "the same uploads and download as plain overlapped copies, no work",
+                "frac_of_link_floor": round(link_ms / (e2e_ms / args.steps), 3)},
         "gpu_launches": launches,
         "fp64_form": fp64_form,
         "algorithm1": algorithm1,
