@@ -163,7 +163,7 @@ extern "C" {
 #define BSF_OPT_PLAN_UNION   6  /* 1 = each bsf_plan widens the plan instead of replacing it:
                                    R and the mass bound become the largest over every plan
                                    since the option was set (one context for many fields) */
-#define BSF_OPT_HOST_BANDS   7  /* row bands of bsf_filter_host's overlapped transfers, 1..32 (default 4) */
+#define BSF_OPT_HOST_BANDS   7  /* row bands of bsf_filter_host's overlapped transfers, 1..32 (default 8) */
 #define BSF_OPT_DIRECTIONS   8  /* direction set of the integer-step filter (BSF_DIRS_*); changing
                                    it drops the plan (the next call plans again) */
 #define BSF_OPT_TILES        9  /* 1 (default): bsf_filter / bsf_filter_rows with an image run as one
@@ -281,11 +281,11 @@ int bsf_filter(bsf_t h, const void* img, int dtype, long long ld,
 
 /* Whole forward filter on HOST buffers, overlapping the transfers with the
  * work: the image is uploaded first and pre-integrated as soon as it has
- * arrived, while the covariance planes follow in row bands (four by default,
- * BSF_OPT_HOST_BANDS) on a second
- * stream; the stencil runs band by band as each band's field arrives, and
- * each finished band of the output goes back on a third stream while the
- * next is computed.  img: host [H][ld] of dtype; cov: host [3][H][W] float32
+ * arrived, while the covariance planes follow in row bands (eight by default,
+ * BSF_OPT_HOST_BANDS; the last band a quarter of the others' height, so that
+ * little work remains after the last upload) on a second stream; the stencil
+ * runs band by band as each band's field arrives, and each finished band of
+ * the output goes back on a third stream while the next is computed.  img: host [H][ld] of dtype; cov: host [3][H][W] float32
  * of cov_kind; out: host [H][ldo] of out_dtype.  Use page-locked host memory
  * (cudaHostAlloc / torch pin_memory) for the copies to overlap; pageable
  * memory works but serialises them.  The library keeps device copies of the

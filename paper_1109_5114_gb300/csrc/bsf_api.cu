@@ -64,7 +64,7 @@ struct bsf_ctx {
   // host-buffer entry (bsf_filter_host): device staging copies of the inputs
   // and the output, one stream per copy direction, and the band events
   static constexpr int kHostBands = 32;  // most bands of bsf_filter_host
-  int host_bands = 4;
+  int host_bands = 8;
   void* hs_img = nullptr;
   void* hs_cov = nullptr;
   void* hs_out = nullptr;
@@ -740,9 +740,12 @@ static int enqueue_host_filter(bsf_t h, const void* img, int dtype, long long ld
   cudaEvent_t ev_img = h->hev[0];
   cudaEvent_t* ev_cov = h->hev + 1;
   cudaEvent_t* ev_out = h->hev + 1 + bsf_ctx::kHostBands;
+  // the last band is a quarter of the others' height: only its stencil and
+  // its download remain after the last upload
+  const long long den = 4LL * (K - 1) + 1;
   auto band = [&](int k, int& y0, int& rows) {
-    y0 = (int)((long long)H * k / K);
-    rows = (int)((long long)H * (k + 1) / K) - y0;
+    y0 = (int)(H * 4LL * k / den);
+    rows = (k == K - 1 ? H : (int)(H * 4LL * (k + 1) / den)) - y0;
   };
   float* dcov = static_cast<float*>(h->hs_cov);
   int rc;

@@ -276,6 +276,26 @@ def test_row_bands_equal_whole_image_bit_exact(n, boundary):
     torch.testing.assert_close(torch.cat(parts, 0), whole, rtol=0, atol=0)
 
 
+@pytest.mark.parametrize("bands", [1, 2, 5, 32])
+def test_host_buffer_entry_band_counts(bands):
+    # the host entry's row bands (the last one shorter than the others) cover
+    # every row exactly once, for any band count up to the row count
+    import torch
+    from paper_1109_5114_gb300 import bsf
+    H, W = 37, 90
+    img = wl.blob_image(H, W, seed=5, n_blobs=8).astype(np.float32)
+    cov = _cov(H, W, seed=4)
+    f_dev = bsf.BoxSplineFilter(H, W, 2, "symmetric", precision=1, frac_bits=6)
+    ref = f_dev.filter(torch.from_numpy(img).cuda(), torch.from_numpy(cov).cuda()).cpu().numpy()
+    f_host = bsf.BoxSplineFilter(H, W, 2, "symmetric", precision=1, frac_bits=6)
+    f_host.set_option(bsf.BSF_OPT_HOST_BANDS, bands)
+    out = torch.full((H, W), float("nan"), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        f_host.filter_host(torch.from_numpy(img).pin_memory(), torch.from_numpy(cov).pin_memory(), out)
+        assert f_host.status() == 0
+        np.testing.assert_array_equal(out.numpy(), ref)
+
+
 @pytest.mark.parametrize("dtype,out64,pinned,rule,n", [(np.float32, False, True, 0, 2), (np.uint8, True, False, 0, 3),
                                                        (np.float64, False, True, 2, 2), (np.float32, False, False, 2, 1)])
 def test_host_buffer_entry_equals_device_filter(dtype, out64, pinned, rule, n):
