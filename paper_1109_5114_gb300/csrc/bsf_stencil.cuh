@@ -25,14 +25,47 @@
 
 namespace {
 
+// Order 2 in exact modular arithmetic, summed by coefficient: the tap
+// t = (t1..t4) in {0,1,2}^4 carries prod_k (1, -2, 1)[t_k] = (-2)^j, j the
+// number of t_k equal to 1, so the 81 taps go into five sums G_j (16, 32,
+// 24, 8 and 1 taps) and acc = G0 - 2 (G1 - 2 (G2 - 2 (G3 - 2 G4))): 80 + 8
+// additions against the nested form's 120, with the same result modulo 2^b.
+template <typename T, bool SH>
+__device__ __forceinline__ T comb2_by_coefficient(const T* __restrict__ S, int idx, const int* s) {
+  T G[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) G[j] = 0;
+#pragma unroll
+  for (int t4 = 0; t4 < 3; ++t4)
+#pragma unroll
+    for (int t3 = 0; t3 < 3; ++t3)
+#pragma unroll
+      for (int t2 = 0; t2 < 3; ++t2)
+#pragma unroll
+        for (int t1 = 0; t1 < 3; ++t1) {
+          const int i = idx - t1 * s[0] - t2 * s[1] - t3 * s[2] - t4 * s[3];
+          T v;
+          if constexpr (SH) v = S[i];
+          else v = bsf_load(S + i);
+          G[(t1 == 1) + (t2 == 1) + (t3 == 1) + (t4 == 1)] += v;
+        }
+  T a = G[4];
+#pragma unroll
+  for (int j = 3; j >= 0; --j) a = G[j] - (a + a);
+  return a;
+}
+
 // Nested order-n differences.  Taps are addressed by 32-bit element indices
 // into S (the padded domain holds fewer than 2^31 elements); level LVL applies
 // the difference along direction LVL-1 (stride s[LVL-1] elements) to level
-// LVL-1, and level 0 loads one element.
+// LVL-1, and level 0 loads one element.  Order 2 on the integer element
+// types takes the grouped form above.
 // SH: S lies in shared memory (plain loads) instead of global memory.
 template <typename T, int NF, int LVL, bool SH = false>
 __device__ __forceinline__ T comb(const T* __restrict__ S, int idx, const int* s) {
-  if constexpr (LVL == 0) {
+  if constexpr (LVL == 4 && NF == 2 && IsFixed<T>::value) {
+    return comb2_by_coefficient<T, SH>(S, idx, s);
+  } else if constexpr (LVL == 0) {
     if constexpr (SH) return S[idx];
     else return bsf_load(S + idx);
   } else {
