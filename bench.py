@@ -558,10 +558,8 @@ def run_gpu(args):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(total_ms / args.steps, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "H": H, "W": W, "n": ORDER, "N": 4,
-                   "boundary": "symmetric", "precision": "fix64", "frac_bits": info.frac_bits,
-                   "R": info.R, "l2": "flushed before every timed step (256 MB write)",
-                   "parallelism": f"replicas x{world}"},
+        "config": workload_config(info.frac_bits, info.R, world,
+                                  "flushed before every timed step (256 MB write)"),
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms / args.steps, 5),
                 "link_floor_ms": round(link_ms, 5),
@@ -624,6 +622,17 @@ def cpu_baseline(img, cov, R, q, rows: int = 512):
                       f"oracle.modular (numpy, one thread), {dt:.1f} s"}
 
 
+# the fraction bits the GPU arm's automatic rule picks on this workload (its
+# value bound and the steps of its field); the reference arm quantises alike
+REF_FRAC_BITS = 24
+
+
+def workload_config(frac_bits: int, R: int, world: int, l2: str) -> dict:
+    return {"workload": WORKLOAD, "H": H, "W": W, "n": ORDER, "N": 4, "boundary": "symmetric",
+            "precision": "fix64", "frac_bits": frac_bits, "R": R, "l2": l2,
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -632,7 +641,7 @@ def run_reference(args):
     from oracle import modular, params
     L, _ = params.integer_steps(cov[0], cov[1], cov[2], ORDER)
     R = max(int(params.reach(L, ORDER).max()), 3 * ORDER)
-    q = 22
+    q = REF_FRAC_BITS
     rows = args.ref_rows
     band_img = np.ascontiguousarray(img[:rows])
     band_cov = np.ascontiguousarray(cov[:, :rows])
@@ -649,7 +658,7 @@ def run_reference(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "H": H, "W": W, "n": ORDER, "sample_rows": rows},
+        "config": workload_config(q, R, 1, "not applicable (host cores)"),
         "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
