@@ -865,9 +865,9 @@ def run_diff(args):
                 "ms_per_step": round(fw_ms / args.steps, 4),
                 "phases_ms": {k: round(ms / max(c, 1), 5) for k, (ms, c) in prof_fw.items() if c}},
         "phases_ms": {k: round(v[0], 5) for k, v in per_phase.items()},
-        # per image: rows, 3 x (agg + apply), stencil, vjp; backward: absmax,
-        # scatter, 3 x (agg + apply), suffix rows, 2 folds
-        "gpu_launches": 8 * ((1 + 3 * 2 + 1 + 1) + (1 + 1 + 3 * 2 + 1 + 2)),
+        # over the timed steps, per image: rows, 3 x (agg + apply), stencil,
+        # vjp; backward: absmax, scatter, 3 x (agg + apply), suffix rows, 2 folds
+        "gpu_launches": args.steps * 8 * ((1 + 3 * 2 + 1 + 1) + (1 + 1 + 3 * 2 + 1 + 2)),
         "loss": loss,
         "clocks": clocks,
     }
