@@ -226,6 +226,31 @@ def test_scan_modes_agree_bit_exact(prec):
     np.testing.assert_array_equal(outs[0][1], outs[1][1])
 
 
+@pytest.mark.parametrize("prec,short", [(1, 0), (1, 1), (2, 0)])
+def test_scan_modes_agree_on_tall_images(prec, short):
+    # many chunks per line (46 of 32 rows, 92 of 16): long look-back walks
+    # before an inclusive state, against the three-phase scan
+    torch = pytest.importorskip("torch")
+    from paper_1109_5114_gb300 import bsf
+    H, W, n = 1400, 70, 2
+    img = wl.random_integer_image(H, W, seed=21, lo=-500, hi=500).astype(np.float32)
+    cov = _cov(H, W, seed=22, smax=6.0)
+    outs = []
+    for mode in (bsf.BSF_SCAN_LOOKBACK, bsf.BSF_SCAN_THREE_PHASE):
+        f = bsf.BoxSplineFilter(H, W, n, "symmetric", precision=prec, frac_bits=4)
+        f.set_option(bsf.BSF_OPT_TILES, 0)
+        f.set_option(bsf.BSF_OPT_SCAN_MODE, mode)
+        f.set_option(bsf.BSF_OPT_SCAN_SHORT_TILES, short)
+        out = f.filter(torch.from_numpy(img).cuda(), torch.from_numpy(cov).cuda())
+        raw, _ = f.preintegrated()
+        torch.cuda.synchronize()
+        assert f.status() == 0
+        outs.append((out.cpu().numpy(), raw.cpu().numpy()))
+        f.close()
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+
+
 def test_bounded_wait_times_out_and_context_stays_usable():
     # failure injection: the first chunk of every look-back scan never marks
     # its state ready, so every wait on it runs out after the wait limit; the
