@@ -48,3 +48,17 @@ def test_product_path_has_no_oracle_import():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
+
+
+def test_binding_refuses_to_load_without_the_library(tmp_path):
+    # no fallback: a copy of the binding whose package has no built library
+    # fails at import, before any call could run anywhere else
+    import importlib.util
+    import shutil
+    pkg = tmp_path / "pkg"
+    pkg.mkdir()
+    shutil.copy(os.path.join(ROOT, "paper_1109_5114_gb300", "bsf.py"), pkg / "bsf.py")
+    spec = importlib.util.spec_from_file_location("bsf_without_library", pkg / "bsf.py")
+    mod = importlib.util.module_from_spec(spec)
+    with pytest.raises(ImportError, match="not built"):
+        spec.loader.exec_module(mod)
