@@ -599,14 +599,20 @@ KERNEL_SOURCES = {
 
 
 def kernel_revision(kernel: str = "stencil") -> str:
-    """Hash of the sources that build one kernel (and the build flags), to
+    """Hash of the code that builds one kernel (its sources with their
+    comments and spacing removed, and the build script with its flags), to
     tell whether stored ncu traffic still applies to it."""
     import hashlib
+    import re
     hsh = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_1109_5114_gb300", "csrc")
-    for fn in KERNEL_SOURCES[kernel] + ["../build.py", "../../include/bsf.h"]:
-        with open(os.path.join(cs, fn), "rb") as fh:
-            hsh.update(os.path.basename(fn).encode() + fh.read())
+    for fn in KERNEL_SOURCES[kernel] + ["../../include/bsf.h"]:
+        with open(os.path.join(cs, fn)) as fh:
+            code = re.sub(r"/\*.*?\*/", " ", fh.read(), flags=re.S)
+        code = " ".join(re.sub(r"//[^\n]*", " ", code).split())
+        hsh.update(os.path.basename(fn).encode() + code.encode())
+    with open(os.path.join(cs, "..", "build.py"), "rb") as fh:
+        hsh.update(b"build.py" + fh.read())
     return hsh.hexdigest()[:16]
 
 

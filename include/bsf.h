@@ -139,9 +139,9 @@ extern "C" {
 /* phases timed by bsf_set_profiling / bsf_read_profile */
 #define BSF_PHASE_STEPS    0  /* per-pixel step solve */
 #define BSF_PHASE_ROWS     1  /* extension + quantisation + running sums along d1 */
-#define BSF_PHASE_D3       2  /* running sums along d3 (three kernels) */
-#define BSF_PHASE_D2       3  /* running sums along d2 (three kernels) */
-#define BSF_PHASE_D4       4  /* running sums along d4 (three kernels) */
+#define BSF_PHASE_D3       2  /* running sums along d3 (two kernels; one with look-back) */
+#define BSF_PHASE_D2       3  /* running sums along d2 (two kernels; one with look-back) */
+#define BSF_PHASE_D4       4  /* running sums along d4 (two kernels; one with look-back) */
 #define BSF_PHASE_STENCIL  5  /* finite differences + final rounding */
 #define BSF_PHASE_BWD_SCATTER 6  /* backward: weight quantisation + tap scatter */
 #define BSF_PHASE_BWD_SCANS   7  /* backward: suffix sums along d4, d2, d3, d1 */
@@ -178,7 +178,7 @@ extern "C" {
                                    bsf_preintegrate); same results as the global passes in fixed
                                    point.  0: always the global passes */
 #define BSF_SCAN_LOOKBACK     0 /* single pass, decoupled look-back between blocks */
-#define BSF_SCAN_THREE_PHASE  1 /* reduce / carry / rescan; no block waits on another
+#define BSF_SCAN_THREE_PHASE  1 /* reduce, then rescan with the carries folded in; no block waits on another
                                    (measured faster on GB300 for 2048^2, n = 2) */
 
 /* device status flags reported through bsf_info_t.flags */
@@ -194,8 +194,8 @@ typedef struct {
   int R;               /* padding reach; -1 until planned */
   int Hp, Wp;          /* padded domain (H + 2R) x (W + 2R) */
   long long pitch;     /* elements per row of S */
-  int elem_bytes;      /* bytes per element of S (8 or 16) */
-  int precision;       /* BSF_FIX64 / BSF_FIX128 */
+  int elem_bytes;      /* bytes per element of S (4, 8 or 16) */
+  int precision;       /* element type of S in use: BSF_FIX32 / _FIX64 / _FIX128 / _F64ACC / _F32KAHAN */
   int frac_bits;       /* q in use (-1 = not yet resolved) */
   int step_rule;       /* BSF_STEP_* */
   int max_reach;       /* largest tap reach of the last plan (-1 before any) */
