@@ -22,6 +22,9 @@ continuous  the continuous-step filter (interpolated taps, Section 2.3) and
 two_pass  Algorithm 1: an isotropic pass, then the space-variant residual pass.
 sampled   the sampled continuous box spline: the filter of the paper's running
           sums interpolated by the grid box spline (eq. "interpolation").
+config    the padding R, the automatic fraction bits q and element width:
+          the configuration rules a run fixes before any arithmetic, so the
+          tests check the library's choice instead of taking it.
 knight    the second box spline beta'_a on the directions (2,1), (1,2), (-1,2),
           (-2,1) (Algorithm 3, Table 1) and the pair switched by sector
           (Algorithm 2).
@@ -29,4 +32,4 @@ knight    the second box spline beta'_a on the directions (2,1), (1,2), (-1,2),
 Parity status of each function is stated in its docstring; "parity unpinned"
 marks a function with no independent pin.
 """
-from . import params, kernels, modular, gaussian, backward, continuous, two_pass, knight, sampled  # noqa: F401
+from . import params, kernels, modular, gaussian, backward, continuous, two_pass, knight, sampled, config  # noqa: F401
