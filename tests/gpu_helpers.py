@@ -1,9 +1,20 @@
 """Helpers shared by the GPU parity tests: run the CUDA path through the C ABI
-and the oracle on the same seeded inputs."""
+and the oracle on the same seeded inputs.
+
+The configuration of a run (the padding R, the automatic fraction bits q and
+element width) is computed by the oracle (oracle.config) and checked against
+the library's choice before any output is compared; nothing the CUDA path
+chose is fed into the oracle."""
 import numpy as np
 
-from oracle import kernels, modular, params
+from oracle import config, kernels, modular, params
 from oracle.rounding import quantize
+
+
+# step rules, direction sets and element widths of the C ABI's codes
+RULES = {0: "corrected", 1: "paper", 2: "d2", 3: "sampled"}
+DIRS = {0: "cartesian", 1: "second", 2: "pair"}
+WIDTHS = {0: None, 1: 64, 2: 128, 5: 32}
 
 
 def torch_mod():
@@ -29,7 +40,17 @@ def run_gpu(img, cov, n, boundary, q, precision=1, out_dtype=np.float32, max_rea
     torch.cuda.synchronize()
     st = f.status()
     info = f.info()
-    res = dict(out=out.cpu().numpy(), R=info.R, q=info.frac_bits, info=info, status=st)
+    # R and q by the oracle's rules, checked against the library's choice
+    rule = RULES[step_rule]
+    dirs = DIRS[directions]
+    R = oracle_R(cov, n, rule, dirs, gpu=info.R, max_reach=max_reach)
+    if precision in (3, 4):       # floating-point running sums hold the values themselves
+        q_or = 0
+        assert info.frac_bits == 0
+    else:
+        bits, q_or = oracle_q(img, cov, n, q, WIDTHS[precision], rule, dirs, gpu=info.frac_bits)
+        assert info.elem_bytes * 8 == bits, (info.elem_bytes, bits)
+    res = dict(out=out.cpu().numpy(), R=R, q=q_or, info=info, status=st)
     if want_steps:
         L = f.steps().cpu().numpy().astype(np.int64) & 0xFFFF
         res["L"] = L & 0x7FFF if directions == 2 else L
@@ -53,7 +74,47 @@ def run_gpu(img, cov, n, boundary, q, precision=1, out_dtype=np.float32, max_rea
     return res
 
 
-def run_oracle(img, cov, n, boundary, q, R, bits=64, out_dtype=np.float32, rule="corrected"):
+def oracle_R(cov, n, rule="corrected", dirs="cartesian", kind=0, gpu=None, max_reach=-1):
+    """The padding R by the oracle's rule (or the test's own explicit bound);
+    with gpu given, asserts that the library chose the same."""
+    R = max_reach if max_reach >= 0 else config.padding(cov, n, rule, dirs, kind)
+    if gpu is not None:
+        got = gpu["R"] if isinstance(gpu, dict) else gpu
+        assert got == R, f"library padding R = {got}, oracle rule {R}"
+    return R
+
+
+def oracle_R_two_pass(cov, n, frac=0.5, kind=0, gpu=None):
+    """Algorithm 1's padding: the oracle's R over both fields of the split
+    (the isotropic sigma^2 I and the residual C - sigma^2 I)."""
+    from oracle import continuous, two_pass
+    C = np.stack(continuous.covariance_planes(cov, kind)).astype(np.float32)
+    iso, res = two_pass.split_field(C, two_pass.sigma2_global(C, frac))
+    R = max(config.padding(iso, n), config.padding(res, n))
+    if gpu is not None:
+        assert gpu == R, f"library padding R = {gpu}, oracle rule {R}"
+    return R
+
+
+def oracle_q(img, cov, n, frac_bits, bits=64, rule="corrected", dirs="cartesian", kind=0, gpu=None,
+             vmax=None):
+    """(bits, q) by the oracle's rule (bits None: automatic width); with gpu
+    given, asserts that the library chose the same q."""
+    mass = config.mass_bound(cov, n, rule, dirs, kind)
+    b, q = config.resolve(img, mass, frac_bits, bits, continuous=(rule == "d2"), vmax=vmax,
+                          wide_only=rule in ("d2", "sampled"))
+    if gpu is not None:
+        got = gpu["q"] if isinstance(gpu, dict) else gpu
+        assert got == q, f"library q = {got}, oracle rule {q}"
+    return b, q
+
+
+def run_oracle(img, cov, n, boundary, q, R=None, bits=64, out_dtype=np.float32, rule="corrected", gpu=None,
+               max_reach=-1):
+    """The modular oracle with the oracle's own R (or the test's explicit
+    max_reach); with gpu given, the library's R must equal it."""
+    if R is None:
+        R = oracle_R(cov, n, rule, gpu=gpu, max_reach=max_reach)
     return modular.filter_modular(img, cov, n, boundary, q=q, bits=bits, out_dtype=out_dtype, R=R,
                                   rule=rule, return_all=True)
 

@@ -6,6 +6,7 @@ import pytest
 
 import workloads as wl
 from oracle import backward, params
+from tests.gpu_helpers import oracle_R
 
 pytestmark = pytest.mark.gpu
 
@@ -44,6 +45,7 @@ def test_backward_bit_exact_vs_oracle_adjoint(n, boundary):
     gout = rng.normal(size=(H, W)).astype(np.float32)
     g, gc, st, R = _gpu_backward(img, cov, gout, n, boundary)
     assert st == 0
+    R = oracle_R(cov, n, gpu=R)
     L, _ = params.integer_steps(cov[0], cov[1], cov[2], n)
     qg = backward.grad_frac_bits(np.abs(gout).max())
     ref = backward.adjoint_modular(gout, L, n, boundary, qg, R)

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import workloads as wl
-from oracle import modular, params
+from oracle import config, modular, params
 
 pytestmark = pytest.mark.gpu
 
@@ -35,7 +35,10 @@ def test_batch_bit_exact_all_modes(n):
     d_outs = [torch.zeros(a.shape, dtype=torch.float32, device="cuda") for a in imgs]
     torch.cuda.synchronize()
     info = bf.plan(d_imgs, d_covs, d_outs, autotune=True)
-    q = info.frac_bits
+    # one q for the batch: the automatic rule at the largest mass of any image
+    mass = max(config.mass_bound(c, n) for c in covs)
+    q = max(config.auto_frac_bits(vmax, mass, 64), 0)
+    assert info.frac_bits == q
     refs = []
     for a, c in zip(imgs, covs):
         L, _ = params.integer_steps(c[0], c[1], c[2], n)

@@ -19,6 +19,7 @@ import pytest
 import workloads as wl
 from oracle import continuous as cn
 from oracle import kernels
+from tests.gpu_helpers import oracle_R, oracle_q
 
 pytestmark = pytest.mark.gpu
 
@@ -62,8 +63,11 @@ def _run(img, planes, n, boundary, q, precision, kind, out_dtype=np.float32, jac
     torch.cuda.synchronize()
     st = f.status()
     info = f.info()
-    return dict(out=out.cpu().numpy(), jac=None if J is None else J.cpu().numpy(), R=info.R,
-                q=info.frac_bits, status=st, filt=f, img=ti, cov=tc)
+    # R and q by the oracle's rules, checked against the library's choice
+    R = oracle_R(planes, n, "d2", kind=kind, gpu=info.R, max_reach=max_reach)
+    bits, q_or = oracle_q(img, planes, n, q, 64 if precision == 1 else 128, "d2", kind=kind, gpu=info.frac_bits)
+    return dict(out=out.cpu().numpy(), jac=None if J is None else J.cpu().numpy(), R=R,
+                q=q_or, status=st, filt=f, img=ti, cov=tc)
 
 
 def _sample(H, W, k, seed):
@@ -268,7 +272,7 @@ def test_image_gradient_bit_exact(n, boundary, kind):
     gimg, _ = f.backward(torch.from_numpy(gout).cuda(), tc, want_gimg=True, want_gcov=False)
     torch.cuda.synchronize()
     assert f.status() == 0
-    R = f.info().R
+    R = oracle_R(planes, n, "d2", kind=kind, gpu=f.info().R)
     qg = cn.grad_frac_bits_d2(float(np.abs(gout).max()))
     pix = [(y, x) for y in range(H) for x in range(W)]
     recs = cn.filter_d2_direct(np.zeros((H, W), dtype=np.int64), planes, n, boundary, pix, kind=kind, R=R)
@@ -305,3 +309,36 @@ def test_autograd_image_and_parameter_gradients():
     lhs = float((gout.double() * Ad.double()).sum())
     rhs = float((gimg.double() * d.double()).sum())
     assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), 1e-3)
+
+
+def test_memory_budget_recompute_route_equals_stored_route():
+    # above its memory budget the differentiable forward keeps only its
+    # inputs; the backward recomputes the running sums and the Jacobian
+    # product.  Both routes give the same gradients bit for bit, even when
+    # another image went through the filter between forward and backward.
+    import torch
+    from paper_1109_5114_gb300 import bsf
+    H, W = 34, 47
+    img = torch.from_numpy(wl.blob_image(H, W, seed=6, n_blobs=9, sigma_range=(2.0, 6.0))).cuda()
+    other = torch.from_numpy(wl.blob_image(H, W, seed=7, n_blobs=5, sigma_range=(2.0, 6.0))).cuda()
+    planes = torch.from_numpy(_fields(H, W, seed=19, kind=1)).cuda()
+    target = torch.from_numpy(wl.uniform_image(H, W, seed=9, lo=0, hi=1).astype(np.float32)).cuda()
+    grads = []
+    for budget in (None, 0):
+        f = bsf.BoxSplineFilter(H, W, 2, "symmetric", precision=bsf.BSF_FIX128, frac_bits=-1, step_rule=2,
+                                cov_kind=1, memory_budget=budget)
+        assert f.stores_jacobian() == (budget is None)
+        f.plan(planes)
+        x = img.clone().requires_grad_(True)
+        p = planes.clone().requires_grad_(True)
+        out = bsf.box_spline_filter(x, p, f)
+        assert len(out.grad_fn.saved_tensors) == (3 if budget is None else 2)
+        f.filter(other, planes)                 # replaces the held running sums
+        loss = 0.5 * ((out - target) ** 2).sum()
+        loss.backward()
+        torch.cuda.synchronize()
+        assert f.status() == 0
+        grads.append((out.detach().cpu().numpy(), x.grad.cpu().numpy(), p.grad.cpu().numpy()))
+        f.close()
+    for a, b in zip(grads[0], grads[1]):
+        np.testing.assert_array_equal(a, b)

@@ -8,7 +8,7 @@ import workloads as wl
 from oracle import knight as kn
 from oracle import modular, two_pass
 from oracle import sampled as sp
-from tests.gpu_helpers import run_gpu
+from tests.gpu_helpers import oracle_R_two_pass, run_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -54,7 +54,7 @@ def test_degenerate_shapes_sampled_and_two_pass(shape):
     np.testing.assert_array_equal(out, sp.filter_sampled(img, cov, 2, 12))
     f = bsf.BoxSplineFilter(H, W, 2, "replicate", frac_bits=16)
     out, s2 = f.filter_two_pass(torch.from_numpy(img).cuda(), torch.from_numpy(cov).cuda(), want_sigma2=True)
-    R = f.info().R
+    R = oracle_R_two_pass(cov, 2, gpu=f.info().R)
     assert f.status() == 0
     f.close()
     ref, s2_ref, _ = two_pass.algorithm1(img, cov, 2, 1, q=16, R=R)

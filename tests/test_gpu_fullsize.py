@@ -19,6 +19,7 @@ import pytest
 import workloads as wl
 from oracle import kernels, modular, params
 from oracle.rounding import finalize, quantize
+from tests.gpu_helpers import oracle_R, oracle_q
 
 pytestmark = pytest.mark.gpu
 
@@ -63,8 +64,8 @@ def test_tiny_256_float64_bit_exact():
     img = wl.uniform_image(H, W, seed=0)
     cov = wl.constant_cov_field(H, W, 16.0, 0.0, 16.0)
     out, st, info = _gpu(img, cov, 1, 40, 1, np.float64)
-    assert st == 0 and info.R == 13
-    ref = modular.filter_modular(img, cov, 1, 2, q=40, bits=64, out_dtype=np.float64, R=info.R)
+    assert st == 0 and info.R == 13 == oracle_R(cov, 1)
+    ref = modular.filter_modular(img, cov, 1, 2, q=40, bits=64, out_dtype=np.float64, R=13)
     np.testing.assert_array_equal(out, ref)
     L, _ = params.integer_steps(cov[0], cov[1], cov[2], 1)
     pix = _sample_pixels(H, W, 64, 1)
@@ -80,8 +81,9 @@ def test_spacevariant_2048_bit_exact_whole_image():
     vmax = float(np.abs(img).max())
     out, st, info = _gpu(img, cov, 2, -1, 1, np.float32, value_bound=vmax)
     assert st == 0
-    ref = modular.filter_modular(img, cov, 2, 2, q=info.frac_bits, bits=64, out_dtype=np.float32,
-                                 R=info.R)
+    R = oracle_R(cov, 2, gpu=info.R)
+    _, q = oracle_q(img, cov, 2, -1, 64, gpu=info.frac_bits, vmax=vmax)
+    ref = modular.filter_modular(img, cov, 2, 2, q=q, bits=64, out_dtype=np.float32, R=R)
     np.testing.assert_array_equal(out, ref)
     L, _ = params.integer_steps(cov[0], cov[1], cov[2], 2)
     pix = _sample_pixels(H, W, 24, 2)
@@ -138,17 +140,19 @@ def test_differentiation_workload_one_image_full_size():
     torch.cuda.synchronize()
     assert f.status() == 0
     info = f.info()
+    R = oracle_R(fl, 2, "d2", kind=1, gpu=info.R)
+    _, q = oracle_q(img, fl, 2, -1, 128, "d2", kind=1, gpu=info.frac_bits, vmax=float(np.abs(img).max()))
     out, J = out.cpu().numpy(), J.cpu().numpy()
     rng = np.random.default_rng(0)
     pix = sorted({(int(y), int(x)) for y, x in zip(rng.integers(0, side, 256), rng.integers(0, side, 256))}
                  | {(0, 0), (side - 1, side - 1), (0, side - 1), (side - 1, 0)})
-    rec = cn.filter_d2_modular(img, fl, 2, kernels.SYMMETRIC, info.frac_bits, bits=128, kind=1,
-                               R=info.R, pixels=pix)
+    rec = cn.filter_d2_modular(img, fl, 2, kernels.SYMMETRIC, q, bits=128, kind=1,
+                               R=R, pixels=pix)
     assert not any(r["far"] for r in rec.values())
-    ref = np.array([cn.output(rec[p], info.frac_bits) for p in pix], dtype=np.float32)
+    ref = np.array([cn.output(rec[p], q) for p in pix], dtype=np.float32)
     np.testing.assert_array_equal(np.array([out[p] for p in pix]), ref)
     refJ = np.array([cn.jacobian_planes(rec[p], fl[:, p[0], p[1]].astype(np.float64), 1, 2,
-                                        info.frac_bits) for p in pix])
+                                        q) for p in pix])
     gotJ = np.array([J[:, p[0], p[1]] for p in pix])
     for c in range(3):
         scale = np.abs(refJ[:, c]).max()

@@ -13,7 +13,7 @@ import pytest
 import workloads as wl
 from oracle import kernels, params
 from oracle.rounding import finalize, quantize
-from tests.gpu_helpers import oracle_S, oracle_steps, run_gpu, run_oracle
+from tests.gpu_helpers import oracle_R, oracle_q, oracle_S, oracle_steps, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -52,7 +52,7 @@ def test_running_sums_of_rows_longer_than_one_pass(n, prec, W):
     cov = _cov(H, W, seed=n, smax=1.5)
     g = run_gpu(img, cov, n, 2, q=3, precision=prec, want_S=True)
     bits = 64 if prec == 1 else 128
-    S = oracle_S(img, n, 2, 3, g["R"], bits)
+    S = oracle_S(img, n, 2, 3, oracle_R(cov, n, gpu=g), bits)
     if bits == 64:
         np.testing.assert_array_equal(g["S"], S)
     else:
@@ -67,7 +67,7 @@ def test_running_sums_bit_exact(n, boundary, prec):
     cov = _cov(H, W, seed=n)
     g = run_gpu(img, cov, n, boundary, q=5, precision=prec, want_S=True)
     bits = 64 if prec == 1 else 128
-    S = oracle_S(img, n, boundary, 5, g["R"], bits)
+    S = oracle_S(img, n, boundary, 5, oracle_R(cov, n, gpu=g), bits)
     if bits == 64:
         np.testing.assert_array_equal(g["S"], S)
     else:
@@ -88,7 +88,7 @@ def test_filter_bit_exact_vs_modular_oracle(n, boundary, dtype):
     for out_dtype in (np.float32, np.float64):
         g = run_gpu(img, cov, n, boundary, q=q, out_dtype=out_dtype)
         assert g["status"] == 0
-        o = run_oracle(img, cov, n, boundary, q, g["R"], out_dtype=out_dtype)
+        o = run_oracle(img, cov, n, boundary, q, out_dtype=out_dtype, gpu=g)
         np.testing.assert_array_equal(g["out"], o["out"])
 
 
@@ -100,7 +100,7 @@ def test_filter_bit_exact_128(n):
     for out_dtype in (np.float32, np.float64):
         g = run_gpu(img, cov, n, 2, q=70, precision=2, out_dtype=out_dtype)
         assert g["status"] == 0
-        o = run_oracle(img, cov, n, 2, 70, g["R"], bits=128, out_dtype=out_dtype)
+        o = run_oracle(img, cov, n, 2, 70, bits=128, out_dtype=out_dtype, gpu=g)
         np.testing.assert_array_equal(g["out"], o["out"])
 
 
@@ -109,8 +109,10 @@ def test_filter_equals_direct_definition():
     img = wl.random_integer_image(H, W, seed=4, lo=0, hi=255).astype(np.float32)
     cov = _cov(H, W, seed=5)
     g = run_gpu(img, cov, n, 2, q=8, out_dtype=np.float64, want_steps=True)
-    acc = kernels.correlate_exact(quantize(img, 8), g["L"], n, 2)
-    D = np.array([[kernels.kernel_mass(g["L"][:, y, x], n) for x in range(W)] for y in range(H)],
+    L, _ = oracle_steps(cov, n)           # the oracle's steps, not the library's
+    np.testing.assert_array_equal(g["L"], L)
+    acc = kernels.correlate_exact(quantize(img, 8), L, n, 2)
+    D = np.array([[kernels.kernel_mass(L[:, y, x], n) for x in range(W)] for y in range(H)],
                  dtype=np.int64)
     ref = finalize(acc.astype(object), D, 8, np.float64)
     np.testing.assert_array_equal(g["out"], ref)
@@ -123,7 +125,7 @@ def test_degenerate_shapes(shape):
     cov = wl.constant_cov_field(H, W, 2.0, 0.3, 1.0)
     for n in (1, 2, 3):
         g = run_gpu(img, cov, n, 2, q=12)
-        o = run_oracle(img, cov, n, 2, 12, g["R"])
+        o = run_oracle(img, cov, n, 2, 12, gpu=g)
         np.testing.assert_array_equal(g["out"], o["out"])
 
 
@@ -158,7 +160,8 @@ def test_out_of_reach_and_overflow_are_reported():
     cov = wl.constant_cov_field(H, W, 25.0, 0.0, 25.0)
     g = run_gpu(img, cov, 2, 2, q=10, max_reach=8)          # needs R ~ 40
     assert g["status"] == bsf.BSF_ERANGE
-    o = run_oracle(img, cov, 2, 2, 10, g["R"])
+    assert g["R"] == 8                                      # the caller's bound
+    o = run_oracle(img, cov, 2, 2, 10, R=8)
     np.testing.assert_array_equal(g["out"], o["out"])       # identity fallback, same as oracle
     g = run_gpu(img, cov, 2, 2, q=60)                       # 100 * 2^60 * mass >= 2^63
     assert g["status"] == bsf.BSF_EOVERFLOW
@@ -180,14 +183,15 @@ def test_automatic_q():
     img = wl.blob_image(H, W, seed=9, n_blobs=5).astype(np.float32)
     cov = _cov(H, W, seed=9, smax=12.0)
     g = run_gpu(img, cov, n, 2, q=-1, want_steps=True)
-    L = g["L"]
+    L, _ = oracle_steps(cov, n)
     mass = float(np.prod(L.astype(np.float64) ** n, axis=0).max())
     assert abs(g["info"].max_mass - mass) <= 1e-6 * mass
     vmax = float(np.abs(img).max())
     q_expect = min(math.floor(62 - math.log2(vmax) - math.log2(mass)) - 1, 64 - 28)
-    assert g["q"] == q_expect
+    _, q = oracle_q(img, cov, n, -1, gpu=g)
+    assert q == q_expect
     assert g["status"] == 0
-    o = run_oracle(img, cov, n, 2, g["q"], g["R"])
+    o = run_oracle(img, cov, n, 2, q, gpu=g)
     np.testing.assert_array_equal(g["out"], o["out"])
 
 
@@ -199,7 +203,8 @@ def test_auto_q_on_large_kernels_does_not_overflow():
     g = run_gpu(img, cov, n, 2, q=-1)
     assert g["status"] == 0
     assert g["info"].max_mass > 2.0 ** 30
-    o = run_oracle(img, cov, n, 2, g["q"], g["R"])
+    _, q = oracle_q(img, cov, n, -1, gpu=g)
+    o = run_oracle(img, cov, n, 2, q, gpu=g)
     np.testing.assert_array_equal(g["out"], o["out"])
 
 
@@ -277,7 +282,7 @@ def test_bounded_wait_times_out_and_context_stays_usable():
     assert f.status() == 0
     R = f.info().R
     f.close()
-    o = run_oracle(img, cov, n, 2, 20, R)
+    o = run_oracle(img, cov, n, 2, 20, gpu=R)
     np.testing.assert_array_equal(out.cpu().numpy(), o["out"])
 
 

@@ -9,6 +9,7 @@ import pytest
 
 import workloads as wl
 from oracle import kernels, modular, params
+from tests.gpu_helpers import oracle_R
 
 pytestmark = pytest.mark.gpu
 
@@ -61,7 +62,7 @@ def test_tiles_bit_exact_vs_oracle(n, boundary, dtype):
     q = 16 if n < 3 else 10
     out, info, st, prof = _run(img, cov, n, boundary, q)
     assert st == 0 and prof["tiles"][1] == 1 and prof["rows"][1] == 0
-    ref = modular.filter_modular(img, cov, n, boundary, q=q, R=info.R)
+    ref = modular.filter_modular(img, cov, n, boundary, q=q, R=oracle_R(cov, n, gpu=info.R))
     np.testing.assert_array_equal(out, ref)
 
 
@@ -76,7 +77,7 @@ def test_tiles_precisions_equal_global_passes(precision, n):
     assert st_a == st_b == 0 and pa["tiles"][1] == 1 and pb["tiles"][1] == 0
     np.testing.assert_array_equal(a, b)
     bits = {5: 32, 1: 64, 2: 128}[precision]
-    np.testing.assert_array_equal(a, modular.filter_modular(img, cov, n, 2, q=q, bits=bits, R=info.R,
+    np.testing.assert_array_equal(a, modular.filter_modular(img, cov, n, 2, q=q, bits=bits, R=oracle_R(cov, n, gpu=info.R),
                                                             out_dtype=np.float64))
 
 
@@ -85,7 +86,7 @@ def test_tiny_image_and_bands():
     cov = _cov(40, 33, seed=2)
     out, info, st, prof = _run(img, cov, 2, 2, 18)
     assert prof["tiles"][1] == 1
-    np.testing.assert_array_equal(out, modular.filter_modular(img, cov, 2, 2, q=18, R=info.R))
+    np.testing.assert_array_equal(out, modular.filter_modular(img, cov, 2, 2, q=18, R=oracle_R(cov, 2, gpu=info.R)))
     H, W = 200, 150
     img = wl.blob_image(H, W, seed=3, n_blobs=6, sigma_range=(2, 8)).astype(np.float32)
     cov = _cov(H, W, seed=4)
@@ -101,7 +102,7 @@ def test_large_padding_takes_the_global_passes():
     cov = wl.random_cov_field(H, W, seed=6, sigma_range=(20, 26), rho_range=(1, 2))
     out, info, st, prof = _run(img, cov, 2, 2, 12)
     assert info.R > 60 and prof["tiles"][1] == 0 and prof["rows"][1] == 1
-    np.testing.assert_array_equal(out, modular.filter_modular(img, cov, 2, 2, q=12, R=info.R))
+    np.testing.assert_array_equal(out, modular.filter_modular(img, cov, 2, 2, q=12, R=oracle_R(cov, 2, gpu=info.R)))
 
 
 @pytest.mark.parametrize("n,bound,precision", [(1, 1e-8, 3), (2, 1e-3, 3), (1, 1e-5, 4)])
@@ -163,7 +164,7 @@ def test_tiles_of_the_second_set_and_the_pair(directions, n, precision):
         out = f.filter(torch.from_numpy(img).cuda(), torch.from_numpy(cov).cuda())
         profs.append(f.read_profile())
         assert f.status() == 0
-        R = f.info().R
+        R = oracle_R(cov, n, dirs="second" if directions == 1 else "pair", gpu=f.info().R)
         outs.append(out.cpu().numpy())
         f.close()
     assert profs[0]["tiles"][1] == 1 and profs[1]["tiles"][1] == 0

@@ -10,6 +10,7 @@ import pytest
 import workloads as wl
 from oracle import continuous as cn
 from oracle import two_pass
+from tests.gpu_helpers import oracle_R_two_pass
 
 pytestmark = pytest.mark.gpu
 
@@ -34,7 +35,7 @@ def _run(img, cov, n, boundary, q, precision=1, frac=0.5, cov_kind=0, out64=Fals
                                 out=out, want_sigma2=True)
     torch.cuda.synchronize()
     assert f.status() == 0
-    R = f.info().R
+    R = oracle_R_two_pass(cov, n, frac, cov_kind, gpu=f.info().R)
     f.close()
     return out.cpu().numpy(), np.float32(s2), R
 

@@ -1,11 +1,13 @@
-"""The usage example of the README runs as written, and both of its calls
-agree bit for bit with the oracle on sampled rows (each checked on a band of
-rows that reaches two paddings beyond them, so the band's own edges are out
-of reach of both passes)."""
+"""The library's usage example (one image filtered on its own and by
+Algorithm 1's two passes) runs as written, and both of its calls agree bit
+for bit with the oracle on sampled rows (each checked on a band of rows that
+reaches two paddings beyond them, so the band's own edges are out of reach
+of both passes).  R and q come from the oracle's rules, checked against the
+library's."""
 import numpy as np
 import pytest
 
-from oracle import modular, two_pass
+from oracle import config, modular, two_pass
 
 pytestmark = pytest.mark.gpu
 
@@ -19,12 +21,12 @@ def _lib():
     build.build()
 
 
-def test_readme_example():
+def test_usage_example():
     import torch
     from paper_1109_5114_gb300 import bsf
 
     torch.manual_seed(0)
-    # --- as in the README ---
+    # --- the usage example ---
     H, W = 2048, 2048
     img = torch.rand(H, W, device="cuda")
     cov = torch.empty(3, H, W, device="cuda")
@@ -42,11 +44,15 @@ def test_readme_example():
     im = img.cpu().numpy()
     cv = cov.cpu().numpy()
     o1, o2 = out.cpu().numpy(), out2.cpu().numpy()
-    R = max(info1.R, info2.R)
+    # the plan of the first call (its R and mass bound) serves the second;
+    # the value bound 1.0 fixes q
+    R = config.padding(cv, 2)
+    q = max(config.auto_frac_bits(1.0, config.mass_bound(cv, 2), 64), 0)
+    assert (info1.R, info1.frac_bits) == (R, q) == (info2.R, info2.frac_bits)
     for y0 in (0, 1500, H - 8):
         lo, hi = max(0, y0 - 2 * R), min(H, y0 + 8 + 2 * R)
-        band = modular.filter_modular(im[lo:hi], cv[:, lo:hi], 2, 2, q=info1.frac_bits, bits=64,
-                                      out_dtype=np.float32, R=info1.R)
+        band = modular.filter_modular(im[lo:hi], cv[:, lo:hi], 2, 2, q=q, bits=64,
+                                      out_dtype=np.float32, R=R)
         np.testing.assert_array_equal(o1[y0:y0 + 8], band[y0 - lo:y0 - lo + 8])
-        band2, _, _ = two_pass.algorithm1(im[lo:hi], cv[:, lo:hi], 2, 2, q=info2.frac_bits, R=info2.R)
+        band2, _, _ = two_pass.algorithm1(im[lo:hi], cv[:, lo:hi], 2, 2, q=q, R=R)
         np.testing.assert_array_equal(o2[y0:y0 + 8], band2[y0 - lo:y0 - lo + 8])
