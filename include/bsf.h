@@ -203,9 +203,14 @@ typedef struct {
   unsigned clamp_count;/* pixels clamped to the elongation bound, last call */
   unsigned flags;      /* BSF_FLAG_* */
   long long workspace_bytes;
+  int grad_elem_bytes; /* bytes per element of the backward's adjoint sums: 16 for the
+                          continuous steps and for 128-bit contexts, else 8 */
 } bsf_info_t;
 
-/* Create a context for H x W images, N = 4 directions, order n in 1..3.
+/* Create a context for H x W images, N = 4 directions, order n in 1..3
+ * (Section 1.1: the four-directional box spline beta_a with directions
+ * 0, pi/4, pi/2, 3pi/4; Section 2.1: its n-fold self-convolution, whose
+ * finite-difference mesh has (n+1)^4 points).
  * boundary: BSF_ZERO / BSF_REPLICATE / BSF_SYMMETRIC.
  * max_reach: padding R >= 0 (fixes the workspace now), or -1 to size it from
  * the first covariance field seen (bsf_plan, or the first bsf_filter).
@@ -237,8 +242,9 @@ int bsf_set_stream(bsf_t h, void* stream);
  * q_t = 0 for uint8 images (exact) and q_t = 25 - ceil(log2 max|f|)
  * otherwise (quantisation below half a float32 ulp of the largest value).
  * 32 bits only for the forward filter with integer steps; the continuous
- * steps choose between 64 and 128; the backward needs the pre-integration
- * to have come out 64-bit (else BSF_EINVAL).  bsf_get_info reports the
+ * steps choose between 64 and 128.  The backward reads no running sums; its
+ * adjoint sums are 128-bit for 128-bit contexts and the continuous steps,
+ * 64-bit otherwise (bsf_info_t.grad_elem_bytes).  bsf_get_info reports the
  * element size taken.  Errors: BSF_EINVAL. */
 int bsf_set_precision(bsf_t h, int mode, int frac_bits);
 
@@ -264,14 +270,21 @@ int bsf_set_option(bsf_t h, int option, long long value);
  * BSF_ECUDA. */
 int bsf_plan(bsf_t h, const float* cov, int cov_kind);
 
-/* Pre-integration (step 1): extend the device image img ([H][ld], dtype
+/* Pre-integration (step 1 of Section 1.1's BoxFilter: the running sums of
+ * the image along each direction, one grid step apart on the axes and on the
+ * diagonals; n-fold for order n, Algorithm 3's recursion form without its
+ * step-length factor): extend the device image img ([H][ld], dtype
  * BSF_U8 / BSF_F32 / BSF_F64) by the boundary rule onto the padded domain,
  * quantise it, and run the n-fold running sums along d1, d3, d2, d4 into the
  * context's workspace.  Requires R (max_reach or a plan).
  * Errors: BSF_EINVAL, BSF_ESTATE (no R yet), BSF_ECUDA. */
 int bsf_preintegrate(bsf_t h, const void* img, int dtype, long long ld);
 
-/* Whole forward filter.  img != NULL: pre-integrate it first (as
+/* Whole forward filter (Section 1.1's BoxFilter: pre-integration, then per
+ * pixel the finite differences of the running sums on the 16-tap mesh of
+ * eq. "geometry"'s scales, generalised to (n+1)^4 taps for order n, the
+ * steps set by the pixel's covariance through the minimum-kurtosis choice,
+ * normalised by the kernel mass).  img != NULL: pre-integrate it first (as
  * bsf_preintegrate; plans on the fly, synchronously, when R is not known);
  * img == NULL: reuse the last pre-integration.  cov: device [3][H][W] float32.
  * out: device [H][ldo] of out_dtype BSF_F32 or BSF_F64.
@@ -345,11 +358,16 @@ int bsf_filter_rows(bsf_t h, const void* img, int dtype, long long ld, const flo
  *   gcov  NULL or device [3][H][W] float32: the integer steps of D1 are
  *         piecewise constant in the covariance, so this gradient is zero
  *         almost everywhere and is written as zeros.
- * Requires a known R (plan or max_reach) and BSF_FIX64.  The first call
- * allocates the backward workspace (synchronous).
+ * Requires a known R (plan or max_reach); any element type of the forward
+ * (the backward reads no running sums).  Contexts with uint128 running sums
+ * (masses too large for 64-bit weights) take the same pipeline in 128 bits:
+ * qg = 118 - ceil(log2 max|gout|) in [0, 126], weights g(p) =
+ * RNE(RN32(RN32(gout 2^qg) / RN32(D))), sums modulo 2^128 (128-bit additions
+ * from two 64-bit atomics and the carry of the first), gimg = RN32(acc)
+ * 2^-qg.  The first call allocates the backward workspace (synchronous).
  * With step rule BSF_STEP_D2: gcov (if not NULL) = gout * d out / d plane,
  * from the held running sums of the forward's image (see
- * bsf_filter_jacobian); gimg (if not NULL, BSF_FIX128 contexts) is the image
+ * bsf_filter_jacobian); gimg (if not NULL; any fixed-point context) is the image
  * gradient: each pixel scatters g(p) = RNE(RN32(RN32(gout 2^qg) / RN32(M)))
  * times the product of its four interpolation weights at its 5^4 (n = 2) or
  * 4^4 (n = 1) samples into uint128 adjoint sums (128-bit additions built from
@@ -361,7 +379,7 @@ int bsf_filter_rows(bsf_t h, const void* img, int dtype, long long ld, const flo
 int bsf_filter_backward(bsf_t h, const float* gout, long long ldg, const float* cov, int cov_kind,
                         float* gimg, long long ldgi, float* gcov);
 
-/* Row-band backward (integer steps): the multi-device form of
+/* Row-band backward (integer or continuous steps): the multi-device form of
  * bsf_filter_backward.  A device that filtered rows [y0, y1) computes the
  * adjoint of its band alone: the pixels of the band scatter into running
  * sums over the band's padded rows [y0 - R, y1 + R), which are summed in
@@ -370,14 +388,16 @@ int bsf_filter_backward(bsf_t h, const float* gout, long long ldg, const float* 
  * whole image's on every input, so these adjoints add up to the whole-image
  * gradient: each device adds its neighbours' overlapping rows (the halo
  * add-exchange of R rows each way) to its own rows [y0, y1) and finalises.
- * The sums are exact integers modulo 2^64 (two's complement int64 in acc),
- * so the assembled gradient equals bsf_filter_backward's bit for bit when
- * every band uses the same grad_bits: take bsf_grad_frac_bits of the maximum
- * of |gout| over all bands (bsf_grad_absmax_rows per band, then the maximum
- * across devices).
- *   acc   device int64 [a1 - a0][lda] (written); row 0 is image row a0.
- * Requires BSF_FIX64, R <= H, integer steps.  Errors: BSF_EINVAL, BSF_ESTATE,
- * BSF_ENOMEM, BSF_ECUDA. */
+ * The sums are exact integers modulo 2^64, or 2^128 where the context's
+ * adjoint is 128-bit (bsf_info_t.grad_elem_bytes = 16: continuous steps,
+ * 128-bit running sums), so the assembled gradient equals
+ * bsf_filter_backward's bit for bit when every band uses the same grad_bits:
+ * take bsf_grad_frac_bits_of of the maximum of |gout| over all bands
+ * (bsf_grad_absmax_rows per band, then the maximum across devices).
+ *   acc   device [a1 - a0][lda] elements of grad_elem_bytes (written): two's
+ *         complement int64, or int128 as (low, high) int64 pairs; row 0 is
+ *         image row a0.
+ * Requires R <= H.  Errors: BSF_EINVAL, BSF_ESTATE, BSF_ENOMEM, BSF_ECUDA. */
 int bsf_filter_backward_rows(bsf_t h, const float* gout, long long ldg, const float* cov,
                              int cov_kind, int y0, int y1, int grad_bits, long long* acc,
                              long long lda);
@@ -386,13 +406,30 @@ int bsf_filter_backward_rows(bsf_t h, const float* gout, long long ldg, const fl
  * m = max |gout| (float32 value of m), clamped to [0, 100].  Pure function. */
 int bsf_grad_frac_bits(double max_abs_gout);
 
+/* The context's rule for qg: bsf_grad_frac_bits for 64-bit adjoint sums, and
+ * 118 - ceil(log2 m) in [0, 126] for 128-bit ones (bsf_info_t.grad_elem_bytes).
+ * Pure function of the context's configuration.  Errors: BSF_EINVAL. */
+int bsf_grad_frac_bits_of(bsf_t h, double max_abs_gout);
+
 /* max |gout| over rows [y0, y1) of device gout [H][ldg] into *result (host
  * float).  Synchronises.  Errors: BSF_EINVAL, BSF_ECUDA. */
 int bsf_grad_absmax_rows(bsf_t h, const float* gout, long long ldg, int y0, int y1, float* result);
 
-/* gimg[r][x] = RN32(acc[r][x]) 2^-grad_bits for rows r < rows (device int64
- * acc [rows][lda], device float32 gimg [rows][ldgi]): the final rounding of
- * the backward.  Errors: BSF_EINVAL, BSF_ECUDA. */
+/* acc[r][x] += halo[r][x] modulo 2^64 (or 2^128: elements of the context's
+ * grad_elem_bytes) for rows r < rows and x < W (device acc [rows][lda] and
+ * halo [rows][ldh], in elements): the add step of the row-band
+ * backward's exchange, where a band's adjoint sums receive the rows its
+ * neighbours' adjoints reach into it (the transpose of Section 1.1's
+ * BoxFilter spreads each band's contribution up to R rows beyond the band).
+ * Exact in two's complement, so the order of the adds does not matter.
+ * Asynchronous on the context's stream.  Errors: BSF_EINVAL, BSF_ECUDA. */
+int bsf_grad_halo_add(bsf_t h, long long* acc, long long lda, const long long* halo, long long ldh,
+                      int rows);
+
+/* gimg[r][x] = RN32(acc[r][x]) 2^-grad_bits for rows r < rows (device acc
+ * [rows][lda] of the context's grad_elem_bytes, two's complement; device
+ * float32 gimg [rows][ldgi]): the final rounding of the backward.
+ * Errors: BSF_EINVAL, BSF_ECUDA. */
 int bsf_grad_finalize(bsf_t h, const long long* acc, long long lda, int rows, int grad_bits,
                       float* gimg, long long ldgi);
 
@@ -496,7 +533,7 @@ int bsf_read_profile(bsf_t h, double* ms, int* count);
  *         steps and make the call return BSF_ERANGE)
  *   frac_bits  q in [0, 62]
  *   stream     cudaStream_t (NULL = legacy default stream)
- * Sizes whose workspace (running sums, scan carries) would not fit the
+ * Sizes whose workspace (running sums, chunk aggregates of the vertical sums) would not fit the
  * array -- at most 2^24 pixels and 2^24 padded elements, and 24 MiB in all --
  * are rejected with BSF_ERANGE before any device work.
  * Synchronous: returns BSF_OK, a host-side error (BSF_EINVAL, BSF_ERANGE,
@@ -504,8 +541,15 @@ int bsf_read_profile(bsf_t h, double* ms, int* count);
  * BSF_ECOV).
  * The first call on each device looks up the array's device address with
  * cudaGetSymbolAddress (the device must be current); make that first call
- * before any stream capture.  All calls share the array and it keeps the last
- * call's contents, so calls that overlap on the GPU race: serialise them. */
+ * before any stream capture.  With CUDA's lazy module loading (the default
+ * since CUDA 12.2) that first call is also when the array's 24 MiB and the
+ * library's code are reserved on the device, and it may synchronise the
+ * device: a caller that hands all remaining device memory to its own pool
+ * should make one small warm-up call on each device at start-up, before
+ * reserving the pool (or set CUDA_MODULE_LOADING=EAGER).  All calls share the
+ * array and it keeps the last call's contents, so calls that overlap on the
+ * GPU race: serialise them.  A failing call returns only after the work it
+ * queued has finished. */
 int bsf_filter_noalloc(const void* img, int dtype, long long ld, int H, int W, int n,
                        int boundary, int reach, int frac_bits, const float* cov,
                        void* out, int out_dtype, long long ldo, void* stream);
@@ -539,11 +583,29 @@ typedef struct {
   int blocks[5];         /* blocks of the five batched phases (rows, d3, d2, d4, stencil) */
   long long pixels;      /* output pixels of the batch */
   int graph_ready;       /* a CUDA graph of the batched launches is instantiated */
+  int persist_items;     /* work items of the persistent launch */
+  int persist_grid;      /* its resident blocks (SMs x blocks per SM) */
+  int rows_per_item;     /* padded rows of one row item */
+  int stencil_tile_rows; /* rows of one finite-difference tile (32 pixels wide) */
+  int persist_graph_ready; /* a CUDA graph of the persistent launch is instantiated */
+  int persist_groups;    /* image groups of the persistent launch */
 } bsf_batch_info_t;
 
-#define BSF_BATCH_GRAPH      1  /* record the batched launches once in a CUDA graph, replay it */
+#define BSF_BATCH_GRAPH      1  /* record the launches once in a CUDA graph, replay it */
 #define BSF_BATCH_PER_IMAGE  2  /* baseline: the per-image kernels, image after image */
-#define BSF_BATCH_AUTOTUNE   4  /* bsf_batch_plan: time scan chunk heights per size class */
+#define BSF_BATCH_AUTOTUNE   4  /* bsf_batch_plan: tune chunk heights, item shapes and blocks per SM */
+#define BSF_BATCH_PERSISTENT 8  /* bsf_filter_batched: the whole batch as one persistent launch */
+
+/* Options of a batch (bsf_batch_set_option). */
+#define BSF_BATCH_OPT_WAIT_LIMIT    1  /* polls of one wait of the persistent launch before it
+                                          records BSF_ETIMEOUT and goes on (default 2^22) */
+#define BSF_BATCH_OPT_TEST_WITHHOLD 2  /* failure injection for tests: 1 = the row phase of image 0
+                                          never signals completion, so every wait on it runs out */
+#define BSF_BATCH_OPT_ROWS_PER_ITEM 3  /* padded rows per row item of the persistent launch (1..64) */
+#define BSF_BATCH_OPT_STENCIL_ROWS  4  /* rows of a finite-difference tile: 8, 16, 32 or 64 */
+#define BSF_BATCH_OPT_BLOCKS_PER_SM 5  /* resident blocks per SM of the persistent launch (0 = all that fit) */
+#define BSF_BATCH_OPT_GROUP_MB      6  /* running-sum MiB of one image group of the persistent launch
+                                          (0 = the whole batch is one group; default 48) */
 
 /* Create a batch object for order n (1..3) and a boundary rule.  It uses
  * uint64 running sums and its own non-blocking stream.  Errors: BSF_EINVAL,
@@ -571,9 +633,16 @@ int bsf_batch_set_tune_cache(bsf_batch_t b, const char* path);
 
 /* Plan a batch of B images (host array of descriptors): solve each image's
  * steps to find its R (synchronous), choose q, allocate one arena, build the
- * per-phase block offsets; with BSF_BATCH_AUTOTUNE also time scan chunk
- * heights of 32, 64 and 128 rows on the largest image of each height class
- * (running the filter on it) and keep the fastest.
+ * per-phase block offsets and the work items of the persistent launch; with
+ * BSF_BATCH_AUTOTUNE also time scan chunk heights of 32, 64 and 128 rows on
+ * the largest image of each height class (running the filter on it), then
+ * tune the persistent launch on the batch itself by coordinate descent (two
+ * passes): the chunk height of each height class present (32..128 rows),
+ * padded rows per row item (1, 2, 4, 8), rows of a finite-difference tile
+ * (8, 16, 32), blocks per SM and the image-group budget (16..96 MiB, or one
+ * group), each kept only when the timed launch gets
+ * faster.  Tuning writes the outputs.  Values from the tune cache (or set
+ * as options) are not tuned again.
  * Errors: BSF_EINVAL, BSF_ENOMEM, BSF_ECUDA. */
 int bsf_batch_plan(bsf_batch_t b, int B, const bsf_image_desc* descs, int flags);
 
@@ -582,7 +651,17 @@ int bsf_batch_plan(bsf_batch_t b, int B, const bsf_image_desc* descs, int flags)
  * kernels of each vertical direction, finite differences: 8 launches);
  * BSF_BATCH_GRAPH records them in a CUDA graph on the first call and replays
  * it; BSF_BATCH_PER_IMAGE runs the single-image kernels image by image
- * (8 launches per image).  Asynchronous on the batch's stream.
+ * (8 launches per image).  BSF_BATCH_PERSISTENT runs the batch as one
+ * persistent launch (a memset of its counters, then one kernel): resident
+ * blocks take work items -- padded rows, chunks of 256 lines of each vertical
+ * direction's two passes, tiles of the finite differences -- from one ticket
+ * counter, image group by image group (consecutive images whose running sums
+ * fit BSF_BATCH_OPT_GROUP_MB, so that a group's sums stay in L2 across its
+ * passes) and within a group phase by phase; an item waits until the phase before it has
+ * finished on its image (a per-image counter; waits are bounded by
+ * BSF_BATCH_OPT_WAIT_LIMIT and report BSF_ETIMEOUT); with BSF_BATCH_GRAPH
+ * that launch is recorded in a CUDA graph and replayed.  The results equal
+ * the other modes' bit for bit.  Asynchronous on the batch's stream.
  * Errors: BSF_EINVAL, BSF_ESTATE, BSF_ECUDA; device-side problems go to
  * bsf_batch_status. */
 int bsf_filter_batched(bsf_batch_t b, int B, const bsf_image_desc* descs, int flags);
@@ -590,6 +669,10 @@ int bsf_filter_batched(bsf_batch_t b, int B, const bsf_image_desc* descs, int fl
 /* Synchronise and return the first device-side error since the last call
  * (as bsf_status), then clear it. */
 int bsf_batch_status(bsf_batch_t b);
+
+/* Set a batch option (BSF_BATCH_OPT_*).  The shape options re-lay the plan
+ * (synchronous) and drop recorded graphs.  Errors: BSF_EINVAL. */
+int bsf_batch_set_option(bsf_batch_t b, int option, long long value);
 
 int bsf_batch_get_info(bsf_batch_t b, bsf_batch_info_t* info);
 const char* bsf_batch_last_error(bsf_batch_t b);

@@ -23,6 +23,10 @@ exact integer arithmetic; the result is RN32(acc) 2^-qg.  qg is chosen from
 max |gout| so that the exact gradient keeps 2^8 of headroom in 62 bits:
 qg = 54 - ceil(log2 max|gout|), clamped to [0, 100].
 
+Contexts whose running sums are 128 bits wide (masses beyond 2^64) take
+the same number format in 128 bits: qg = 118 - ceil(log2 max|gout|) in
+[0, 126], exact sums modulo 2^128 (adjoint_direct_wide).
+
 Two routes, pinned against each other:
   adjoint_direct   -- the definition: explicit kernels, explicit scatter;
   adjoint_modular  -- the pipeline's transpose: scatter w_t g(p) at the taps,
@@ -94,6 +98,39 @@ def adjoint_direct_acc(g: np.ndarray, Lfield: np.ndarray, n: int, boundary: int)
 def adjoint_direct(gout: np.ndarray, Lfield: np.ndarray, n: int, boundary: int, qg: int):
     D = modular.masses(Lfield, n)
     g = quantize_weights(gout, D, qg)
+    return _finish(adjoint_direct_acc(g, Lfield, n, boundary), qg)
+
+
+# ---------------------------------------------------------------------------
+# 128-bit number format (contexts whose kernel masses exceed the reach of
+# 64-bit weights): the same route with qg = 118 - ceil(log2 max|gout|) in
+# [0, 126], exact sums modulo 2^128 (Python integers here, no modulus needed)
+# ---------------------------------------------------------------------------
+
+def grad_frac_bits_wide(max_abs_gout: float) -> int:
+    """qg = 118 - ceil(log2 m) for m = max |gout| (float32), clamped to [0, 126]."""
+    m = float(np.float32(max_abs_gout))
+    if m == 0.0 or not math.isfinite(m):
+        c = 0
+    else:
+        mant, e = math.frexp(m)
+        c = e - 1 if mant == 0.5 else e
+    return int(min(max(118 - c, 0), 126))
+
+
+def quantize_weights_wide(gout: np.ndarray, D: np.ndarray, qg: int) -> np.ndarray:
+    """g(p) = RNE(RN32(gout 2^qg) / RN32(D)) as Python integers (object array)."""
+    x = gout.astype(np.float32) * np.float32(math.ldexp(1.0, qg))
+    Dobj = np.asarray(D).astype(object)
+    y = np.vectorize(rn_f32_int, otypes=[np.float32])(Dobj)
+    g = (x / y).astype(np.float32)
+    return np.vectorize(lambda v: int(round(float(v))), otypes=[object])(g)
+
+
+def adjoint_direct_wide(gout: np.ndarray, Lfield: np.ndarray, n: int, boundary: int):
+    """The image gradient in the 128-bit number format, by the definition."""
+    qg = grad_frac_bits_wide(float(np.abs(gout).max(initial=0.0)))
+    g = quantize_weights_wide(gout, modular.masses(Lfield, n), qg)
     return _finish(adjoint_direct_acc(g, Lfield, n, boundary), qg)
 
 

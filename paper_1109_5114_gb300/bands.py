@@ -41,14 +41,17 @@ def check_bands(H: int, R: int, world: int) -> None:
                          "use fewer bands")
 
 
-def halo_exchange_add(acc, H: int, R: int, rank: int, world: int, group=None):
-    """Add the neighbours' halo contributions to this rank's own rows.
+def halo_exchange(acc, H: int, R: int, rank: int, world: int, group=None):
+    """Send this band's halo rows to the neighbours and receive theirs.
 
-    acc: int64 tensor [a1 - a0][W] of the band's adjoint sums (CPU or CUDA, as
-    the process group's backend requires).  Rows [a0, y0) go to rank - 1 and
+    acc: int64 tensor [a1 - a0][W] of the band's adjoint sums, or [a1 - a0][W][2]
+    for 128-bit sums as (low, high) pairs (CPU or CUDA, as the process group's
+    backend requires).  Rows [a0, y0) go to rank - 1 and
     rows [y1, a1) to rank + 1; the matching rows of the neighbours are
-    received and added (two's complement, wrapping like the library's
-    modular sums).  Returns the own rows [y0, y1) as a tensor."""
+    received.  Returns (own, recvs): own is a copy of the own rows [y0, y1),
+    recvs a list of (first own row, received rows) that still have to be
+    added to own (two's complement, wrapping like the library's modular
+    sums: the library's bsf_grad_halo_add does that on the device)."""
     import torch
     import torch.distributed as dist
     y0, y1 = band_bounds(H, world, rank)
@@ -58,31 +61,32 @@ def halo_exchange_add(acc, H: int, R: int, rank: int, world: int, group=None):
     if rank > 0:
         ops.append(dist.P2POp(dist.isend, acc[:y0 - a0].contiguous(), rank - 1, group))
         n_up = min(H, y0 + R) - y0                 # rank - 1's rows below its band
-        buf = torch.empty((n_up, acc.shape[1]), dtype=acc.dtype, device=acc.device)
+        buf = torch.empty((n_up,) + tuple(acc.shape[1:]), dtype=acc.dtype, device=acc.device)
         ops.append(dist.P2POp(dist.irecv, buf, rank - 1, group))
         recvs.append((0, buf))
     if rank < world - 1:
         ops.append(dist.P2POp(dist.isend, acc[y1 - a0:].contiguous(), rank + 1, group))
         n_dn = y1 - max(0, y1 - R)                 # rank + 1's rows above its band
-        buf = torch.empty((n_dn, acc.shape[1]), dtype=acc.dtype, device=acc.device)
+        buf = torch.empty((n_dn,) + tuple(acc.shape[1:]), dtype=acc.dtype, device=acc.device)
         ops.append(dist.P2POp(dist.irecv, buf, rank + 1, group))
         recvs.append((y1 - y0 - n_dn, buf))
     if ops:
         for req in dist.batch_isend_irecv(ops):
             req.wait()
-    for start, buf in recvs:
-        own[start:start + buf.shape[0]] += buf
-    return own
+    return own, recvs
 
 
-def common_grad_bits(local_max: float, group=None, device="cpu") -> int:
-    """All-reduce (max) of the bands' max |gout|, then the library's scale rule."""
+def common_grad_bits(local_max: float, group=None, device="cpu", filt=None) -> int:
+    """All-reduce (max) of the bands' max |gout|, then the library's scale rule
+    (the context's: 64- or 128-bit adjoint sums; without a context the 64-bit
+    rule)."""
     import torch
     import torch.distributed as dist
     from . import bsf
     t = torch.tensor([local_max], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
-    return int(bsf.bsf_grad_frac_bits(float(t.item())))
+    m = float(t.item())
+    return filt.grad_frac_bits(m) if filt is not None else int(bsf.bsf_grad_frac_bits(m))
 
 
 def backward_bands(filt, gout, cov, rank: int, world: int, group=None):
@@ -93,7 +97,9 @@ def backward_bands(filt, gout, cov, rank: int, world: int, group=None):
     info = filt.info()
     check_bands(filt.H, info.R, world)
     y0, y1 = band_bounds(filt.H, world, rank)
-    qg = common_grad_bits(filt.grad_absmax_rows(gout, y0, y1), group, device=gout.device)
+    qg = common_grad_bits(filt.grad_absmax_rows(gout, y0, y1), group, device=gout.device, filt=filt)
     acc, _, _ = filt.backward_rows(gout, cov, y0, y1, qg)
-    own = halo_exchange_add(acc, filt.H, info.R, rank, world, group)
+    own, recvs = halo_exchange(acc, filt.H, info.R, rank, world, group)
+    for start, buf in recvs:
+        filt.grad_halo_add(own[start:start + buf.shape[0]], buf)
     return filt.grad_finalize(own, qg)

@@ -48,7 +48,7 @@ class bsf_info_t(ctypes.Structure):
                 ("elem_bytes", c_int), ("precision", c_int), ("frac_bits", c_int),
                 ("step_rule", c_int), ("max_reach", c_int), ("max_mass", c_double),
                 ("clamp_count", ctypes.c_uint), ("flags", ctypes.c_uint),
-                ("workspace_bytes", c_ll)]
+                ("workspace_bytes", c_ll), ("grad_elem_bytes", c_int)]
 
 
 def _fn(name, restype, *argtypes):
@@ -85,6 +85,7 @@ bsf_jacobian_vjp = _fn("bsf_jacobian_vjp", c_int, bsf_t, c_void_p, c_ll, c_void_
 bsf_filter_backward_rows = _fn("bsf_filter_backward_rows", c_int, bsf_t, c_void_p, c_ll, c_void_p, c_int,
                                c_int, c_int, c_int, c_void_p, c_ll)
 bsf_grad_frac_bits = _fn("bsf_grad_frac_bits", c_int, c_double)
+bsf_grad_frac_bits_of = _fn("bsf_grad_frac_bits_of", c_int, bsf_t, c_double)
 bsf_grad_absmax_rows = _fn("bsf_grad_absmax_rows", c_int, bsf_t, c_void_p, c_ll, c_int, c_int,
                            ctypes.POINTER(ctypes.c_float))
 bsf_filter_host = _fn("bsf_filter_host", c_int, bsf_t, c_void_p, c_int, c_ll, c_void_p, c_int, c_void_p,
@@ -92,6 +93,7 @@ bsf_filter_host = _fn("bsf_filter_host", c_int, bsf_t, c_void_p, c_int, c_ll, c_
 bsf_filter_two_pass = _fn("bsf_filter_two_pass", c_int, bsf_t, c_void_p, c_int, c_ll, c_void_p, c_int,
                           c_double, c_void_p, c_int, c_ll, ctypes.POINTER(ctypes.c_float))
 bsf_grad_finalize = _fn("bsf_grad_finalize", c_int, bsf_t, c_void_p, c_ll, c_int, c_int, c_void_p, c_ll)
+bsf_grad_halo_add = _fn("bsf_grad_halo_add", c_int, bsf_t, c_void_p, c_ll, c_void_p, c_ll, c_int)
 
 class bsf_image_desc(ctypes.Structure):
     _fields_ = [("H", c_int), ("W", c_int), ("img", c_void_p), ("dtype", c_int), ("ld", c_ll),
@@ -101,7 +103,9 @@ class bsf_image_desc(ctypes.Structure):
 class bsf_batch_info_t(ctypes.Structure):
     _fields_ = [("B", c_int), ("frac_bits", c_int), ("arena_bytes", c_ll),
                 ("scan_chunk", c_int * 4), ("blocks", c_int * 5), ("pixels", c_ll),
-                ("graph_ready", c_int)]
+                ("graph_ready", c_int), ("persist_items", c_int), ("persist_grid", c_int),
+                ("rows_per_item", c_int), ("stencil_tile_rows", c_int), ("persist_graph_ready", c_int),
+                ("persist_groups", c_int)]
 
 
 bsf_batch_t = ctypes.c_void_p
@@ -116,6 +120,7 @@ bsf_filter_batched = _fn("bsf_filter_batched", c_int, bsf_batch_t, c_int, ctypes
 bsf_batch_status = _fn("bsf_batch_status", c_int, bsf_batch_t)
 bsf_batch_get_info = _fn("bsf_batch_get_info", c_int, bsf_batch_t, ctypes.POINTER(bsf_batch_info_t))
 bsf_batch_last_error = _fn("bsf_batch_last_error", ctypes.c_char_p, bsf_batch_t)
+bsf_batch_set_option = _fn("bsf_batch_set_option", c_int, bsf_batch_t, c_int, c_ll)
 
 ERROR_NAMES = {v: k for k, v in _C.items() if k.startswith("BSF_E")}
 
@@ -170,16 +175,23 @@ class BoxSplineFilter:
     directions: BSF_DIRS_CARTESIAN (0), BSF_DIRS_SECOND (1: the box spline on
     (2,1), (1,2), (-1,2), (-2,1)) or BSF_DIRS_PAIR (2: both, switched per
     pixel by sector).
+    memory_budget: bytes that box_spline_filter may keep from the forward for
+    the backward beyond its inputs (None: no limit).  The continuous-step
+    forward with a covariance that requires grad stores its Jacobian
+    (12 bytes per pixel) only within the budget; above it the backward
+    recomputes the running sums of the image and the Jacobian product
+    (bsf_filter_backward) instead, with the same result bit for bit.
     """
 
     def __init__(self, H: int, W: int, n: int, boundary="symmetric", max_reach: int = -1,
                  precision: int = 1, frac_bits: int = -1, value_bound=None, step_rule: int = 0,
-                 cov_kind: int = 0, directions: int = 0):
+                 cov_kind: int = 0, directions: int = 0, memory_budget=None):
         if isinstance(boundary, str):
             boundary = _BOUNDARY[boundary]
         self.H, self.W, self.n = H, W, n
         self.cov_kind = cov_kind
         self.step_rule = step_rule
+        self.memory_budget = memory_budget
         h = bsf_t()
         rc = bsf_create(ctypes.byref(h), H, W, 4, n, boundary, max_reach)
         if rc != 0:
@@ -317,10 +329,19 @@ class BoxSplineFilter:
         check(self._h, rc)
         return out
 
+    def jacobian_bytes(self) -> int:
+        """Bytes of the continuous-step Jacobian a stored-route forward keeps."""
+        return 12 * self.H * self.W
+
+    def stores_jacobian(self) -> bool:
+        """True when the Jacobian fits memory_budget (the stored route)."""
+        return self.memory_budget is None or self.jacobian_bytes() <= self.memory_budget
+
     def backward(self, gout, cov, gimg=None, want_gcov=False, want_gimg=True):
         """Gradients of the last filter: image gradient (D1; the covariance
-        gradient of D1 is zero) or, for continuous steps, the covariance
-        gradient only (recomputed from the held running sums)."""
+        gradient of D1 is zero) or, for continuous steps, the image gradient
+        and the covariance gradient, recomputed from the held running sums of
+        the last pre-integrated image."""
         import torch
         self._stream()
         H, W = self.H, self.W
@@ -344,18 +365,32 @@ class BoxSplineFilter:
                                             y0, y1, ctypes.byref(r)))
         return float(r.value)
 
-    def backward_rows(self, gout, cov, y0: int, y1: int, grad_bits: int):
-        """Band adjoint: exact int64 sums on image rows [a0, a1) = [y0 - R, y1 + R) clipped.
+    def grad_frac_bits(self, max_abs_gout: float) -> int:
+        """The context's fraction-bit rule of the gradient weights (64- or 128-bit sums)."""
+        return int(bsf_grad_frac_bits_of(self._h, float(max_abs_gout)))
 
-        Returns (acc, a0, a1), acc an int64 CUDA tensor [a1 - a0][W]."""
+    @staticmethod
+    def _acc_ld(acc) -> int:
+        # elements per row of an adjoint-sum tensor: int64 [rows][W], or int128
+        # as int64 pairs [rows][W][2]
+        return acc.stride(0) if acc.dim() == 2 else acc.stride(0) // 2
+
+    def backward_rows(self, gout, cov, y0: int, y1: int, grad_bits: int):
+        """Band adjoint: exact sums on image rows [a0, a1) = [y0 - R, y1 + R) clipped.
+
+        Returns (acc, a0, a1), acc a CUDA tensor of int64 [a1 - a0][W] (64-bit
+        adjoint sums) or of int64 pairs [a1 - a0][W][2] (int128, low word first:
+        continuous steps and 128-bit contexts)."""
         import torch
         self._stream()
-        R = self.info().R
+        inf = self.info()
+        R = inf.R
         a0, a1 = max(0, y0 - R), min(self.H, y1 + R)
-        acc = torch.empty((a1 - a0, self.W), dtype=torch.int64, device=gout.device)
+        shape = (a1 - a0, self.W) if inf.grad_elem_bytes == 8 else (a1 - a0, self.W, 2)
+        acc = torch.empty(shape, dtype=torch.int64, device=gout.device)
         check(self._h, bsf_filter_backward_rows(self._h, ctypes.c_void_p(gout.data_ptr()), gout.stride(0),
                                                 ctypes.c_void_p(cov.data_ptr()), self.cov_kind, y0, y1,
-                                                grad_bits, ctypes.c_void_p(acc.data_ptr()), acc.stride(0)))
+                                                grad_bits, ctypes.c_void_p(acc.data_ptr()), self._acc_ld(acc)))
         return acc, a0, a1
 
     def grad_finalize(self, acc, grad_bits: int, gimg=None):
@@ -365,9 +400,22 @@ class BoxSplineFilter:
         rows = acc.shape[0]
         if gimg is None:
             gimg = torch.empty((rows, self.W), dtype=torch.float32, device=acc.device)
-        check(self._h, bsf_grad_finalize(self._h, ctypes.c_void_p(acc.data_ptr()), acc.stride(0), rows,
+        check(self._h, bsf_grad_finalize(self._h, ctypes.c_void_p(acc.data_ptr()), self._acc_ld(acc), rows,
                                          grad_bits, ctypes.c_void_p(gimg.data_ptr()), gimg.stride(0)))
         return gimg
+
+    def grad_halo_add(self, acc, halo):
+        """acc += halo modulo 2^64 or 2^128 (library kernel): CUDA tensors of the
+        same shape, int64 [rows][W] or int64 pairs [rows][W][2] (acc may be a row
+        slice of a larger tensor)."""
+        import torch
+        self._stream()
+        assert acc.dtype == torch.int64 and halo.dtype == torch.int64 and acc.shape == halo.shape
+        assert acc.is_cuda and halo.is_cuda and acc.stride(-1) == 1 and (acc.dim() == 2 or acc.stride(1) == 2)
+        halo = halo.to(acc.device).contiguous()
+        check(self._h, bsf_grad_halo_add(self._h, ctypes.c_void_p(acc.data_ptr()), self._acc_ld(acc),
+                                         ctypes.c_void_p(halo.data_ptr()), self._acc_ld(halo), acc.shape[0]))
+        return acc
 
     def preintegrate(self, img):
         self._stream()
@@ -427,23 +475,30 @@ def _make_autograd():
     class BoxSplineFilterFunction(torch.autograd.Function):
         """out = filter(img, cov).  Integer steps (D1): backward gives d/dimg
         through the library's adjoint kernels (the steps are piecewise
-        constant, so d/dcov = 0).  Continuous steps (D2): the forward also
-        writes d out / d cov-plane when cov requires grad, and the backward
-        multiplies it by the incoming gradient (library kernel); the image
-        gradient of D2 is not available."""
+        constant, so d/dcov = 0).  Continuous steps (D2): when cov requires
+        grad and the Jacobian (12 bytes per pixel) fits the filter's
+        memory_budget, the forward also writes d out / d cov-plane and the
+        backward multiplies it by the incoming gradient (library kernel);
+        above the budget the forward keeps nothing but its inputs and the
+        backward recomputes the image's running sums and the Jacobian product
+        (bsf_preintegrate, bsf_filter_backward).  The image gradient of D2
+        (uint128 contexts) comes from the library's adjoint kernels."""
 
         @staticmethod
         def forward(ctx, img, cov, filt):
             ctx.filt = filt
             ctx.d2 = filt.step_rule == BSF_STEP_D2  # noqa: F821
+            ctx.recompute = False
             if ctx.d2:
                 cov = cov.contiguous()
-                if cov.requires_grad:
-                    out, jac = filt.filter_jacobian(img.contiguous(), cov)
-                    ctx.save_for_backward(cov, jac)
+                img = img.contiguous()
+                if cov.requires_grad and filt.stores_jacobian():
+                    out, jac = filt.filter_jacobian(img, cov)
+                    ctx.save_for_backward(img, cov, jac)
                     return out
-                ctx.save_for_backward(cov)
-                return filt.filter(img.contiguous(), cov)
+                ctx.recompute = cov.requires_grad
+                ctx.save_for_backward(img, cov)
+                return filt.filter(img, cov)
             out = filt.filter(img.contiguous(), cov.contiguous())
             ctx.save_for_backward(cov)
             return out
@@ -453,11 +508,19 @@ def _make_autograd():
             gout = gout.contiguous().float()
             if ctx.d2:
                 saved = ctx.saved_tensors
+                img, cov = saved[0], saved[1]
                 gimg = gcov = None
+                if ctx.recompute:
+                    # the running sums of this image again (another call may
+                    # have replaced them), then both gradients from them
+                    ctx.filt.preintegrate(img)
+                    gimg, gcov = ctx.filt.backward(gout, cov, want_gimg=ctx.needs_input_grad[0],
+                                                   want_gcov=ctx.needs_input_grad[1])
+                    return gimg, gcov, None
                 if ctx.needs_input_grad[0]:
-                    gimg, _ = ctx.filt.backward(gout, saved[0], want_gimg=True, want_gcov=False)
+                    gimg, _ = ctx.filt.backward(gout, cov, want_gimg=True, want_gcov=False)
                 if ctx.needs_input_grad[1]:
-                    gcov = ctx.filt.jacobian_vjp(gout, saved[1])
+                    gcov = ctx.filt.jacobian_vjp(gout, saved[2])
                 return gimg, gcov, None
             (cov,) = ctx.saved_tensors
             gimg, gcov = ctx.filt.backward(gout.contiguous().float(), cov,
@@ -530,6 +593,9 @@ class BatchFilter:
 
     def run(self, flags: int = 0):
         self._chk(bsf_filter_batched(self._b, self._B, self._descs, flags))
+
+    def set_option(self, option: int, value: int):
+        self._chk(bsf_batch_set_option(self._b, option, int(value)))
 
     def status(self) -> int:
         return bsf_batch_status(self._b)

@@ -29,12 +29,12 @@ _NOFMA = ["-fmad=false"]
 EXTRA = {"bsf_steps.cu": _NOFMA, "bsf_continuous.cu": _NOFMA, "bsf_continuous64.cu": _NOFMA,
          "bsf_continuous128.cu": _NOFMA, "bsf_stencil.cu": _NOFMA, "bsf_backward.cu": _NOFMA,
          "bsf_two_pass.cu": _NOFMA, "bsf_stencil_second.cu": _NOFMA,
-         "bsf_tiles.cu": _NOFMA, "bsf_sampled.cu": _NOFMA}
+         "bsf_tiles.cu": _NOFMA, "bsf_sampled.cu": _NOFMA, "bsf_persistent.cu": _NOFMA}
 
 SOURCES = ["bsf_api.cu", "bsf_steps.cu", "bsf_scan.cu", "bsf_stencil.cu", "bsf_backward.cu",
            "bsf_batch.cu", "bsf_noalloc.cu", "bsf_continuous.cu", "bsf_continuous64.cu",
            "bsf_continuous128.cu", "bsf_two_pass.cu", "bsf_stencil_second.cu", "bsf_tiles.cu",
-           "bsf_sampled.cu"]
+           "bsf_sampled.cu", "bsf_persistent.cu"]
 
 
 def nvcc() -> str:

@@ -35,9 +35,10 @@ struct bsf_ctx {
   void* agg = nullptr;
   void* carry = nullptr;
   size_t scan_bytes = 0;
-  void* G = nullptr;               // backward: adjoint running sums [Hp][pitch] (uint64)
+  void* G = nullptr;               // backward: adjoint running sums [Hp][pitch] (uint64 or uint128)
   void* Gx = nullptr;              // backward: row-folded [Hp][W]
-  size_t G_bytes = 0, Gx_bytes = 0;
+  void* bagg = nullptr;            // backward: chunk states of the reversed vertical sums
+  size_t G_bytes = 0, Gx_bytes = 0, bagg_bytes = 0;
   unsigned* sync_words = nullptr;  // look-back ticket + tile flags
   size_t sync_bytes = 0;
   int scan_mode = BSF_SCAN_THREE_PHASE;
@@ -132,8 +133,9 @@ void free_workspace(bsf_t h) {
   if (h->sync_words) cudaFree(h->sync_words);
   if (h->G) cudaFree(h->G);
   if (h->Gx) cudaFree(h->Gx);
-  h->G = h->Gx = nullptr;
-  h->G_bytes = h->Gx_bytes = 0;
+  if (h->bagg) cudaFree(h->bagg);
+  h->G = h->Gx = h->bagg = nullptr;
+  h->G_bytes = h->Gx_bytes = h->bagg_bytes = 0;
   h->S = h->agg = h->carry = nullptr;
   h->sync_words = nullptr;
   h->sync_bytes = 0;
@@ -959,28 +961,67 @@ int bsf_jacobian_vjp(bsf_t h, const float* gout, long long ldg, const float* jac
   return BSF_OK;
 }
 
-// G (adjoint running sums) and Gx (row-folded) for the whole padded domain.
-static int ensure_backward_workspace(bsf_t h) {
-  if (h->precision != BSF_FIX64) return fail(h, BSF_EINVAL, "backward needs BSF_FIX64");
+// Width of the backward's adjoint sums: 128 bits for the continuous steps and
+// for contexts whose running sums are 128 bits (kernel masses beyond the reach
+// of 64-bit weights), 64 bits otherwise.  The forward's element type plays no
+// other part in the backward (it reads no running sums).
+static int grad_elem(bsf_t h) {
+  return h->step_rule == BSF_STEP_D2 || h->precision == BSF_FIX128 ? 16 : 8;
+}
+static int grad_prec(int be) { return be == 16 ? BSF_FIX128 : BSF_FIX64; }
+static int grad_q_max(int be) { return be == 16 ? 126 : 100; }
+
+// G (adjoint running sums), Gx (row-folded) and the chunk states of the
+// reversed vertical sums, for the whole padded domain, in elements of be bytes.
+static int ensure_backward_workspace(bsf_t h, int be) {
   if (h->R < 0) return fail(h, BSF_ESTATE, "padding unknown: plan or filter first");
   int rc;
   if ((rc = ensure_workspace(h))) return rc;
-  const size_t G_bytes = (size_t)h->pitch * h->Hp * 8, Gx_bytes = (size_t)h->Hp * h->W * 8;
-  if (h->G_bytes != G_bytes || h->Gx_bytes != Gx_bytes) {
+  const size_t G_bytes = (size_t)h->pitch * h->Hp * be, Gx_bytes = (size_t)h->Hp * h->W * be;
+  const int nchunks = (h->Hp + kScanChunkMin - 1) / kScanChunkMin;
+  const size_t bagg_bytes = (size_t)nchunks * h->n * (size_t)(h->Wp + h->Hp - 1) * be;
+  if (h->G_bytes != G_bytes || h->Gx_bytes != Gx_bytes || h->bagg_bytes != bagg_bytes) {
     BSF_CUDA(h, cudaStreamSynchronize(h->stream));
     if (h->G) cudaFree(h->G);
     if (h->Gx) cudaFree(h->Gx);
-    h->G = h->Gx = nullptr;
-    h->G_bytes = h->Gx_bytes = 0;
+    if (h->bagg) cudaFree(h->bagg);
+    h->G = h->Gx = h->bagg = nullptr;
+    h->G_bytes = h->Gx_bytes = h->bagg_bytes = 0;
     BSF_CUDA(h, cudaMalloc(&h->G, G_bytes));
     BSF_CUDA(h, cudaMalloc(&h->Gx, Gx_bytes));
+    BSF_CUDA(h, cudaMalloc(&h->bagg, bagg_bytes));
     h->G_bytes = G_bytes;
     h->Gx_bytes = Gx_bytes;
+    h->bagg_bytes = bagg_bytes;
   }
   return BSF_OK;
 }
 
+// Reversed n-fold sums of G over Hb padded rows: d4, d2, d3 (three-phase, or
+// the look-back scan for 64-bit sums of a 64-bit context), then the rows.
+static int backward_sums(bsf_t h, int be, int Hb) {
+  cudaError_t e = cudaSuccess;
+  const int skews[3] = {-1, 1, 0};  // transposes in reverse order: d4, d2, d3
+  const bool lb = h->scan_mode == BSF_SCAN_LOOKBACK && be == 8 && h->elem == 8 && Hb == h->Hp;
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    if (lb)
+      e = bsf_launch_vscan_lb(BSF_FIX64, h->n, skews[i], true, h->short_tiles != 0, h->G, h->pitch, h->Hp,
+                              h->Wp, h->agg, h->carry, h->sync_words, h->wait_limit, 0, h->st, h->stream);
+    else
+      e = bsf_launch_vscan(grad_prec(be), h->n, skews[i], true, h->G, h->pitch, Hb, h->Wp, h->scan_chunk,
+                           h->bagg, nullptr, h->stream);
+  }
+  if (e == cudaSuccess) e = bsf_launch_suffix_rows(be, h->n, h->G, h->pitch, Hb, h->Wp, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "backward running sums");
+  return BSF_OK;
+}
+
 int bsf_grad_frac_bits(double max_abs_gout) { return bsf_grad_q_host(max_abs_gout); }
+
+int bsf_grad_frac_bits_of(bsf_t h, double max_abs_gout) {
+  if (!h) return BSF_EINVAL;
+  return grad_elem(h) == 16 ? bsf_grad_q_host_wide(max_abs_gout) : bsf_grad_q_host(max_abs_gout);
+}
 
 int bsf_grad_absmax_rows(bsf_t h, const float* gout, long long ldg, int y0, int y1, float* result) {
   if (!h) return BSF_EINVAL;
@@ -1002,14 +1043,16 @@ int bsf_filter_backward_rows(bsf_t h, const float* gout, long long ldg, const fl
   if (!h) return BSF_EINVAL;
   int rc = check_cov_kind(h, cov_kind);
   if (rc) return rc;
-  if (h->step_rule == BSF_STEP_D2 || h->step_rule == BSF_STEP_SAMPLED)
-    return fail(h, BSF_EINVAL, "band backward: integer steps only");
+  if (h->step_rule == BSF_STEP_SAMPLED) return fail(h, BSF_EINVAL, "the sampled box spline: forward only");
+  if (h->step_rule == BSF_STEP_D2 && (rc = check_d2(h))) return rc;
   if (h->dirset != BSF_DIRS_CARTESIAN) return fail(h, BSF_EINVAL, "backward: Cartesian direction set only");
   if (!gout || !cov || !acc) return fail(h, BSF_EINVAL, "NULL gout, cov or acc");
   if (ldg < h->W || lda < h->W) return fail(h, BSF_EINVAL, "leading dimension < W");
   if (y0 < 0 || y1 <= y0 || y1 > h->H) return fail(h, BSF_EINVAL, "bad row band");
-  if (grad_bits < 0 || grad_bits > 100) return fail(h, BSF_EINVAL, "grad_bits outside [0, 100]");
-  if ((rc = ensure_backward_workspace(h))) return rc;
+  const int be = grad_elem(h);
+  if (grad_bits < 0 || grad_bits > grad_q_max(be))
+    return fail(h, BSF_EINVAL, "grad_bits outside [0, %d]", grad_q_max(be));
+  if ((rc = ensure_backward_workspace(h, be))) return rc;
   if (h->R > h->H) return fail(h, BSF_EINVAL, "band backward needs R <= H");
   const int rows = y1 - y0, Hb = rows + 2 * h->R;
   const int a0 = y0 - h->R > 0 ? y0 - h->R : 0, a1 = y1 + h->R < h->H ? y1 + h->R : h->H;
@@ -1017,23 +1060,22 @@ int bsf_filter_backward_rows(bsf_t h, const float* gout, long long ldg, const fl
   cudaError_t e;
   {
     PhaseTimer t(h, BSF_PHASE_BWD_SCATTER);
-    BSF_CUDA(h, cudaMemsetAsync(h->G, 0, (size_t)h->pitch * Hb * 8, h->stream));
-    e = bsf_launch_scatter_d1(h->n, h->G, h->pitch, h->R, cov, cov_kind, h->step_rule, gout, ldg,
-                              h->H, h->W, y0, rows, grad_bits, h->st, h->stream);
+    BSF_CUDA(h, cudaMemsetAsync(h->G, 0, (size_t)h->pitch * Hb * be, h->stream));
+    if (h->step_rule == BSF_STEP_D2)
+      e = bsf_launch_scatter_d2(h->n, h->G, h->pitch, h->R, cov, cov_kind, gout, ldg, h->H, h->W, y0, rows,
+                                grad_bits, h->st, h->stream);
+    else
+      e = bsf_launch_scatter_d1(h->n, be, h->G, h->pitch, h->R, cov, cov_kind, h->step_rule, gout, ldg,
+                                h->H, h->W, y0, rows, grad_bits, h->st, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "band scatter");
   {
     PhaseTimer t(h, BSF_PHASE_BWD_SCANS);
-    const int skews[3] = {-1, 1, 0};
-    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
-      e = bsf_launch_vscan(BSF_FIX64, h->n, skews[i], true, h->G, h->pitch, Hb, h->Wp, h->scan_chunk,
-                           h->agg, h->carry, h->stream);
-    if (e == cudaSuccess) e = bsf_launch_suffix_rows(8, h->n, h->G, h->pitch, Hb, h->Wp, h->stream);
+    if ((rc = backward_sums(h, be, Hb))) return rc;
   }
-  if (e != cudaSuccess) return cuda_fail(h, e, "band running sums");
   {
     PhaseTimer t(h, BSF_PHASE_BWD_FOLD);
-    e = bsf_launch_fold_band(h->G, h->pitch, Hb, h->H, h->W, h->R, y0, h->boundary, h->Gx, a0, a1,
+    e = bsf_launch_fold_band(be, h->G, h->pitch, Hb, h->H, h->W, h->R, y0, h->boundary, h->Gx, a0, a1,
                              acc, lda, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "band fold");
@@ -1046,9 +1088,22 @@ int bsf_grad_finalize(bsf_t h, const long long* acc, long long lda, int rows, in
   if (!acc || !gimg) return fail(h, BSF_EINVAL, "NULL acc or gimg");
   if (lda < h->W || ldgi < h->W || rows <= 0 || rows > h->H)
     return fail(h, BSF_EINVAL, "bad rows or leading dimension");
-  if (grad_bits < 0 || grad_bits > 100) return fail(h, BSF_EINVAL, "grad_bits outside [0, 100]");
-  cudaError_t e = bsf_launch_grad_finalize(acc, lda, rows, h->W, grad_bits, gimg, ldgi, h->stream);
+  const int be = grad_elem(h);
+  if (grad_bits < 0 || grad_bits > grad_q_max(be))
+    return fail(h, BSF_EINVAL, "grad_bits outside [0, %d]", grad_q_max(be));
+  cudaError_t e = bsf_launch_grad_finalize(be, acc, lda, rows, h->W, grad_bits, gimg, ldgi, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "gradient finalize");
+  return BSF_OK;
+}
+
+int bsf_grad_halo_add(bsf_t h, long long* acc, long long lda, const long long* halo, long long ldh,
+                      int rows) {
+  if (!h) return BSF_EINVAL;
+  if (!acc || !halo) return fail(h, BSF_EINVAL, "NULL acc or halo");
+  if (lda < h->W || ldh < h->W || rows <= 0 || rows > h->H)
+    return fail(h, BSF_EINVAL, "bad rows or leading dimension");
+  cudaError_t e = bsf_launch_add_rows(grad_elem(h), acc, lda, halo, ldh, rows, h->W, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "halo add");
   return BSF_OK;
 }
 
@@ -1059,8 +1114,6 @@ static int backward_d2(bsf_t h, const float* gout, long long ldg, const float* c
   int rc = check_d2(h);
   if (rc) return rc;
   if (!gcov && !gimg) return fail(h, BSF_EINVAL, "continuous steps: gimg and gcov are NULL");
-  if (gimg && h->precision != BSF_FIX128)
-    return fail(h, BSF_EINVAL, "continuous steps: the image gradient needs BSF_FIX128");
   if (h->R < 0) return fail(h, BSF_ESTATE, "padding unknown: plan or filter first");
   if ((rc = reset_counters(h, true, false))) return rc;
   cudaError_t e = cudaSuccess;
@@ -1074,38 +1127,23 @@ static int backward_d2(bsf_t h, const float* gout, long long ldg, const float* c
     if (e != cudaSuccess) return cuda_fail(h, e, "continuous-step vjp");
   }
   if (!gimg) return BSF_OK;
-  if ((rc = ensure_workspace(h))) return rc;
-  const size_t G_bytes = (size_t)h->pitch * h->Hp * 16, Gx_bytes = (size_t)h->Hp * h->W * 16;
-  if (h->G_bytes != G_bytes || h->Gx_bytes != Gx_bytes) {
-    BSF_CUDA(h, cudaStreamSynchronize(h->stream));
-    if (h->G) cudaFree(h->G);
-    if (h->Gx) cudaFree(h->Gx);
-    h->G = h->Gx = nullptr;
-    h->G_bytes = h->Gx_bytes = 0;
-    BSF_CUDA(h, cudaMalloc(&h->G, G_bytes));
-    BSF_CUDA(h, cudaMalloc(&h->Gx, Gx_bytes));
-    h->G_bytes = G_bytes;
-    h->Gx_bytes = Gx_bytes;
-  }
+  // the image gradient reads no running sums: 128-bit adjoint sums whatever
+  // the forward's element type
+  if ((rc = ensure_backward_workspace(h, 16))) return rc;
   {
     PhaseTimer t(h, BSF_PHASE_BWD_SCATTER);
     BSF_CUDA(h, cudaMemsetAsync(&h->st->max_absg_bits, 0, sizeof(unsigned), h->stream));
-    BSF_CUDA(h, cudaMemsetAsync(h->G, 0, G_bytes, h->stream));
+    BSF_CUDA(h, cudaMemsetAsync(h->G, 0, h->G_bytes, h->stream));
     e = bsf_launch_gabsmax(gout, ldg, h->H, h->W, h->st, h->stream);
     if (e == cudaSuccess)
-      e = bsf_launch_scatter_d2(h->n, h->G, h->pitch, h->R, cov, cov_kind, gout, ldg, h->H, h->W,
+      e = bsf_launch_scatter_d2(h->n, h->G, h->pitch, h->R, cov, cov_kind, gout, ldg, h->H, h->W, 0, h->H, -1,
                                 h->st, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "continuous-step scatter");
   {
     PhaseTimer t(h, BSF_PHASE_BWD_SCANS);
-    const int skews[3] = {-1, 1, 0};
-    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
-      e = bsf_launch_vscan(BSF_FIX128, h->n, skews[i], true, h->G, h->pitch, h->Hp, h->Wp,
-                           h->scan_chunk, h->agg, h->carry, h->stream);
-    if (e == cudaSuccess) e = bsf_launch_suffix_rows(16, h->n, h->G, h->pitch, h->Hp, h->Wp, h->stream);
+    if ((rc = backward_sums(h, 16, h->Hp))) return rc;
   }
-  if (e != cudaSuccess) return cuda_fail(h, e, "continuous-step adjoint sums");
   {
     PhaseTimer t(h, BSF_PHASE_BWD_FOLD);
     e = bsf_launch_fold128(h->G, h->pitch, h->Hp, h->H, h->W, h->R, h->boundary, h->Gx, gimg, ldgi,
@@ -1129,39 +1167,32 @@ int bsf_filter_backward(bsf_t h, const float* gout, long long ldg, const float* 
   }
   if (!gout || !cov || !gimg) return fail(h, BSF_EINVAL, "NULL gout, cov or gimg");
   if (ldg < h->W || ldgi < h->W) return fail(h, BSF_EINVAL, "leading dimension < W");
-  if ((rc = ensure_backward_workspace(h))) return rc;
-  const size_t G_bytes = h->G_bytes;
+  const int be = grad_elem(h);
+  if ((rc = ensure_backward_workspace(h, be))) return rc;
   if ((rc = reset_counters(h, true, false))) return rc;
   cudaError_t e;
   {
     PhaseTimer t(h, BSF_PHASE_BWD_SCATTER);
     BSF_CUDA(h, cudaMemsetAsync(&h->st->max_absg_bits, 0, sizeof(unsigned), h->stream));
-    BSF_CUDA(h, cudaMemsetAsync(h->G, 0, G_bytes, h->stream));
+    BSF_CUDA(h, cudaMemsetAsync(h->G, 0, h->G_bytes, h->stream));
     e = bsf_launch_gabsmax(gout, ldg, h->H, h->W, h->st, h->stream);
     if (e == cudaSuccess)
-      e = bsf_launch_scatter_d1(h->n, h->G, h->pitch, h->R, cov, cov_kind, h->step_rule, gout, ldg, h->H,
+      e = bsf_launch_scatter_d1(h->n, be, h->G, h->pitch, h->R, cov, cov_kind, h->step_rule, gout, ldg, h->H,
                                 h->W, 0, h->H, -1, h->st, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "backward scatter");
   {
     PhaseTimer t(h, BSF_PHASE_BWD_SCANS);
-    const int skews[3] = {-1, 1, 0};  // transposes in reverse order: d4, d2, d3
-    for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
-      if (h->scan_mode == BSF_SCAN_LOOKBACK)
-        e = bsf_launch_vscan_lb(BSF_FIX64, h->n, skews[i], true, h->short_tiles != 0, h->G, h->pitch,
-                                h->Hp, h->Wp, h->agg, h->carry, h->sync_words, h->wait_limit, 0,
-                                h->st, h->stream);
-      else
-        e = bsf_launch_vscan(BSF_FIX64, h->n, skews[i], true, h->G, h->pitch, h->Hp, h->Wp, h->scan_chunk,
-                             h->agg, h->carry, h->stream);
-    }
-    if (e == cudaSuccess) e = bsf_launch_suffix_rows(8, h->n, h->G, h->pitch, h->Hp, h->Wp, h->stream);
+    if ((rc = backward_sums(h, be, h->Hp))) return rc;
   }
-  if (e != cudaSuccess) return cuda_fail(h, e, "backward running sums");
   {
     PhaseTimer t(h, BSF_PHASE_BWD_FOLD);
-    e = bsf_launch_fold(h->G, h->pitch, h->Hp, h->H, h->W, h->R, h->boundary, h->Gx, gimg, ldgi,
-                        h->st, h->stream);
+    if (be == 16)
+      e = bsf_launch_fold128(h->G, h->pitch, h->Hp, h->H, h->W, h->R, h->boundary, h->Gx, gimg, ldgi, h->st,
+                             h->stream);
+    else
+      e = bsf_launch_fold(h->G, h->pitch, h->Hp, h->H, h->W, h->R, h->boundary, h->Gx, gimg, ldgi,
+                          h->st, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "backward fold");
   if (gcov) BSF_CUDA(h, cudaMemsetAsync(gcov, 0, (size_t)3 * h->H * h->W * sizeof(float), h->stream));
@@ -1202,8 +1233,10 @@ int bsf_get_info(bsf_t h, bsf_info_t* info) {
   info->max_mass = h->plan_mass;
   info->clamp_count = h->host_st.clamp_count;
   info->flags = h->host_st.clamp_count ? BSF_FLAG_CLAMPED : 0u;
-  info->workspace_bytes = (long long)(h->S_bytes + 2 * h->scan_bytes + h->sync_bytes + h->G_bytes + h->Gx_bytes) +
+  info->workspace_bytes = (long long)(h->S_bytes + 2 * h->scan_bytes + h->sync_bytes + h->G_bytes + h->Gx_bytes +
+                                      h->bagg_bytes) +
                           (long long)h->H * h->W * (long long)sizeof(ushort4) + (long long)sizeof(DevStatus);
+  info->grad_elem_bytes = grad_elem(h);
   return BSF_OK;
 }
 

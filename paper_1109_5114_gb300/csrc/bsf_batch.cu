@@ -9,10 +9,18 @@
 // replay it.  The per-image mode runs the same kernels image by image (the
 // baseline the batched form is measured against).
 //
+// BSF_BATCH_PERSISTENT runs the whole batch as one persistent launch
+// (bsf_persistent.cu): resident blocks take work items -- rows, chunks of the
+// vertical directions, tiles of the finite differences -- from one ticket
+// counter, each item waiting (bounded) on a per-image counter of the phase
+// before it; with BSF_BATCH_GRAPH that launch is recorded in a CUDA graph.
+//
 // The autotuner picks the scan chunk height per size class of the padded
-// image (height classes up to 384, 768, 1536 rows and above) by timing the
-// vertical running sums of the class's largest image with each candidate;
-// the choices can be kept in a text cache file between runs.
+// image (height classes up to 384, 768, 1536 rows and above), and the work
+// item shapes of the persistent launch (padded rows per row item, rows of a
+// finite-difference tile) and its blocks per SM, by timing the batch itself
+// (coordinate descent over the candidates, the whole persistent launch as
+// the objective); the choices can be kept in a text cache file between runs.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -54,6 +62,24 @@ struct bsf_batch {
   int tune_chunk[4] = {0, 0, 0, 0};  // per height class; 0 = default
   std::string tune_cache;
   char msg[512] = "ok";
+
+  // the persistent launch
+  PersistentShape pshape{4, 1};
+  int ctas_per_sm = 0;               // 0 = as many as fit
+  int group_mb = 48;                 // running-sum bytes of one image group (0 = one group)
+  int tuned_persist = 0;             // the shape and blocks came from the tuner or its cache
+  int wait_limit = 1 << 22;          // polls of one wait before BSF_ETIMEOUT
+  int test_withhold = 0;
+  std::vector<PersistSegment> psegs;  // kPersistPhases * B segments in ticket order
+  std::vector<int> pcounts;           // items per (image, phase)
+  int ptotal = 0;
+  int ngroups = 0;
+  PersistSegment* d_psegs = nullptr;
+  int* d_pcounts = nullptr;
+  unsigned* d_ctrl = nullptr;        // ticket, then done[B][kPersistPhases]
+  int pgrid = 0;
+  cudaGraph_t pgraph = nullptr;
+  cudaGraphExec_t pexec = nullptr;
 };
 
 namespace {
@@ -85,6 +111,10 @@ void drop_graph(bsf_batch_t b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   b->exec = nullptr;
   b->graph = nullptr;
+  if (b->pexec) cudaGraphExecDestroy(b->pexec);
+  if (b->pgraph) cudaGraphDestroy(b->pgraph);
+  b->pexec = nullptr;
+  b->pgraph = nullptr;
 }
 
 void free_plan(bsf_batch_t b) {
@@ -92,9 +122,15 @@ void free_plan(bsf_batch_t b) {
   if (b->arena) cudaFree(b->arena);
   if (b->d_imgs) cudaFree(b->d_imgs);
   if (b->d_starts) cudaFree(b->d_starts);
+  if (b->d_psegs) cudaFree(b->d_psegs);
+  if (b->d_pcounts) cudaFree(b->d_pcounts);
+  if (b->d_ctrl) cudaFree(b->d_ctrl);
   b->arena = nullptr;
   b->d_imgs = nullptr;
   b->d_starts = nullptr;
+  b->d_psegs = nullptr;
+  b->d_pcounts = nullptr;
+  b->d_ctrl = nullptr;
   b->arena_bytes = 0;
   b->planned = false;
 }
@@ -117,8 +153,15 @@ void load_cache(bsf_batch_t b) {
   char name[256];
   int cls, n, ch;
   const std::string me = gpu_name();
-  while (std::fscanf(f, "%255s %d %d %d", name, &cls, &n, &ch) == 4)
-    if (me == name && n == b->n && cls >= 0 && cls < 4 && ch >= kScanChunkMin) b->tune_chunk[cls] = ch;
+  while (std::fscanf(f, "%255s %d %d %d", name, &cls, &n, &ch) == 4) {
+    if (me != name || n != b->n) continue;
+    if (cls >= 0 && cls < 4 && ch >= kScanChunkMin) b->tune_chunk[cls] = ch;
+    // persistent launch: 100 rows per row item, 101 finite-difference tile rows / 8, 102 blocks per SM
+    if (cls == 100 && ch >= 1 && ch <= 64) { b->pshape.rows_per_item = ch; b->tuned_persist = 1; }
+    if (cls == 101 && ch >= 1 && ch <= 16) { b->pshape.stencil_rows = ch; b->tuned_persist = 1; }
+    if (cls == 102 && ch >= 1 && ch <= 32) { b->ctas_per_sm = ch; b->tuned_persist = 1; }
+    if (cls == 103 && ch >= 0 && ch <= 4096) { b->group_mb = ch; b->tuned_persist = 1; }
+  }
   std::fclose(f);
 }
 
@@ -129,6 +172,12 @@ void save_cache(bsf_batch_t b) {
   const std::string me = gpu_name();
   for (int c = 0; c < 4; ++c)
     if (b->tune_chunk[c]) std::fprintf(f, "%s %d %d %d\n", me.c_str(), c, b->n, b->tune_chunk[c]);
+  if (b->tuned_persist) {
+    std::fprintf(f, "%s 100 %d %d\n", me.c_str(), b->n, b->pshape.rows_per_item);
+    std::fprintf(f, "%s 101 %d %d\n", me.c_str(), b->n, b->pshape.stencil_rows);
+    std::fprintf(f, "%s 102 %d %d\n", me.c_str(), b->n, b->ctas_per_sm);
+    std::fprintf(f, "%s 103 %d %d\n", me.c_str(), b->n, b->group_mb);
+  }
   std::fclose(f);
 }
 
@@ -182,6 +231,168 @@ bool same_descs(bsf_batch_t b, int B, const bsf_image_desc* d) {
       return false;
   }
   return true;
+}
+
+// Block offsets of the batched launches and work items of the persistent
+// launch, from the images' chunk heights and the persistent item shape;
+// uploads them (synchronous) and drops recorded graphs.
+int layout(bsf_batch_t b) {
+  const int B = b->B;
+  b->starts.assign(kBatchPhases * (B + 1), 0);
+  for (int p = 0; p < kBatchPhases; ++p) {
+    long long acc = 0;
+    for (int i = 0; i < B; ++i) {
+      b->starts[p * (B + 1) + i] = (int)acc;
+      const BatchImage& im = b->imgs[i];
+      long long blocks = 0;
+      if (p == kBatchRows) {
+        blocks = im.Hp;
+      } else if (p == kBatchStencil) {
+        blocks = (long long)((im.W + 31) / 32) * ((im.H + 7) / 8);
+      } else {
+        const int Nu = p == kBatchV0 ? im.Wp : im.Wp + im.Hp - 1;
+        blocks = (long long)((Nu + 127) / 128) * ((im.Hp + im.ch - 1) / im.ch);
+      }
+      if (acc + blocks >= (1LL << 31)) return bfail(b, BSF_EINVAL, "batch too large");
+      acc += blocks;
+    }
+    b->starts[p * (B + 1) + B] = (int)acc;
+    b->totals[p] = (int)acc;
+  }
+  // the persistent launch: groups of consecutive images whose running sums
+  // fit group_mb, tickets group by group and within a group phase by phase
+  b->pcounts.assign((size_t)B * kPersistPhases, 0);
+  for (int i = 0; i < B; ++i)
+    for (int p = 0; p < kPersistPhases; ++p)
+      b->pcounts[i * kPersistPhases + p] = bsf_persistent_items(b->imgs[i], p, b->pshape);
+  b->psegs.clear();
+  b->ngroups = 0;
+  long long ticket = 0;
+  const double budget = b->group_mb > 0 ? b->group_mb * 1048576.0 : 1e300;
+  for (int g0 = 0; g0 < B;) {
+    int g1 = g0 + 1;
+    double bytes = (double)b->imgs[g0].pitch * b->imgs[g0].Hp * 8;
+    while (g1 < B && bytes + (double)b->imgs[g1].pitch * b->imgs[g1].Hp * 8 <= budget) {
+      bytes += (double)b->imgs[g1].pitch * b->imgs[g1].Hp * 8;
+      ++g1;
+    }
+    for (int p = 0; p < kPersistPhases; ++p)
+      for (int i = g0; i < g1; ++i) {
+        b->psegs.push_back(PersistSegment{(int)ticket, p, i, 0});
+        ticket += b->pcounts[i * kPersistPhases + p];
+        if (ticket >= (1LL << 31)) return bfail(b, BSF_EINVAL, "batch too large");
+      }
+    ++b->ngroups;
+    g0 = g1;
+  }
+  b->ptotal = (int)ticket;
+  int dev = 0, sms = 0;
+  BSF_BCUDA(b, cudaGetDevice(&dev));
+  BSF_BCUDA(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int occ = bsf_persistent_occupancy(b->n, b->dtype, b->out_dtype);
+  const int per_sm = b->ctas_per_sm > 0 && b->ctas_per_sm < occ ? b->ctas_per_sm : occ;
+  b->pgrid = sms * per_sm;
+  drop_graph(b);
+  BSF_BCUDA(b, cudaMemcpyAsync(b->d_imgs, b->imgs.data(), sizeof(BatchImage) * B, cudaMemcpyHostToDevice,
+                               b->stream));
+  BSF_BCUDA(b, cudaMemcpyAsync(b->d_starts, b->starts.data(), sizeof(int) * b->starts.size(),
+                               cudaMemcpyHostToDevice, b->stream));
+  BSF_BCUDA(b, cudaMemcpyAsync(b->d_psegs, b->psegs.data(), sizeof(PersistSegment) * b->psegs.size(),
+                               cudaMemcpyHostToDevice, b->stream));
+  BSF_BCUDA(b, cudaMemcpyAsync(b->d_pcounts, b->pcounts.data(), sizeof(int) * b->pcounts.size(),
+                               cudaMemcpyHostToDevice, b->stream));
+  BSF_BCUDA(b, cudaStreamSynchronize(b->stream));
+  return BSF_OK;
+}
+
+// The persistent launch: zero the ticket and the phase counters, then one
+// kernel over every work item of the batch.
+int run_persistent(bsf_batch_t b) {
+  BSF_BCUDA(b, cudaMemsetAsync(b->d_ctrl, 0, sizeof(unsigned) * (1 + (size_t)b->B * kPersistPhases),
+                               b->stream));
+  cudaError_t e = bsf_launch_batch_persistent(b->n, b->dtype, b->out_dtype, b->pgrid, b->d_imgs, b->d_psegs,
+                                              (int)b->psegs.size(), b->d_pcounts, b->ptotal, b->pshape,
+                                              b->boundary, b->q, b->step_rule,
+                                              b->d_ctrl, b->d_ctrl + 1, b->wait_limit, b->test_withhold, b->st,
+                                              b->stream);
+  if (e != cudaSuccess) return bfail(b, BSF_ECUDA, "persistent launch: %s", cudaGetErrorString(e));
+  return BSF_OK;
+}
+
+// Median-free timing of the persistent launch: the mean of `reps` launches
+// after one untimed one.
+int time_persistent(bsf_batch_t b, int reps, float* ms) {
+  cudaEvent_t e0, e1;
+  BSF_BCUDA(b, cudaEventCreate(&e0));
+  BSF_BCUDA(b, cudaEventCreate(&e1));
+  int rc = reset_status(b);
+  if (!rc) rc = run_persistent(b);
+  if (!rc) rc = cudaEventRecord(e0, b->stream) == cudaSuccess ? BSF_OK : BSF_ECUDA;
+  for (int r = 0; r < reps && !rc; ++r) rc = run_persistent(b);
+  if (!rc) rc = cudaEventRecord(e1, b->stream) == cudaSuccess ? BSF_OK : BSF_ECUDA;
+  if (!rc) rc = cudaEventSynchronize(e1) == cudaSuccess ? BSF_OK : BSF_ECUDA;
+  float t = 0.f;
+  if (!rc) cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return bfail(b, rc, "timing the persistent launch");
+  *ms = t / reps;
+  return BSF_OK;
+}
+
+// Coordinate descent over the persistent launch's parameters with the batch
+// itself as the workload: the scan chunk height of each height class present,
+// padded rows per row item, rows of a finite-difference tile (in units of 8)
+// and blocks per SM.  Two passes over the parameters; each candidate is kept
+// only if it is faster than the best so far.
+int tune_persistent(bsf_batch_t b) {
+  const int occ = bsf_persistent_occupancy(b->n, b->dtype, b->out_dtype);
+  bool present[4] = {false, false, false, false};
+  for (const BatchImage& im : b->imgs) present[height_class(im.Hp)] = true;
+  float best = 0.f;
+  int rc;
+  if ((rc = time_persistent(b, 3, &best))) return rc;
+  auto try_value = [&](int* slot, int value, bool chunk_class, int cls) -> int {
+    const int old = *slot;
+    if (value == old) return BSF_OK;
+    *slot = value;
+    if (chunk_class)
+      for (BatchImage& im : b->imgs)
+        if (height_class(im.Hp) == cls) im.ch = value;
+    int r = layout(b);
+    float t = 0.f;
+    if (!r) r = time_persistent(b, 3, &t);
+    if (r) return r;
+    if (t < best) {
+      best = t;
+      return BSF_OK;
+    }
+    *slot = old;
+    if (chunk_class)
+      for (BatchImage& im : b->imgs)
+        if (height_class(im.Hp) == cls) im.ch = old;
+    return layout(b);
+  };
+  for (int c = 0; c < 4; ++c)
+    if (!b->tune_chunk[c]) b->tune_chunk[c] = kScanChunk;
+  if (b->ctas_per_sm <= 0) b->ctas_per_sm = occ;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int cls = 0; cls < 4; ++cls) {
+      if (!present[cls]) continue;
+      for (int ch : {32, 48, 64, 96, 128})
+        if ((rc = try_value(&b->tune_chunk[cls], ch, true, cls))) return rc;
+    }
+    for (int r : {1, 2, 4, 8})
+      if ((rc = try_value(&b->pshape.rows_per_item, r, false, 0))) return rc;
+    for (int r : {1, 2, 4})
+      if ((rc = try_value(&b->pshape.stencil_rows, r, false, 0))) return rc;
+    for (int k = 1; k <= occ; ++k)
+      if ((rc = try_value(&b->ctas_per_sm, k, false, 0))) return rc;
+    for (int mb : {16, 32, 48, 64, 96, 0})
+      if ((rc = try_value(&b->group_mb, mb, false, 0))) return rc;
+  }
+  b->tuned_persist = 1;
+  return BSF_OK;
 }
 
 }  // namespace
@@ -367,36 +578,18 @@ int bsf_batch_plan(bsf_batch_t b, int B, const bsf_image_desc* descs, int flags)
     save_cache(b);
   }
 
-  // block offsets per phase
-  b->starts.assign(kBatchPhases * (B + 1), 0);
-  for (int p = 0; p < kBatchPhases; ++p) {
-    int acc = 0;
-    for (int i = 0; i < B; ++i) {
-      b->starts[p * (B + 1) + i] = acc;
-      const BatchImage& im = b->imgs[i];
-      long long blocks = 0;
-      if (p == kBatchRows) {
-        blocks = im.Hp;
-      } else if (p == kBatchStencil) {
-        blocks = (long long)((im.W + 31) / 32) * ((im.H + 7) / 8);
-      } else {
-        const int Nu = p == kBatchV0 ? im.Wp : im.Wp + im.Hp - 1;
-        blocks = (long long)((Nu + 127) / 128) * ((im.Hp + im.ch - 1) / im.ch);
-      }
-      if (acc + blocks >= (1LL << 31)) return bfail(b, BSF_EINVAL, "batch too large");
-      acc += (int)blocks;
-    }
-    b->starts[p * (B + 1) + B] = acc;
-    b->totals[p] = acc;
-  }
   BSF_BCUDA(b, cudaMalloc(&b->d_imgs, sizeof(BatchImage) * B));
-  BSF_BCUDA(b, cudaMalloc(&b->d_starts, sizeof(int) * b->starts.size()));
-  BSF_BCUDA(b, cudaMemcpyAsync(b->d_imgs, b->imgs.data(), sizeof(BatchImage) * B,
-                               cudaMemcpyHostToDevice, b->stream));
-  BSF_BCUDA(b, cudaMemcpyAsync(b->d_starts, b->starts.data(), sizeof(int) * b->starts.size(),
-                               cudaMemcpyHostToDevice, b->stream));
-  BSF_BCUDA(b, cudaStreamSynchronize(b->stream));
+  BSF_BCUDA(b, cudaMalloc(&b->d_starts, sizeof(int) * kBatchPhases * (B + 1)));
+  BSF_BCUDA(b, cudaMalloc(&b->d_psegs, sizeof(PersistSegment) * kPersistPhases * (size_t)B));
+  BSF_BCUDA(b, cudaMalloc(&b->d_pcounts, sizeof(int) * kPersistPhases * (size_t)B));
+  BSF_BCUDA(b, cudaMalloc(&b->d_ctrl, sizeof(unsigned) * (1 + (size_t)B * kPersistPhases)));
+  int rc = layout(b);
+  if (rc) return rc;
   b->planned = true;
+  if ((flags & BSF_BATCH_AUTOTUNE) && !b->tuned_persist) {
+    if ((rc = tune_persistent(b))) return rc;
+    save_cache(b);
+  }
   return BSF_OK;
 }
 
@@ -405,6 +598,25 @@ int bsf_filter_batched(bsf_batch_t b, int B, const bsf_image_desc* descs, int fl
   if (!b->planned || !same_descs(b, B, descs))
     return bfail(b, BSF_ESTATE, "descriptors differ from the plan (call bsf_batch_plan)");
   int rc;
+  if (flags & BSF_BATCH_PERSISTENT) {
+    if (flags & BSF_BATCH_GRAPH) {
+      if (!b->pexec) {
+        BSF_BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        rc = reset_status(b);
+        if (!rc) rc = run_persistent(b);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+        if (e != cudaSuccess) return bfail(b, BSF_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        b->pgraph = g;
+        BSF_BCUDA(b, cudaGraphInstantiate(&b->pexec, b->pgraph, 0));
+      }
+      BSF_BCUDA(b, cudaGraphLaunch(b->pexec, b->stream));
+      return BSF_OK;
+    }
+    if ((rc = reset_status(b))) return rc;
+    return run_persistent(b);
+  }
   if (flags & BSF_BATCH_PER_IMAGE) {
     if ((rc = reset_status(b))) return rc;
     for (int i = 0; i < B; ++i)
@@ -452,6 +664,52 @@ int bsf_batch_get_info(bsf_batch_t b, bsf_batch_info_t* info) {
   for (const BatchImage& im : b->imgs) px += (long long)im.H * im.W;
   info->pixels = px;
   info->graph_ready = b->exec != nullptr;
+  info->persist_items = b->ptotal;
+  info->persist_groups = b->ngroups;
+  info->persist_grid = b->pgrid;
+  info->rows_per_item = b->pshape.rows_per_item;
+  info->stencil_tile_rows = 8 * b->pshape.stencil_rows;
+  info->persist_graph_ready = b->pexec != nullptr;
+  return BSF_OK;
+}
+
+int bsf_batch_set_option(bsf_batch_t b, int option, long long value) {
+  if (!b) return BSF_EINVAL;
+  switch (option) {
+    case BSF_BATCH_OPT_WAIT_LIMIT:
+      if (value < 1 || value > (1LL << 30)) return bfail(b, BSF_EINVAL, "wait limit outside [1, 2^30]");
+      b->wait_limit = (int)value;
+      break;
+    case BSF_BATCH_OPT_TEST_WITHHOLD:
+      b->test_withhold = value != 0;
+      break;
+    case BSF_BATCH_OPT_ROWS_PER_ITEM:
+      if (value < 1 || value > 64) return bfail(b, BSF_EINVAL, "rows per item outside [1, 64]");
+      b->pshape.rows_per_item = (int)value;
+      b->tuned_persist = 1;
+      break;
+    case BSF_BATCH_OPT_STENCIL_ROWS:
+      if (value != 8 && value != 16 && value != 32 && value != 64)
+        return bfail(b, BSF_EINVAL, "finite-difference tile rows must be 8, 16, 32 or 64");
+      b->pshape.stencil_rows = (int)value / 8;
+      b->tuned_persist = 1;
+      break;
+    case BSF_BATCH_OPT_GROUP_MB:
+      if (value < 0 || value > 4096) return bfail(b, BSF_EINVAL, "group budget outside [0, 4096] MiB");
+      b->group_mb = (int)value;
+      b->tuned_persist = 1;
+      break;
+    case BSF_BATCH_OPT_BLOCKS_PER_SM:
+      if (value < 0 || value > 32) return bfail(b, BSF_EINVAL, "blocks per SM outside [0, 32]");
+      b->ctas_per_sm = (int)value;
+      b->tuned_persist = value != 0;
+      break;
+    default:
+      return bfail(b, BSF_EINVAL, "unknown batch option %d", option);
+  }
+  drop_graph(b);  // the recorded launches carry the old parameters
+  if (b->planned && option != BSF_BATCH_OPT_WAIT_LIMIT && option != BSF_BATCH_OPT_TEST_WITHHOLD)
+    return layout(b);
   return BSF_OK;
 }
 

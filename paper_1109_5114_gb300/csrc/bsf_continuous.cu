@@ -64,10 +64,15 @@ template <int NF> __device__ __forceinline__ int tap_weight(unsigned th, int i) 
 // so lane x + 1 adds it to its own through a shuffle and one 128-bit add
 // serves both (n = 2: samples 0/1 and 3/4 pair up, n = 1: 0/1 and 2/3).  The
 // low-word atomics of a group are all issued before their high-word adds.
+// Pixels of image rows [row0, row0 + rows) scatter into G, whose padded row
+// 0 is image row row0 - R (the whole image: row0 = 0, rows = H); qg_given >=
+// 0 fixes the fraction bits of the weights, -1 takes them from the device
+// maximum of |gout|.
 template <int NF>
 __global__ void __launch_bounds__(128)
 k_scatter_d2(u128* __restrict__ G, long long pitch, int R, const float* __restrict__ cov, int kind,
-             const float* __restrict__ gout, long long ldg, int H, int W, DevStatus* st) {
+             const float* __restrict__ gout, long long ldg, int H, int W, int row0, int rows, int qg_given,
+             DevStatus* st) {
   using P = Pattern<NF>;
   constexpr int NP = P::NP;
   // the pairs along d1: (first, second) sample indices
@@ -75,12 +80,12 @@ k_scatter_d2(u128* __restrict__ G, long long pitch, int R, const float* __restri
   const int lane = threadIdx.x;
   const int x = blockIdx.x * 32 + lane;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (y >= H) return;  // uniform across the warp
+  if (y >= rows) return;  // uniform across the warp
   const bool in = x < W;
   int Hq[4] = {kHalf, kHalf, kHalf, kHalf};
   u128 g = 0;
   if (in) {
-    const long long HW = (long long)H * W, i = (long long)y * W + x;
+    const long long HW = (long long)H * W, i = (long long)(row0 + y) * W + x;
     float C11, C12, C22;
     load_cov(cov, kind, HW, i, C11, C12, C22);
     int flags, reach;
@@ -88,8 +93,8 @@ k_scatter_d2(u128* __restrict__ G, long long pitch, int R, const float* __restri
     pixel_steps_d2(C11, C12, C22, NF, R, Hq, lam, flags, reach);
     u128 M = 1;
     for (int k = 0; k < 4; ++k) M *= (u128)d2_mass(Hq[k], NF);
-    const int qg = grad_q128(st->max_absg_bits);
-    const float xg = __fmul_rn(gout[(long long)y * ldg + x], bsf_pow2_f32(qg));  // exact scaling
+    const int qg = qg_given >= 0 ? qg_given : grad_q128(st->max_absg_bits);
+    const float xg = __fmul_rn(gout[(long long)(row0 + y) * ldg + x], bsf_pow2_f32(qg));  // exact scaling
     bool ok;
     g = bsf_quantize_f32<u128>(__fdiv_rn(xg, bsf_rn32_u(M)), 0, ok);
     if (!ok) bsf_set_error(st, BSF_EOVERFLOW);
@@ -251,12 +256,14 @@ cudaError_t bsf_launch_jacobian_vjp(const float* gout, long long ldg, const floa
 
 cudaError_t bsf_launch_scatter_d2(int n, void* G, long long pitch, int R, const float* cov,
                                   int cov_kind, const float* gout, long long ldg, int H, int W,
-                                  DevStatus* st, cudaStream_t s) {
-  const dim3 block(32, 4), grid((W + 31) / 32, (H + 3) / 4);
+                                  int row0, int rows, int qg, DevStatus* st, cudaStream_t s) {
+  const dim3 block(32, 4), grid((W + 31) / 32, (rows + 3) / 4);
   if (n == 1)
-    k_scatter_d2<1><<<grid, block, 0, s>>>((u128*)G, pitch, R, cov, cov_kind, gout, ldg, H, W, st);
+    k_scatter_d2<1><<<grid, block, 0, s>>>((u128*)G, pitch, R, cov, cov_kind, gout, ldg, H, W, row0, rows, qg,
+                                           st);
   else if (n == 2)
-    k_scatter_d2<2><<<grid, block, 0, s>>>((u128*)G, pitch, R, cov, cov_kind, gout, ldg, H, W, st);
+    k_scatter_d2<2><<<grid, block, 0, s>>>((u128*)G, pitch, R, cov, cov_kind, gout, ldg, H, W, row0, rows, qg,
+                                           st);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();

@@ -105,6 +105,22 @@ template <> __device__ __forceinline__ u128 bsf_load<u128>(const u128* p) {
   return ((u128)v.y << 64) | (u128)v.x;
 }
 
+// Loads of data that other blocks of the same launch wrote (persistent
+// kernels): bsf_load_coherent reads at L2 (the point of coherence) and leaves
+// L1 alone; bsf_load_weak is a plain L1-cached load, valid for data that no
+// block of the launch writes after the reader's acquire (no L1 line of it was
+// filled earlier in the launch).
+template <typename T> __device__ __forceinline__ T bsf_load_coherent(const T* p);
+template <> __device__ __forceinline__ uint64_t bsf_load_coherent<uint64_t>(const uint64_t* p) {
+  return __ldcg(reinterpret_cast<const unsigned long long*>(p));
+}
+template <typename T> __device__ __forceinline__ T bsf_load_weak(const T* p);
+template <> __device__ __forceinline__ uint64_t bsf_load_weak<uint64_t>(const uint64_t* p) {
+  unsigned long long v;
+  asm volatile("ld.global.ca.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+
 template <typename T> __device__ __forceinline__ T bsf_shfl_up(T v, int d);
 template <> __device__ __forceinline__ double bsf_shfl_up<double>(double v, int d) {
   return __shfl_up_sync(0xffffffffu, v, d);

@@ -61,26 +61,34 @@ cudaError_t bsf_launch_vscan_lb(int prec, int n, int skew, bool reverse, bool sh
 cudaError_t bsf_launch_suffix_rows(int elem_bytes, int n, void* S, long long pitch, int Hp, int Wp,
                                    cudaStream_t s);
 
-// Backward of the D1 filter (uint64): max|gout| reduction, tap scatter into G
-// (zeroed by the caller), extension fold of G (via Gx: [Hp][W]) into gimg.
+// Backward of the D1 filter (uint64, or uint128 for contexts with 128-bit
+// running sums): max|gout| reduction, tap scatter into G (zeroed by the
+// caller), extension fold of G (via Gx: [Hp][W]) into gimg.  elem_bytes (8
+// or 16) is the adjoint element width.
 cudaError_t bsf_launch_gabsmax(const float* gout, long long ldg, int H, int W, DevStatus* st,
                                cudaStream_t s);
 // Scatter of the pixels of rows [row0, row0 + rows) into G (the band's padded
 // rows); qg >= 0 fixes the weights' fraction bits, -1 takes them from the
 // device maximum of |gout| (bsf_launch_gabsmax).
-cudaError_t bsf_launch_scatter_d1(int n, void* G, long long pitch, int R, const float* cov,
+cudaError_t bsf_launch_scatter_d1(int n, int elem_bytes, void* G, long long pitch, int R, const float* cov,
                                   int cov_kind, int rule, const float* gout, long long ldg, int H,
                                   int W, int row0, int rows, int qg, DevStatus* st, cudaStream_t s);
 // Band fold: G's Hb padded rows (row 0 = image row row0 - R) folded by the
-// extension rule into image rows [a0, a1) as exact int64 sums (acc, lda per row).
-cudaError_t bsf_launch_fold_band(const void* G, long long pitch, int Hb, int H, int W, int R,
-                                 int row0, int boundary, void* Gx, int a0, int a1, long long* acc,
+// extension rule into image rows [a0, a1) as exact sums (acc: elements of
+// elem_bytes, two's complement, lda elements per row).
+cudaError_t bsf_launch_fold_band(int elem_bytes, const void* G, long long pitch, int Hb, int H, int W, int R,
+                                 int row0, int boundary, void* Gx, int a0, int a1, void* acc,
                                  long long lda, cudaStream_t s);
+// acc += halo modulo 2^(8 elem_bytes), rows x W.
+cudaError_t bsf_launch_add_rows(int elem_bytes, void* acc, long long lda, const void* halo, long long ldh,
+                                int rows, int W, cudaStream_t s);
 // gimg = RN32(acc) 2^-qg, rows x W.
-cudaError_t bsf_launch_grad_finalize(const long long* acc, long long lda, int rows, int W, int qg,
+cudaError_t bsf_launch_grad_finalize(int elem_bytes, const void* acc, long long lda, int rows, int W, int qg,
                                      float* gimg, long long ldo, cudaStream_t s);
-// qg = 54 - ceil(log2 m) of the float32 value of m, clamped to [0, 100].
+// qg = 54 - ceil(log2 m) of the float32 value of m, clamped to [0, 100]
+// (64-bit adjoint sums); the 128-bit sums' rule 118 - ceil(log2 m) in [0, 126].
 int bsf_grad_q_host(double m);
+int bsf_grad_q_host_wide(double m);
 cudaError_t bsf_launch_fold(const void* G, long long pitch, int Hp, int H, int W, int R,
                             int boundary, void* Gx, float* gimg, long long ldo, const DevStatus* st,
                             cudaStream_t s);
@@ -102,6 +110,31 @@ struct BatchImage {
 // Phases with their own block ranges: starts[phase * (B + 1) + i] is the first
 // block of image i (starts[... + B] = total blocks).
 enum { kBatchRows = 0, kBatchV0 = 1, kBatchVp = 2, kBatchVm = 3, kBatchStencil = 4, kBatchPhases = 5 };
+
+// The persistent batch kernel (bsf_persistent.cu): eight phases of work
+// items (rows, three vertical directions in two passes each, finite
+// differences).  A segment is the run of tickets of one image's items of one
+// phase; segments are sorted by their first ticket.  counts[i * 8 + p] is
+// the number of items of image i in phase p, and done holds one counter per
+// image and phase (zeroed, as the ticket, before each launch).
+constexpr int kPersistPhases = 8;
+struct PersistentShape {
+  int rows_per_item;  // padded rows of one item of the row phase
+  int stencil_rows;   // a finite-difference item is 32 x (8 stencil_rows) pixels
+};
+struct PersistSegment {
+  int first;  // first ticket
+  int phase;
+  int image;
+  int pad;
+};
+int bsf_persistent_items(const BatchImage& im, int phase, PersistentShape shp);
+int bsf_persistent_occupancy(int n, int dtype, int out_dtype);
+cudaError_t bsf_launch_batch_persistent(int n, int dtype, int out_dtype, int grid, const BatchImage* imgs,
+                                        const PersistSegment* segs, int nseg, const int* counts, int total,
+                                        PersistentShape shp,
+                                        int boundary, int q, int rule, unsigned* ticket, unsigned* done,
+                                        int wait_limit, int test_withhold, DevStatus* st, cudaStream_t s);
 
 cudaError_t bsf_launch_batch_rows(int n, int dtype, const BatchImage* imgs, const int* starts, int B,
                                   int total, int boundary, int q, DevStatus* st, cudaStream_t s);
@@ -132,7 +165,7 @@ cudaError_t bsf_launch_stencil_d2(int prec, int n, int mode, const void* S, long
 // qg from the device maximum of |gout| (bsf_launch_gabsmax).
 cudaError_t bsf_launch_scatter_d2(int n, void* G, long long pitch, int R, const float* cov,
                                   int cov_kind, const float* gout, long long ldg, int H, int W,
-                                  DevStatus* st, cudaStream_t s);
+                                  int row0, int rows, int qg, DevStatus* st, cudaStream_t s);
 cudaError_t bsf_launch_fold128(const void* G, long long pitch, int Hp, int H, int W, int R,
                                int boundary, void* Gx, float* gimg, long long ldo, const DevStatus* st,
                                cudaStream_t s);

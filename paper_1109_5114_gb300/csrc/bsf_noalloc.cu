@@ -17,6 +17,12 @@
 // is a stand-in symbol).  The first call on each device looks its device
 // address up with cudaGetSymbolAddress while that device is current; that
 // first call should therefore happen before any stream capture begins.
+// Under CUDA's lazy module loading (the default since CUDA 12.2) this file's
+// module, and with it the 24 MiB array, is loaded by that first lookup, which
+// can also synchronise the device: a caller that will hand all remaining
+// device memory to its own pool should make one small warm-up call on each
+// device at start-up, before reserving the pool (or run with
+// CUDA_MODULE_LOADING=EAGER, which loads every module at context creation).
 #include <cstring>
 #include <mutex>
 
@@ -68,15 +74,14 @@ extern "C" int bsf_filter_noalloc(const void* img, int dtype, long long ld, int 
   if (out_dtype != BSF_F32 && out_dtype != BSF_F64) return BSF_EINVAL;
   if (ld < W || ldo < W || reach < 3 * n || frac_bits < 0 || frac_bits > 62) return BSF_EINVAL;
 
-  // carve the scratch: status | S [Hp][pitch] | agg | carry
+  // carve the scratch: status | S [Hp][pitch] | chunk aggregates of the vertical sums
   const long long Hp = (long long)H + 2LL * reach, Wp = (long long)W + 2LL * reach;
   const long long pitch = round_up((size_t)Wp, 32);
   const long long nchunks = (Hp + kNoallocChunk - 1) / kNoallocChunk;
   const size_t off_S = round_up(sizeof(DevStatus), 256);
   const size_t scan_bytes = (size_t)nchunks * n * (size_t)(Wp + Hp - 1) * 8;
   const size_t off_agg = off_S + round_up((size_t)pitch * Hp * 8, 256);
-  const size_t off_carry = off_agg + round_up(scan_bytes, 256);
-  const size_t need = off_carry + scan_bytes;
+  const size_t need = off_agg + scan_bytes;
   if ((long long)H * W > (1LL << 24) || Hp * pitch > (1LL << 24) || need > kScratchBytes)
     return BSF_ERANGE;  // larger than the static workspace (24 MiB)
 
@@ -87,27 +92,32 @@ extern "C" int bsf_filter_noalloc(const void* img, int dtype, long long ld, int 
   DevStatus* st = reinterpret_cast<DevStatus*>(b);
   void* S = b + off_S;
   void* agg = b + off_agg;
-  void* carry = b + off_carry;
 
+  // once anything is queued, a failure still waits for the queued work, so
+  // that no kernel of this call touches the shared array after the return
+  auto fail_after_queue = [s]() {
+    (void)cudaStreamSynchronize(s);
+    return BSF_ECUDA;
+  };
   // the status word must start from zero; everything else is fully written
   // before it is read
-  if (cudaMemsetAsync(st, 0, sizeof(DevStatus), s) != cudaSuccess) return BSF_ECUDA;
+  if (cudaMemsetAsync(st, 0, sizeof(DevStatus), s) != cudaSuccess) return fail_after_queue();
   if (bsf_launch_scan_rows(BSF_FIX64, n, img, dtype, ld, H, W, reach, 0, boundary, frac_bits, S, pitch,
                            (int)Hp, (int)Wp, st, s) != cudaSuccess)
-    return BSF_ECUDA;
+    return fail_after_queue();
   const int skews[3] = {0, 1, -1};
   for (int i = 0; i < 3; ++i)
-    if (bsf_launch_vscan(BSF_FIX64, n, skews[i], false, S, pitch, (int)Hp, (int)Wp, kNoallocChunk, agg, carry, s) !=
-        cudaSuccess)
-      return BSF_ECUDA;
+    if (bsf_launch_vscan(BSF_FIX64, n, skews[i], false, S, pitch, (int)Hp, (int)Wp, kNoallocChunk, agg, nullptr,
+                         s) != cudaSuccess)
+      return fail_after_queue();
   if (bsf_launch_stencil_d1(BSF_FIX64, n, S, pitch, reach, cov, BSF_COV_C, BSF_STEP_D1, H, W, 0, H, frac_bits, out,
                             out_dtype, ldo, st, s) != cudaSuccess)
-    return BSF_ECUDA;
+    return fail_after_queue();
 
   // synchronous: report the device-side status of this call
   DevStatus host{};
   if (cudaMemcpyAsync(&host, st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    return BSF_ECUDA;
+    return fail_after_queue();
   if (cudaStreamSynchronize(s) != cudaSuccess) return BSF_ECUDA;
   return host.err;
 }

@@ -30,7 +30,16 @@ namespace {
 // number of t_k equal to 1, so the 81 taps go into five sums G_j (16, 32,
 // 24, 8 and 1 taps) and acc = G0 - 2 (G1 - 2 (G2 - 2 (G3 - 2 G4))): 80 + 8
 // additions against the nested form's 120, with the same result modulo 2^b.
-template <typename T, bool SH>
+// SH: 0 = global memory through the read-only path, 1 = shared memory,
+// 2 = global memory by plain loads (data written earlier in the same launch).
+template <typename T, int SH>
+__device__ __forceinline__ T tap_load(const T* __restrict__ S, int i) {
+  if constexpr (SH == 1) return S[i];
+  else if constexpr (SH == 2) return bsf_load_weak(S + i);
+  else return bsf_load(S + i);
+}
+
+template <typename T, int SH>
 __device__ __forceinline__ T comb2_by_coefficient(const T* __restrict__ S, int idx, const int* s) {
   T G[5];
 #pragma unroll
@@ -44,10 +53,7 @@ __device__ __forceinline__ T comb2_by_coefficient(const T* __restrict__ S, int i
 #pragma unroll
         for (int t1 = 0; t1 < 3; ++t1) {
           const int i = idx - t1 * s[0] - t2 * s[1] - t3 * s[2] - t4 * s[3];
-          T v;
-          if constexpr (SH) v = S[i];
-          else v = bsf_load(S + i);
-          G[(t1 == 1) + (t2 == 1) + (t3 == 1) + (t4 == 1)] += v;
+          G[(t1 == 1) + (t2 == 1) + (t3 == 1) + (t4 == 1)] += tap_load<T, SH>(S, i);
         }
   T a = G[4];
 #pragma unroll
@@ -60,14 +66,13 @@ __device__ __forceinline__ T comb2_by_coefficient(const T* __restrict__ S, int i
 // the difference along direction LVL-1 (stride s[LVL-1] elements) to level
 // LVL-1, and level 0 loads one element.  Order 2 on the integer element
 // types takes the grouped form above.
-// SH: S lies in shared memory (plain loads) instead of global memory.
-template <typename T, int NF, int LVL, bool SH = false>
+// SH: where S lies and how it is loaded (tap_load).
+template <typename T, int NF, int LVL, int SH = 0>
 __device__ __forceinline__ T comb(const T* __restrict__ S, int idx, const int* s) {
   if constexpr (LVL == 4 && NF == 2 && IsFixed<T>::value) {
     return comb2_by_coefficient<T, SH>(S, idx, s);
   } else if constexpr (LVL == 0) {
-    if constexpr (SH) return S[idx];
-    else return bsf_load(S + idx);
+    return tap_load<T, SH>(S, idx);
   } else {
     const int sk = s[LVL - 1];
     const T v0 = comb<T, NF, LVL - 1, SH>(S, idx, s);
@@ -187,17 +192,25 @@ __device__ __forceinline__ void finish_pixel(T acc, const int* L, float maxq, fl
 // e3 = (-1,2), e4 = (-2,1); BSF_DIRS_PAIR chooses per pixel between S
 // (Cartesian running sums) and S2 (running sums of the second set), which
 // share one pitch.
-template <typename T, int NF, typename Out, int DS = BSF_DIRS_CARTESIAN>
+// LD: the load mode of the taps (tap_load); (tx, ty) the thread's place in a
+// block of 32 x bdy pixels (default: the launch's thread indices).
+template <typename T, int NF, typename Out, int DS = BSF_DIRS_CARTESIAN, int LD = 0>
 __device__ __forceinline__ void stencil_d1_body(const T* __restrict__ S, const T* __restrict__ S2,
                                                 long long pitch, int R,
                                                 const float* __restrict__ cov, int kind, int rule, int H,
                                                 int W, int row0, int rows, float scale_f,
                                                 double scale_d, Out* __restrict__ out,
-                                                long long ldo, DevStatus* st, int bx, int by) {
+                                                long long ldo, DevStatus* st, int bx, int by,
+                                                int tx = -1, int ty = 0, int bdy = 0) {
   // pixel (x, row0 + y) of an H x W image; rows [row0, row0 + rows) are
   // filtered from running sums whose padded row 0 is image row row0 - R
-  const int x = bx * 32 + threadIdx.x;
-  const int y = by * blockDim.y + threadIdx.y;
+  if (tx < 0) {
+    tx = threadIdx.x;
+    ty = threadIdx.y;
+    bdy = blockDim.y;
+  }
+  const int x = bx * 32 + tx;
+  const int y = by * bdy + ty;
   if (x >= W || y >= rows) return;
   const long long HW = (long long)H * W, i = (long long)(row0 + y) * W + x;
   int L[4], flags, reach;
@@ -226,7 +239,7 @@ __device__ __forceinline__ void stencil_d1_body(const T* __restrict__ S, const T
             c4 = NF * (L4w - 1) / 2;
   const int base = (y + R) * p32 + (x + R) + c1 * e1 + c2 * e2 + c3 * e3 + c4 * e4;
   const int s[4] = {L1 * e1, L2 * e2, L3 * e3, L4w * e4};
-  const T acc = comb<T, NF, 4>(Sp, base, s);
+  const T acc = comb<T, NF, 4, LD>(Sp, base, s);
   finish_pixel<T, NF, Out>(acc, L, __uint_as_float(st->max_absq_bits) + 1.f, scale_f, scale_d,
                            out + (long long)(y) * ldo + x, st);
 }

@@ -129,7 +129,8 @@ def test_fix32_argument_errors():
         bsf.BoxSplineFilter(H, W, 2, "symmetric", precision=FIX32, frac_bits=31)
     f = bsf.BoxSplineFilter(H, W, 2, "symmetric", precision=FIX32, frac_bits=0)
     f.filter(torch.zeros((H, W), dtype=torch.uint8, device="cuda"), cov)
-    with pytest.raises(bsf.BsfError):
-        f.backward(torch.ones((H, W), device="cuda"), cov)
+    # the backward reads no running sums: 64-bit adjoint sums on a 32-bit context
+    g, _ = f.backward(torch.ones((H, W), device="cuda"), cov)
     torch.cuda.synchronize()
+    assert f.status() == 0 and torch.isfinite(g).all()
     f.close()

@@ -73,3 +73,28 @@ def test_grad_frac_bits():
     assert backward.grad_frac_bits(0.5) == 55
     assert backward.grad_frac_bits(0.0) == 54
     assert backward.grad_frac_bits(2.0 ** 60) == 0
+
+
+def test_grad_frac_bits_wide():
+    assert backward.grad_frac_bits_wide(1.0) == 118
+    assert backward.grad_frac_bits_wide(1.5) == 117
+    assert backward.grad_frac_bits_wide(2.0 ** -20) == 126
+    assert backward.grad_frac_bits_wide(2.0 ** 120) == 0
+
+
+def test_wide_format_keeps_large_kernels_accurate():
+    # kernel masses near 2^60 (n = 3, steps ~ 40): the 64-bit format's weights
+    # 2^54 gout / D round to a few units and lose the gradient, the 128-bit
+    # format keeps it to float32 accuracy against the float64 adjoint
+    H, W, n, boundary = 7, 9, 3, 2
+    rng = np.random.default_rng(11)
+    gout = rng.normal(size=(H, W)).astype(np.float32)
+    cov = wl.random_cov_field(H, W, seed=12, sigma_range=(24.0, 28.0), rho_range=(1.0, 2.0))
+    L, _ = params.integer_steps(cov[0], cov[1], cov[2], n)
+    assert max(kernels.kernel_mass(L[:, y, x], n) for y in range(H) for x in range(W)) > 2 ** 55
+    exact = backward.adjoint_f64(gout.astype(np.float64), L, n, boundary)
+    wide = backward.adjoint_direct_wide(gout, L, n, boundary)
+    scale = np.abs(exact).max()
+    np.testing.assert_allclose(wide, exact, rtol=2e-6, atol=2e-6 * scale)
+    narrow = backward.adjoint_direct(gout, L, n, boundary, backward.grad_frac_bits(np.abs(gout).max()))
+    assert np.abs(narrow - exact).max() > 1e-3 * scale
