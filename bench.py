@@ -15,8 +15,15 @@ events on the launch stream.  The e2e figure times the same call with the
 image and covariance copied from pinned host memory and the output copied
 back, inside the timed region.
 
+The default line also carries the batching workload (64 images of uneven
+sizes, key batch64) and the differentiation workload (8 x 1024^2, continuous
+steps, image and field gradients, key diff8x1024), a few steps each, and the
+CPU baseline: the oracle on all host cores (row bands with their halos) and
+on one core, and the direct definition on sampled pixels.
+
 --impl reference times the CPU oracle (oracle.modular, the running-sum
-pipeline in exact integer arithmetic) on a bounded band of the same workload.
+pipeline in exact integer arithmetic) on all host cores over the same
+workload.
 
 Prints one JSON line.  Under torchrun (N > 1) every rank filters its own
 replica (no data exchange: the single-image path does not shard here) and
@@ -151,6 +158,14 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+def init_group(world: int):
+    """NCCL process group of the replicas (once; nested runs reuse it)."""
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group("nccl")
+
+
 def barrier(world: int):
     if world > 1:
         import torch.distributed as dist
@@ -163,9 +178,7 @@ def run_gpu(args):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    init_group(world)
     img, cov = make_inputs()
     vmax = float(np.abs(img).max())
     d_img = torch.from_numpy(img).cuda()
@@ -472,7 +485,8 @@ def run_gpu(args):
     e2e_ms = max_over_ranks(e2e_ms, world)
     h2d = img.nbytes + cov.nbytes
     d2h = H * W * 4
-    assert np.array_equal(h_out.numpy(), d_out.cpu().numpy())  # same result both ways
+    gpu_out = d_out.cpu().numpy()
+    assert np.array_equal(h_out.numpy(), gpu_out)  # same result both ways
     f.close()
 
     # the host link's own floor for the same bytes: the uploads and the
@@ -500,6 +514,12 @@ def run_gpu(args):
         link_ms += (time.perf_counter() - t0) * 1e3
     link_ms /= 5
     del d_img_l, d_cov_l
+
+    # ---- the batching and differentiation workloads, a few steps each ------
+    sub = argparse.Namespace(**vars(args))
+    sub.steps, sub.warmup = min(args.steps, 10), 3
+    batch_line = run_batch(sub)
+    diff_line = run_diff(sub)
 
     if rank != 0:
         if world > 1:
@@ -582,9 +602,15 @@ def run_gpu(args):
                      "algorithmic_bytes_per_launch": alg[dominant]},
         "phases_ms": {k: round(v[0], 5) for k, v in per_phase.items()},
         "clocks": clocks,
+        "batch64": {k: batch_line[k] for k in ("value", "unit", "ms_per_step", "steps", "config", "modes",
+                                                "gpu_launches_per_step")},
+        "diff8x1024": {"fwd_bwd": {k: diff_line[k] for k in ("value", "unit", "ms_per_step", "phases_ms")},
+                       "fwd": diff_line["fwd"], "steps": diff_line["steps"], "config": diff_line["config"],
+                       "loss": diff_line["loss"], "clocks": diff_line["clocks"]},
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(img, cov, info.R, info.frac_bits, rows=args.cpu_rows)
+        line["cpu_baseline"] = cpu_baseline(img, cov, info.R, info.frac_bits, rows=args.cpu_rows,
+                                            gpu_out=gpu_out)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -616,17 +642,99 @@ def kernel_revision(kernel: str = "stencil") -> str:
     return hsh.hexdigest()[:16]
 
 
-def cpu_baseline(img, cov, R, q, rows: int = 512):
-    """The oracle's running-sum pipeline on a band of `rows` rows of the workload."""
+def host_cores() -> int:
+    return len(os.sched_getaffinity(0))
+
+
+def _oracle_band(job):
+    """One process's share of the all-cores oracle run: rows [y0, y1) of the
+    workload from the band [y0 - R, y1 + R) (clipped to the image), whose
+    running sums restart above it; the rows it returns are exact (every tap
+    of a band pixel lies in the padded band)."""
+    y0, y1, R, q = job
     from oracle import modular
+    img, cov = _WORKER_INPUTS
+    a0, a1 = max(0, y0 - R), min(H, y1 + R)
+    out = modular.filter_modular(np.ascontiguousarray(img[a0:a1]), np.ascontiguousarray(cov[:, a0:a1]),
+                                 ORDER, 2, q=q, bits=64, out_dtype=np.float32, R=R)
+    return y0, out[y0 - a0:y1 - a0]
+
+
+class OraclePool:
+    """The oracle's running-sum pipeline on all host cores, one process per
+    core (spawned: the workers start fresh interpreters, no CUDA state),
+    each filtering a band of rows with its R-row halos."""
+
+    def __init__(self, cores=None):
+        import multiprocessing as mp
+        self.cores = cores or host_cores()
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_init_worker)
+
+    def run(self, rows: int, R: int, q: int):
+        """Filter image rows [0, rows) split into one band per core; returns
+        (output rows, seconds)."""
+        per = -(-rows // self.cores)
+        jobs = [(y, min(rows, y + per), R, q) for y in range(0, rows, per)]
+        t0 = time.perf_counter()
+        parts = self.pool.map(_oracle_band, jobs)
+        dt = time.perf_counter() - t0
+        parts.sort(key=lambda p: p[0])
+        return np.concatenate([p[1] for p in parts]), dt
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+_WORKER_INPUTS = None
+
+
+def _init_worker():
+    """Once per worker process, outside the timed runs: one thread for numpy,
+    the oracle imported, the workload generated."""
+    global _WORKER_INPUTS
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    import oracle  # noqa: F401
+    _WORKER_INPUTS = make_inputs()
+
+
+def cpu_baseline(img, cov, R, q, rows: int = 512, gpu_out=None):
+    """The oracle timed on the host: its running-sum pipeline (oracle.modular)
+    on all cores by row bands over the whole image, and on one core on a band
+    of `rows` rows; the definition (oracle.kernels.correlate_f64, the direct
+    correlation) on a seeded sample of pixels, extrapolated."""
+    from oracle import kernels, modular, params
+    pool = OraclePool()
+    pool.run(H, R, q)                      # warm-up: the workers' start-up is not timed
+    full, dt_all = pool.run(H, R, q)
+    pool.close()
+    if gpu_out is not None:   # the oracle's whole image is the GPU's, bit for bit
+        assert np.array_equal(full, gpu_out)
     band_img = np.ascontiguousarray(img[:rows])
     band_cov = np.ascontiguousarray(cov[:, :rows])
     t0 = time.perf_counter()
     modular.filter_modular(band_img, band_cov, ORDER, 2, q=q, bits=64, out_dtype=np.float32, R=R)
-    dt = time.perf_counter() - t0
-    return {"value": round(rows * W / dt / 1e6, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"rows 0-{rows - 1} of the 2048x2048 workload ({rows}x{W} px), "
-                      f"oracle.modular (numpy, one thread), {dt:.1f} s"}
+    dt1 = time.perf_counter() - t0
+    rng = np.random.default_rng(0)
+    pix = sorted({(int(y), int(x)) for y, x in zip(rng.integers(0, H, 400), rng.integers(0, W, 400))})
+    L, _ = params.integer_steps(cov[0], cov[1], cov[2], ORDER)
+    t0 = time.perf_counter()
+    kernels.correlate_f64(img.astype(np.float64), L, ORDER, 2, pixels=pix)
+    dtd = time.perf_counter() - t0
+    return {"value": round(H * W / dt_all / 1e6, 4), "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+            "sample": f"the whole 2048x2048 workload, oracle.modular (numpy) in {pool.cores} spawned "
+                      f"processes, one band of rows each with its R-row halos, {dt_all:.2f} s "
+                      f"(os.sched_getaffinity: {pool.cores} cores)"
+                      + ("; equal to the GPU output bit for bit" if gpu_out is not None else ""),
+            "one_core": {"value": round(rows * W / dt1 / 1e6, 4), "unit": UNIT, "cores": 1,
+                         "sample": f"rows 0-{rows - 1} ({rows}x{W} px), oracle.modular, one process, "
+                                   f"{dt1:.1f} s"},
+            "direct_definition": {"value": round(len(pix) / dtd / 1e6, 6), "unit": UNIT, "cores": 1,
+                                  "sample": f"{len(pix)} seeded pixels of the workload, "
+                                            f"oracle.kernels.correlate_f64 (the direct correlation "
+                                            f"with each pixel's kernel), {dtd:.1f} s, extrapolated "
+                                            "per pixel"}}
 
 
 # the fraction bits the GPU arm's automatic rule picks on this workload (its
@@ -645,28 +753,27 @@ def run_reference(args):
     if rank != 0:
         return None
     img, cov = make_inputs()
-    from oracle import modular, params
-    L, _ = params.integer_steps(cov[0], cov[1], cov[2], ORDER)
-    R = max(int(params.reach(L, ORDER).max()), 3 * ORDER)
+    from oracle import config
+    R = config.padding(cov, ORDER)
     q = REF_FRAC_BITS
-    rows = args.ref_rows
-    band_img = np.ascontiguousarray(img[:rows])
-    band_cov = np.ascontiguousarray(cov[:, :rows])
+    rows = args.ref_rows if args.ref_rows > 0 else H
+    pool = OraclePool()
     for _ in range(args.warmup):
-        modular.filter_modular(band_img, band_cov, ORDER, 2, q=q, bits=64, out_dtype=np.float32, R=R)
-    t0 = time.perf_counter()
+        pool.run(rows, R, q)
+    dt = 0.0
     for _ in range(args.steps):
-        modular.filter_modular(band_img, band_cov, ORDER, 2, q=q, bits=64, out_dtype=np.float32, R=R)
-    dt = time.perf_counter() - t0
+        dt += pool.run(rows, R, q)[1]
+    pool.close()
     value = rows * W * args.steps / dt / 1e6
-    sample = f"rows 0-{rows - 1} of the 2048x2048 workload ({rows}x{W} px) per step"
+    sample = (f"rows 0-{rows - 1} of the 2048x2048 workload ({rows}x{W} px) per step, oracle.modular in "
+              f"{pool.cores} spawned processes (one band of rows each, with R-row halos)")
     return {
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": workload_config(q, R, 1, "not applicable (host cores)"),
-        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": pool.cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -679,17 +786,18 @@ BATCH_WORKLOAD = ("batch: 64 fp32 blob images, sides log-uniform in [128, 2048] 
 
 
 def run_batch(args):
-    """Batched form: one launch per phase over 64 images, replayed from a CUDA
-    graph, against the same kernels launched image by image."""
+    """Batched form of 64 images: the whole batch as one persistent launch
+    replayed from a CUDA graph (the headline, its parameters autotuned on the
+    batch), against one launch per phase over the batch (direct and
+    graph-replayed), the persistent launch without a graph, and the same
+    kernels launched image by image."""
     import torch
     import workloads as wl
     from paper_1109_5114_gb300 import bsf
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    init_group(world)
     sizes = wl.batch_sizes_loguniform(64, seed=1, lo=128, hi=2048)
     imgs, covs = [], []
     for i, (h, w) in enumerate(sizes):
@@ -706,8 +814,10 @@ def run_batch(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     bstream = bf.stream()
     results = {}
+    P = bsf.BSF_BATCH_PERSISTENT
     for name, flags in [("per_image", bsf.BSF_BATCH_PER_IMAGE), ("batched", 0),
-                        ("graph", bsf.BSF_BATCH_GRAPH)]:
+                        ("graph", bsf.BSF_BATCH_GRAPH), ("persistent", P),
+                        ("persistent_graph", P | bsf.BSF_BATCH_GRAPH)]:
         for _ in range(args.warmup):
             bf.run(flags)
         assert bf.status() == 0
@@ -727,10 +837,11 @@ def run_batch(args):
         total = max_over_ranks(total, world)
         results[name] = {"ms_per_step": round(total / args.steps, 4),
                          "value": round(world * px * args.steps / (total * 1e-3) / 1e6, 2)}
+    info = bf.info()
     bf.close()
     if rank != 0:
         return None
-    g = results["graph"]
+    g = results["persistent_graph"]
     return {
         "metric": METRIC, "value": g["value"], "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": g["ms_per_step"],
@@ -738,11 +849,18 @@ def run_batch(args):
         "data": "synthetic",
         "config": {"workload": BATCH_WORKLOAD, "images": len(sizes), "pixels": px, "n": ORDER,
                    "frac_bits": info.frac_bits, "scan_chunk_by_class": list(info.scan_chunk),
+                   "persistent": {"work_items": info.persist_items, "blocks": info.persist_grid,
+                                  "image_groups": info.persist_groups,
+                                  "rows_per_item": info.rows_per_item,
+                                  "stencil_tile": f"32x{info.stencil_tile_rows}",
+                                  "tuned": "coordinate descent over chunk heights, item shapes and "
+                                           "blocks per SM, timing the batch itself"},
                    "arena_bytes": info.arena_bytes,
                    "l2": "flushed before every timed step (256 MB write)",
                    "parallelism": f"replicas x{world}"},
         "modes": results,
-        "gpu_launches_per_step": {"per_image": 8 * len(sizes), "batched": 8, "graph": 1},
+        "gpu_launches_per_step": {"per_image": 8 * len(sizes), "batched": 8, "graph": 8,
+                                  "persistent": 1, "persistent_graph": 1},
     }
 
 
@@ -776,9 +894,7 @@ def run_diff(args):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    init_group(world)
     side = 1024
     imgs, fields, tfields = diff_inputs(8, side)
     vmax = max(float(np.abs(im).max()) for im in imgs)
@@ -893,9 +1009,7 @@ def run_single(args):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    init_group(world)
     if args.workload == "tiles4096":
         h = w = 4096
         img = torch.from_numpy(wl.blob_image_u8(h, w, seed=0)).cuda()
@@ -967,8 +1081,8 @@ def main():
     ap.add_argument("--impl", default="bsf", choices=["bsf", "reference"])
     ap.add_argument("--cpu-rows", type=int, default=1536,
                     help="rows of the workload the cpu_baseline leg filters (one pass)")
-    ap.add_argument("--ref-rows", type=int, default=256,
-                    help="rows of the workload each --impl reference step filters")
+    ap.add_argument("--ref-rows", type=int, default=0,
+                    help="rows of the workload each --impl reference step filters (0: all)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="spacevariant2048",
                     choices=["spacevariant2048", "batch64", "diff8x1024", "tiles4096", "sampled2048",
