@@ -38,11 +38,57 @@ k_scan_rows(const In* __restrict__ img, long long ld, int H, int W, int R, int r
                                blockIdx.x);
 }
 
+// The reduction pass with each chunk's rows split between two warps: a block
+// is 64 lines x 2 halves of the chunk (warps 0, 1: the first half of lines
+// 0..31, 32..63; warps 2, 3: the second half); the halves' zero-carry states
+// combine through shared memory.  Twice the threads of one line per thread,
+// for twice the loads in flight.
 template <typename T, int NF, int SKEW, bool REV>
 __global__ void __launch_bounds__(128)
 k_vscan_agg(const T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, int Nu, int ch,
             T* __restrict__ agg) {
-  vscan_agg_body<T, NF, SKEW, REV>(S, pitch, Hp, Wp, umin, Nu, ch, agg, blockIdx.x, blockIdx.y);
+  // raw storage: the element types with constructors are written before read
+  __shared__ __align__(16) unsigned char s_raw[NF * 64 * sizeof(T)];
+  T(*s_half)[64] = reinterpret_cast<T(*)[64]>(s_raw);
+  const int t = threadIdx.x, line = t & 63, half = t >> 6;
+  const int ui = blockIdx.x * 64 + line;
+  const int c = blockIdx.y;
+  const int y0 = c * ch, y1 = min(y0 + ch, Hp), ym = min(y0 + (ch + 1) / 2, y1);
+  const int r0 = half ? ym : y0, r1 = half ? y1 : ym;  // this thread's rows (scan order)
+  T s[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) s[f] = 0;
+  if (ui < Nu) {
+    const int u = umin + ui;
+    const int A = REV ? u + SKEW * (Hp - 1) : u;
+    constexpr int B = REV ? -SKEW : SKEW;
+    int lo = r0, hi = r1;
+    line_rows<B>(A, Wp, lo, hi);
+    if (lo < hi) {
+#pragma unroll 8
+      for (int yl = lo; yl < hi; ++yl) {
+        const int y = REV ? Hp - 1 - yl : yl;
+        const T v = S[(long long)y * pitch + (A + B * yl)];
+        s[0] += v;
+#pragma unroll
+        for (int f = 1; f < NF; ++f) s[f] += s[f - 1];
+      }
+      zero_rows_transfer<T, NF>(s, r1 - hi);  // leading zero rows leave the state at zero
+    }
+  }
+  if (half) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) s_half[f][line] = s[f];
+  }
+  __syncthreads();
+  if (!half && ui < Nu) {
+    T a[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) a[f] = s_half[f][line];
+    tp_combine<T, NF>(s, a, y1 - ym);  // the first half, then the second half's rows
+#pragma unroll
+    for (int f = 0; f < NF; ++f) agg[((long long)c * NF + f) * Nu + ui] = s[f];
+  }
 }
 
 template <typename T, int NF, int SKEW, bool REV>
@@ -305,7 +351,8 @@ cudaError_t launch_v_t(T* S, long long pitch, int Hp, int Wp, int ch, T* agg, T*
   const int threads = 128;
   dim3 grid((Nu + threads - 1) / threads, nchunks);
   (void)carry;
-  k_vscan_agg<T, NF, SKEW, REV><<<grid, threads, 0, s>>>(S, pitch, Hp, Wp, umin, Nu, ch, agg);
+  k_vscan_agg<T, NF, SKEW, REV><<<dim3((Nu + 63) / 64, nchunks), threads, 0, s>>>(S, pitch, Hp, Wp, umin, Nu, ch,
+                                                                                 agg);
   k_vscan_apply<T, NF, SKEW, REV><<<grid, threads, 0, s>>>(S, pitch, Hp, Wp, umin, Nu, ch, agg);
   return cudaGetLastError();
 }
