@@ -38,23 +38,28 @@ k_scan_rows(const In* __restrict__ img, long long ld, int H, int W, int R, int r
                                blockIdx.x);
 }
 
-// The reduction pass with each chunk's rows split between two warps: a block
-// is 64 lines x 2 halves of the chunk (warps 0, 1: the first half of lines
-// 0..31, 32..63; warps 2, 3: the second half); the halves' zero-carry states
-// combine through shared memory.  Twice the threads of one line per thread,
-// for twice the loads in flight.
-template <typename T, int NF, int SKEW, bool REV>
+// The reduction pass with each chunk's rows split between SPLIT warps of a
+// block of 128 threads: 128 / SPLIT lines x SPLIT consecutive parts of the
+// chunk (thread t: line t mod (128 / SPLIT), part t div (128 / SPLIT)); the
+// parts' zero-carry states combine in order through shared memory.  SPLIT
+// times the threads of one line per thread, for SPLIT times the loads in
+// flight.
+constexpr int kAggSplit = 2;
+
+template <typename T, int NF, int SKEW, bool REV, int SPLIT>
 __global__ void __launch_bounds__(128)
 k_vscan_agg(const T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, int Nu, int ch,
             T* __restrict__ agg) {
+  constexpr int LINES = 128 / SPLIT;
   // raw storage: the element types with constructors are written before read
-  __shared__ __align__(16) unsigned char s_raw[NF * 64 * sizeof(T)];
-  T(*s_half)[64] = reinterpret_cast<T(*)[64]>(s_raw);
-  const int t = threadIdx.x, line = t & 63, half = t >> 6;
-  const int ui = blockIdx.x * 64 + line;
+  __shared__ __align__(16) unsigned char s_raw[SPLIT * NF * LINES * sizeof(T)];
+  T(*s_part)[NF][LINES] = reinterpret_cast<T(*)[NF][LINES]>(s_raw);
+  const int t = threadIdx.x, line = t % LINES, part = t / LINES;
+  const int ui = blockIdx.x * LINES + line;
   const int c = blockIdx.y;
-  const int y0 = c * ch, y1 = min(y0 + ch, Hp), ym = min(y0 + (ch + 1) / 2, y1);
-  const int r0 = half ? ym : y0, r1 = half ? y1 : ym;  // this thread's rows (scan order)
+  const int y0 = c * ch, y1 = min(y0 + ch, Hp);
+  const int plen = (ch + SPLIT - 1) / SPLIT;
+  const int r0 = min(y0 + part * plen, y1), r1 = min(r0 + plen, y1);  // this thread's rows (scan order)
   T s[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) s[f] = 0;
@@ -76,16 +81,17 @@ k_vscan_agg(const T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, 
       zero_rows_transfer<T, NF>(s, r1 - hi);  // leading zero rows leave the state at zero
     }
   }
-  if (half) {
 #pragma unroll
-    for (int f = 0; f < NF; ++f) s_half[f][line] = s[f];
-  }
+  for (int f = 0; f < NF; ++f) s_part[part][f][line] = s[f];
   __syncthreads();
-  if (!half && ui < Nu) {
-    T a[NF];
+  if (part == 0 && ui < Nu) {
+    for (int p = 1; p < SPLIT; ++p) {
+      const int q0 = min(y0 + p * plen, y1), q1 = min(q0 + plen, y1);
+      T a[NF];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) a[f] = s_half[f][line];
-    tp_combine<T, NF>(s, a, y1 - ym);  // the first half, then the second half's rows
+      for (int f = 0; f < NF; ++f) a[f] = s_part[p][f][line];
+      tp_combine<T, NF>(s, a, q1 - q0);  // the parts before, then part p's rows
+    }
 #pragma unroll
     for (int f = 0; f < NF; ++f) agg[((long long)c * NF + f) * Nu + ui] = s[f];
   }
@@ -351,8 +357,8 @@ cudaError_t launch_v_t(T* S, long long pitch, int Hp, int Wp, int ch, T* agg, T*
   const int threads = 128;
   dim3 grid((Nu + threads - 1) / threads, nchunks);
   (void)carry;
-  k_vscan_agg<T, NF, SKEW, REV><<<dim3((Nu + 63) / 64, nchunks), threads, 0, s>>>(S, pitch, Hp, Wp, umin, Nu, ch,
-                                                                                 agg);
+  k_vscan_agg<T, NF, SKEW, REV, kAggSplit><<<dim3((Nu + 128 / kAggSplit - 1) / (128 / kAggSplit), nchunks), threads, 0,
+                                             s>>>(S, pitch, Hp, Wp, umin, Nu, ch, agg);
   k_vscan_apply<T, NF, SKEW, REV><<<grid, threads, 0, s>>>(S, pitch, Hp, Wp, umin, Nu, ch, agg);
   return cudaGetLastError();
 }

@@ -276,6 +276,7 @@ __device__ __forceinline__ void tp_combine(T* s, const T* a, long long m) {
 // then the chunk is rescanned in batches of kApplyBatch rows whose loads are
 // all issued before any store.
 constexpr int kApplyBatch = 16;
+constexpr int kFoldUnroll = 4;  // earlier chunks' states loaded per round trip
 
 template <typename T, int NF, int SKEW, bool REV, typename Load = BsfLoadCached>
 __device__ __forceinline__ void vscan_apply_body(T* __restrict__ S, long long pitch, int Hp, int Wp,
@@ -297,7 +298,7 @@ __device__ __forceinline__ void vscan_apply_body(T* __restrict__ S, long long pi
   T s[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) s[f] = 0;
-#pragma unroll 4
+#pragma unroll kFoldUnroll
   for (int j = glo / ch; j < c; ++j) {
     T a[NF];
 #pragma unroll
