@@ -29,13 +29,33 @@
 
 namespace {
 
+// A block takes rows yp = blockIdx.x, + gridDim.x, ... and updates the status
+// word once for all of them.
 template <typename T, int NF, typename In, int V>
 __global__ void __launch_bounds__(kRowThreads)
 k_scan_rows(const In* __restrict__ img, long long ld, int H, int W, int R, int row0, int boundary,
             float scale_f, int q, T* __restrict__ S, long long pitch, int Hp, int Wp,
             DevStatus* st) {
-  scan_rows_body<T, NF, In, V>(img, ld, H, W, R, row0, boundary, scale_f, q, S, pitch, Hp, Wp, st,
-                               blockIdx.x);
+  float amax = 0.f;
+  bool all_ok = true;
+  for (int yp = blockIdx.x; yp < Hp; yp += gridDim.x)
+    scan_row<T, NF, In, V>(img, ld, H, W, R, row0, boundary, scale_f, q, S, pitch, Wp, yp, amax, all_ok);
+  scan_rows_status(amax, all_ok, st);
+}
+
+// blocks of the row pass: this many per SM (each loops over rows)
+constexpr int kRowBlocksPerSM = 8;
+
+int rows_grid(int Hp) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+      sms = 152;
+  }
+  const int g = sms * kRowBlocksPerSM;
+  return Hp < g ? Hp : g;
 }
 
 // The reduction pass with each chunk's rows split between SPLIT warps of a
@@ -314,15 +334,15 @@ cudaError_t launch_rows_v(const void* img, int dtype, long long ld, int H, int W
   const float scale = ldexpf(1.f, q);  // q <= 100: a normal float32
   switch (dtype) {
     case BSF_U8:
-      k_scan_rows<T, NF, uint8_t, V><<<Hp, kRowThreads, 0, s>>>(
+      k_scan_rows<T, NF, uint8_t, V><<<rows_grid(Hp), kRowThreads, 0, s>>>(
           (const uint8_t*)img, ld, H, W, R, row0, boundary, scale, q, S, pitch, Hp, Wp, st);
       break;
     case BSF_F32:
-      k_scan_rows<T, NF, float, V><<<Hp, kRowThreads, 0, s>>>(
+      k_scan_rows<T, NF, float, V><<<rows_grid(Hp), kRowThreads, 0, s>>>(
           (const float*)img, ld, H, W, R, row0, boundary, scale, q, S, pitch, Hp, Wp, st);
       break;
     case BSF_F64:
-      k_scan_rows<T, NF, double, V><<<Hp, kRowThreads, 0, s>>>(
+      k_scan_rows<T, NF, double, V><<<rows_grid(Hp), kRowThreads, 0, s>>>(
           (const double*)img, ld, H, W, R, row0, boundary, scale, q, S, pitch, Hp, Wp, st);
       break;
     default: return cudaErrorInvalidValue;

@@ -145,17 +145,13 @@ __device__ __forceinline__ void row_scan_segments(int Wp, Load&& load, Store&& s
 }
 
 template <typename T, int NF, typename In, int V>
-__device__ __forceinline__ void scan_rows_body(const In* __restrict__ img, long long ld, int H,
-                                               int W, int R, int row0, int boundary, float scale_f,
-                                               int q, T* __restrict__ S, long long pitch, int Hp,
-                                               int Wp, DevStatus* st, int yp) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void scan_row(const In* __restrict__ img, long long ld, int H, int W, int R,
+                                         int row0, int boundary, float scale_f, int q, T* __restrict__ S,
+                                         long long pitch, int Wp, int yp, float& amax, bool& all_ok) {
   bool yvalid;
   const int ys = bsf_map_index(row0 + yp - R, H, boundary, yvalid);  // row0: first row of a band
   const In* src = img + (long long)ys * ld;
   T* row = S + (long long)yp * pitch;
-  float amax = 0.f;
-  bool all_ok = true;
   row_scan_segments<T, NF, V>(
       Wp,
       [&](int xp) -> T {
@@ -171,8 +167,12 @@ __device__ __forceinline__ void scan_rows_body(const In* __restrict__ img, long 
         return q_;
       },
       [&](int xp, T val) { row[xp] = val; });
-  // one atomic per block on the status word (per-warp atomics on one word
-  // serialise)
+}
+
+// The status of a block's rows: max |Q| and overflow, one atomic per block
+// on the status word (per-warp atomics on one word serialise).
+__device__ __forceinline__ void scan_rows_status(float amax, bool all_ok, DevStatus* st) {
+  const int lane = threadIdx.x & 31;
   __shared__ float s_amax[kRowThreads / 32];
   __shared__ int s_bad;
   if (threadIdx.x == 0) s_bad = 0;
@@ -190,6 +190,19 @@ __device__ __forceinline__ void scan_rows_body(const In* __restrict__ img, long 
     if (m > 0.f) bsf_atomic_max_pos_float(&st->max_absq_bits, m);
     if (s_bad) bsf_set_error(st, BSF_EOVERFLOW);
   }
+}
+
+// One padded row yp: extension, quantisation, n-fold sums, and the block's
+// status update.
+template <typename T, int NF, typename In, int V>
+__device__ __forceinline__ void scan_rows_body(const In* __restrict__ img, long long ld, int H,
+                                               int W, int R, int row0, int boundary, float scale_f,
+                                               int q, T* __restrict__ S, long long pitch, int Hp,
+                                               int Wp, DevStatus* st, int yp) {
+  float amax = 0.f;
+  bool all_ok = true;
+  scan_row<T, NF, In, V>(img, ld, H, W, R, row0, boundary, scale_f, q, S, pitch, Wp, yp, amax, all_ok);
+  scan_rows_status(amax, all_ok, st);
 }
 
 
