@@ -149,7 +149,9 @@ extern "C" {
 #define BSF_PHASE_SECOND      9  /* BSF_DIRS_SECOND / _PAIR: extension + quantisation, then the
                                     running sums along e1..e4 (nine kernels) */
 #define BSF_PHASE_TILES      10  /* the fused tile filter (BSF_OPT_TILES): one kernel */
-#define BSF_NUM_PHASES        11
+#define BSF_PHASE_VJP        11  /* continuous steps: the covariance gradient, from a stored
+                                    Jacobian (bsf_jacobian_vjp) or recomputed (bsf_filter_backward) */
+#define BSF_NUM_PHASES        12
 
 /* options of bsf_set_option */
 #define BSF_OPT_SCAN_MODE    1  /* value BSF_SCAN_THREE_PHASE (default) or BSF_SCAN_LOOKBACK */

@@ -439,7 +439,7 @@ class BoxSplineFilter:
         if rc < 0:
             check(self._h, rc)
         names = ["steps", "rows", "d3", "d2", "d4", "stencil", "bwd_scatter", "bwd_scans", "bwd_fold",
-                 "second", "tiles"]
+                 "second", "tiles", "vjp"]
         return {names[i]: (ms[i], cnt[i]) for i in range(n)}
 
     def status(self) -> int:

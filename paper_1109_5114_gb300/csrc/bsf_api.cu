@@ -955,7 +955,7 @@ int bsf_jacobian_vjp(bsf_t h, const float* gout, long long ldg, const float* jac
   if (!h) return BSF_EINVAL;
   if (!gout || !jac || !gcov) return fail(h, BSF_EINVAL, "NULL gout, jac or gcov");
   if (ldg < h->W || ldj < h->W) return fail(h, BSF_EINVAL, "leading dimension < W");
-  PhaseTimer t(h, BSF_PHASE_BWD_SCATTER);
+  PhaseTimer t(h, BSF_PHASE_VJP);
   cudaError_t e = bsf_launch_jacobian_vjp(gout, ldg, jac, ldj, gcov, h->H, h->W, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "jacobian vjp");
   return BSF_OK;
@@ -1120,7 +1120,7 @@ static int backward_d2(bsf_t h, const float* gout, long long ldg, const float* c
   if (gcov) {
     if (!h->have_S || h->S_R != h->R || h->S_elem != h->elem || h->S_row0 != 0 || h->S_rows != h->H)
       return fail(h, BSF_ESTATE, "no whole-image pre-integration is held");
-    PhaseTimer t(h, BSF_PHASE_BWD_SCATTER);
+    PhaseTimer t(h, BSF_PHASE_VJP);
     e = bsf_launch_stencil_d2(h->precision, h->n, 2, h->S, h->pitch, h->R, cov, cov_kind, h->H, h->W,
                               0, h->H, h->S_q, nullptr, BSF_F32, h->W, gcov, h->W,
                               (long long)h->H * h->W, gout, ldg, h->st, h->stream);
