@@ -1,5 +1,7 @@
 // Dispatch of the continuous-step stencil by element type, and the
 // vector-Jacobian product kernel.  The stencil itself is in bsf_continuous.cuh.
+#include <climits>
+
 #include "bsf_continuous.cuh"
 
 cudaError_t bsf_launch_stencil_d2_u64(int n, int mode, const void* S, long long pitch, int R,
@@ -58,33 +60,18 @@ template <int NF> __device__ __forceinline__ int tap_weight(unsigned th, int i) 
 // Adjoint of the continuous-step taps: each pixel adds g(p) times the
 // product of its four interpolation weights at each of its samples, g(p) =
 // RNE(RN32(RN32(gout 2^qg) / RN32(M))) the quantised normalised weight.
-// A warp is 32 consecutive pixels of one row (blockDim.x == 32).  Along d1
-// the second sample of a bracket pair of lane x falls on the first sample of
-// lane x + 1 when both pixels have the same brackets a0 in every direction,
-// so lane x + 1 adds it to its own through a shuffle and one 128-bit add
-// serves both (n = 2: samples 0/1 and 3/4 pair up, n = 1: 0/1 and 2/3).  The
-// low-word atomics of a group are all issued before their high-word adds.
 // Pixels of image rows [row0, row0 + rows) scatter into G, whose padded row
 // 0 is image row row0 - R (the whole image: row0 = 0, rows = H); qg_given >=
 // 0 fixes the fraction bits of the weights, -1 takes them from the device
 // maximum of |gout|.
-// Six resident blocks per SM asked of the register allocator (80 registers):
-// the scatter waits on its atomics' returns, and more warps in flight hide
-// that latency (1.51 against 1.88 ms per 1024^2 image with the default 126).
+
+// One pixel's weight g and its interpolation brackets a0 / fractions th per
+// direction (identity steps for pixels outside the image or the band).
 template <int NF>
-__global__ void __launch_bounds__(128, 6)
-k_scatter_d2(u128* __restrict__ G, long long pitch, int R, const float* __restrict__ cov, int kind,
-             const float* __restrict__ gout, long long ldg, int H, int W, int row0, int rows, int qg_given,
-             DevStatus* st) {
-  using P = Pattern<NF>;
-  constexpr int NP = P::NP;
-  // the pairs along d1: (first, second) sample indices
-  constexpr int PA0 = 0, PA1 = 1, PB0 = NF == 2 ? 3 : 2, PB1 = NF == 2 ? 4 : 3;
-  const int lane = threadIdx.x;
-  const int x = blockIdx.x * 32 + lane;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (y >= rows) return;  // uniform across the warp
-  const bool in = x < W;
+__device__ __forceinline__ u128 scatter_pixel(const float* __restrict__ cov, int kind,
+                                              const float* __restrict__ gout, long long ldg, int H, int W,
+                                              int R, int row0, int x, int y, bool in, int qg_given,
+                                              DevStatus* st, int a0[4], unsigned th[4]) {
   int Hq[4] = {kHalf, kHalf, kHalf, kHalf};
   u128 g = 0;
   if (in) {
@@ -102,77 +89,184 @@ k_scatter_d2(u128* __restrict__ G, long long pitch, int R, const float* __restri
     g = bsf_quantize_f32<u128>(__fdiv_rn(xg, bsf_rn32_u(M)), 0, ok);
     if (!ok) bsf_set_error(st, BSF_EOVERFLOW);
   }
-  const int p32 = (int)pitch;
-  const int estep[4] = {1, p32 + 1, p32, p32 - 1};
-  int a0[4];
-  unsigned th[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int Q0 = NF == 2 ? 2 * Hq[k] - 1024 : Hq[k] - 512;
     a0[k] = Q0 >> 10;
     th[k] = (unsigned)(Q0 & 1023);
   }
-  // lanes whose brackets agree in every direction share sample positions
-  const unsigned sa = in ? (unsigned)a0[0] | ((unsigned)a0[1] << 16) : 0xffffffffu;
-  const unsigned sb = in ? (unsigned)a0[2] | ((unsigned)a0[3] << 16) : 0xffffffffu;
-  const unsigned la = __shfl_up_sync(0xffffffffu, sa, 1), lb = __shfl_up_sync(0xffffffffu, sb, 1);
-  const unsigned ra = __shfl_down_sync(0xffffffffu, sa, 1), rb = __shfl_down_sync(0xffffffffu, sb, 1);
-  const bool from_left = in && lane > 0 && la == sa && lb == sb;     // take lane - 1's seconds
-  const bool to_right = in && lane < 31 && ra == sa && rb == sb;     // lane + 1 takes mine
-  const int base = (y + R) * p32 + (x + R);
-  // weights of the first direction's samples, and their positions
-  int w1[NP], off1[NP];
+  return g;
+}
+
+// The block's pixels (a tile of kWinTX x kWinTY) first sum their samples in
+// a window of G held in shared memory, then add the window to G: neighbouring
+// pixels' samples fall on the same cells (the fields are smooth, and the 625
+// samples of a pixel sweep a box a few steps wide), so each global 128-bit
+// add carries the sum of many samples.  The window is the bounding box of
+// the tile's samples; a box taller than the window's capacity is covered in
+// row bands, one pass each, every pixel adding only its samples that fall in
+// the band.  A box that would need more than kWinMaxPasses bands falls back
+// to the direct global adds.  Shared words: low and high 64-bit planes of
+// 128-bit cells, the low add returning the old word for the carry.
+constexpr int kWinTX = 32, kWinTY = 8;
+constexpr int kWinCells = 4096;     // 64 KB: three blocks per SM
+constexpr int kWinMaxPasses = 8;
+
+// Sample offsets along one direction: [lo, hi] (a0 >= -1).
+template <int NF> __device__ __forceinline__ int pos_lo(int a0) { return NF == 2 ? -a0 - 3 : -a0 - 2; }
+__device__ __forceinline__ int pos_hi(int a0) { return a0 + 1; }
+
+// Sample i of one direction's adjoint for coefficient c, from u = 1024 c
+// and t = th c: n = 2 weights 1024 - th, th, -2048, th, 1024 - th; n = 1
+// 1024 - th, th, -th, th - 1024 (all modulo 2^128).
+template <int NF> __device__ __forceinline__ u128 dir_value(u128 u, u128 t, int i) {
+  if (NF == 2) return i == 1 || i == 3 ? t : (i == 2 ? (u128)0 - (u << 1) : u - t);
+  return i == 0 ? u - t : (i == 1 ? t : (i == 2 ? (u128)0 - t : t - u));
+}
+
+// One pixel's samples whose rows fall in [0, nr) of a target laid out in
+// rows of `stride` 64-bit word pairs: the shared window (low and high words
+// in two planes, `hi_off` words apart) or G itself (interleaved 128-bit
+// cells: stride 2 pitch, hi_off 1, every row in range).  Row and column of
+// the pixel relative to the target origin: ry, rx.  The low-word add returns
+// the old word, whose carry goes into the high word's add.
+template <int NF>
+__device__ __forceinline__ void deposit_samples(unsigned long long* __restrict__ tgt, int stride, int cellw,
+                                                int hi_off, int nr, int ry, int rx, u128 u4, u128 t4,
+                                                const int a0[4], const unsigned th[4]) {
+  using P = Pattern<NF>;
+  constexpr int NP = P::NP;
+  int off1[NP];
 #pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    w1[i] = tap_weight<NF>(th[0], i);
-    off1[i] = P::pos(a0[0], i);
-  }
+  for (int i = 0; i < NP; ++i) off1[i] = P::pos(a0[0], i) * cellw;
+  const int d2lo = pos_lo<NF>(a0[1]), d2hi = pos_hi(a0[1]);
 #pragma unroll 1
   for (int i4 = 0; i4 < NP; ++i4) {
-    const int w4 = tap_weight<NF>(th[3], i4);
-    const u128 c4 = mul_signed(g, w4);
-    const int b4 = base + P::pos(a0[3], i4) * estep[3];
+    const int p4 = P::pos(a0[3], i4);
+    const u128 c4 = dir_value<NF>(u4, t4, i4);
+    const u128 u3 = c4 << 10, t3 = mul_small(c4, th[2]);
 #pragma unroll 1
     for (int i3 = 0; i3 < NP; ++i3) {
-      const int w3 = tap_weight<NF>(th[2], i3);
-      const u128 c3 = mul_signed(c4, w3);
-      const int b3 = b4 + P::pos(a0[2], i3) * estep[2];
+      const int r3 = ry + p4 + P::pos(a0[2], i3);
+      if (r3 + d2hi < 0 || r3 + d2lo >= nr) continue;  // no d2 sample of the group in range
+      const u128 c3 = dir_value<NF>(u3, t3, i3);
+      const u128 u2 = c3 << 10, t2 = mul_small(c3, th[1]);
 #pragma unroll
       for (int i2 = 0; i2 < NP; ++i2) {
-        const int w2 = tap_weight<NF>(th[1], i2);
-        const u128 c2 = mul_signed(c3, w2);
-        const int b2 = b3 + P::pos(a0[1], i2) * estep[1];
-        u128 v[NP];
+        const int p2 = P::pos(a0[1], i2);
+        const int r = r3 + p2;
+        if ((unsigned)r >= (unsigned)nr) continue;
+        const u128 c2 = dir_value<NF>(u2, t2, i2);
+        const u128 u1 = c2 << 10, t1 = mul_small(c2, th[0]);
+        unsigned long long* q = tgt + (long long)r * stride + (rx + p2 - p4) * cellw;
+        // the samples' words are recomputed for the high adds (fewer live registers)
+        unsigned long long old[NP];
 #pragma unroll
-        for (int i = 0; i < NP; ++i) v[i] = mul_signed(c2, w1[i]);
-        // merge the left neighbour's second samples into my first ones
-        const u128 sA = bsf_shfl_up(v[PA1], 1), sB = bsf_shfl_up(v[PB1], 1);
-        if (from_left) {
-          v[PA0] += sA;
-          v[PB0] += sB;
-        }
-        if (to_right) {
-          v[PA1] = 0;
-          v[PB1] = 0;
-        }
-        // 128-bit adds: every low word first, then the high words with carries
-        unsigned long long old[NP], lo[NP], hi[NP];
-        unsigned long long* q[NP];
+        for (int i = 0; i < NP; ++i) old[i] = atomicAdd(q + off1[i], (unsigned long long)dir_value<NF>(u1, t1, i));
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
-          q[i] = reinterpret_cast<unsigned long long*>(G + b2 + off1[i]);
-          lo[i] = (unsigned long long)v[i];
-          hi[i] = (unsigned long long)(v[i] >> 64);
-          old[i] = (in && v[i] != 0) ? atomicAdd(q[i], lo[i]) : 0ull;
-        }
-#pragma unroll
-        for (int i = 0; i < NP; ++i) {
-          if (!in || v[i] == 0) continue;
-          const unsigned long long h = hi[i] + ((old[i] + lo[i] < old[i]) ? 1ull : 0ull);
-          if (h) atomicAdd(q[i] + 1, h);
+          const u128 v = dir_value<NF>(u1, t1, i);
+          const unsigned long long lo = (unsigned long long)v;
+          const unsigned long long h = (unsigned long long)(v >> 64) + ((old[i] + lo < old[i]) ? 1ull : 0ull);
+          if (h) atomicAdd(q + off1[i] + hi_off, h);
         }
       }
     }
+  }
+}
+
+template <int NF>
+__global__ void __launch_bounds__(kWinTX * kWinTY, 3)
+k_scatter_d2(u128* __restrict__ G, long long pitch, int R, const float* __restrict__ cov, int kind,
+             const float* __restrict__ gout, long long ldg, int H, int W, int row0, int rows, int qg_given,
+             DevStatus* st) {
+  using P = Pattern<NF>;
+  constexpr int NP = P::NP;
+  constexpr int NT = kWinTX * kWinTY;
+  extern __shared__ unsigned long long win_lo[];  // [kWinCells] low words, then [kWinCells] high words
+  unsigned long long* win_hi = win_lo + kWinCells;
+  __shared__ int box[4];                          // x0, -x1, y0, -y1
+  const int lane = threadIdx.x, tid = threadIdx.y * kWinTX + lane;
+  const int x = blockIdx.x * kWinTX + lane;
+  const int y = blockIdx.y * kWinTY + threadIdx.y;
+  const bool in = x < W && y < rows;
+  int a0[4];
+  unsigned th[4];
+  const u128 g = scatter_pixel<NF>(cov, kind, gout, ldg, H, W, R, row0, x, y, in, qg_given, st, a0, th);
+  const int p32 = (int)pitch;
+  const int cx = x + R, cy = y + R;  // the pixel in padded coordinates
+  // bounding box of the samples of the block's pixels: d1 = (1, 0),
+  // d2 = (1, 1), d3 = (0, 1), d4 = (-1, 1)
+  if (tid == 0) box[0] = box[1] = box[2] = box[3] = INT_MAX;
+  __syncthreads();
+  int bx0 = INT_MAX, bx1 = INT_MAX, by0 = INT_MAX, by1 = INT_MAX;  // x0, -x1, y0, -y1
+  if (in) {
+    bx0 = cx + pos_lo<NF>(a0[0]) + pos_lo<NF>(a0[1]) - pos_hi(a0[3]);
+    bx1 = -(cx + pos_hi(a0[0]) + pos_hi(a0[1]) - pos_lo<NF>(a0[3]));
+    by0 = cy + pos_lo<NF>(a0[1]) + pos_lo<NF>(a0[2]) + pos_lo<NF>(a0[3]);
+    by1 = -(cy + pos_hi(a0[1]) + pos_hi(a0[2]) + pos_hi(a0[3]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    bx0 = min(bx0, __shfl_xor_sync(0xffffffffu, bx0, o));
+    bx1 = min(bx1, __shfl_xor_sync(0xffffffffu, bx1, o));
+    by0 = min(by0, __shfl_xor_sync(0xffffffffu, by0, o));
+    by1 = min(by1, __shfl_xor_sync(0xffffffffu, by1, o));
+  }
+  if (lane == 0 && bx0 != INT_MAX) {
+    atomicMin(&box[0], bx0);
+    atomicMin(&box[1], bx1);
+    atomicMin(&box[2], by0);
+    atomicMin(&box[3], by1);
+  }
+  __syncthreads();
+  if (box[0] == INT_MAX) return;  // no pixel of the block in the image (uniform)
+  const int X0 = box[0], X1 = -box[1], Y0 = box[2], Y1 = -box[3];
+  const int Ww = X1 - X0 + 1, band = kWinCells / Ww;
+  // each direction's weights are 1024 base_i + th diff_i: per coefficient c
+  // one product t = th c and the shift u = 1024 c give all of its samples
+  const u128 u4 = g << 10, t4 = mul_small(g, th[3]);
+  const bool live = in && g != 0;
+  if (band < 1 || (Y1 - Y0 + band) / band > kWinMaxPasses) {  // direct adds into G
+    if (live)
+      deposit_samples<NF>(reinterpret_cast<unsigned long long*>(G), 2 * p32, 2, 1, INT_MAX / 2, cy, cx,
+                          u4, t4, a0, th);
+    return;
+  }
+  for (int Yb = Y0; Yb <= Y1; Yb += band) {
+    const int nr = min(band, Y1 - Yb + 1), ncell = nr * Ww;
+    for (int c = tid; c < ncell; c += NT) {
+      win_lo[c] = 0ull;
+      win_hi[c] = 0ull;
+    }
+    __syncthreads();
+    if (live) deposit_samples<NF>(win_lo, Ww, 1, kWinCells, nr, cy - Yb, cx - X0, u4, t4, a0, th);
+    __syncthreads();
+    // the band into G: low words first, then the high words with carries
+    constexpr int KF = 4;
+    for (int c0 = tid; c0 < ncell; c0 += KF * NT) {
+      unsigned long long old[KF], lo[KF], hi[KF];
+      unsigned long long* q[KF];
+#pragma unroll
+      for (int k = 0; k < KF; ++k) {
+        const int c = c0 + k * NT;
+        lo[k] = hi[k] = 0ull;
+        q[k] = nullptr;
+        if (c < ncell) {
+          lo[k] = win_lo[c];
+          hi[k] = win_hi[c];
+          const int r = c / Ww;
+          q[k] = reinterpret_cast<unsigned long long*>(G + (long long)(Yb + r) * pitch + X0 + (c - r * Ww));
+        }
+        old[k] = lo[k] ? atomicAdd(q[k], lo[k]) : 0ull;
+      }
+#pragma unroll
+      for (int k = 0; k < KF; ++k) {
+        const unsigned long long h = hi[k] + ((old[k] + lo[k] < old[k]) ? 1ull : 0ull);
+        if (h) atomicAdd(q[k] + 1, h);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -260,15 +354,23 @@ cudaError_t bsf_launch_jacobian_vjp(const float* gout, long long ldg, const floa
 cudaError_t bsf_launch_scatter_d2(int n, void* G, long long pitch, int R, const float* cov,
                                   int cov_kind, const float* gout, long long ldg, int H, int W,
                                   int row0, int rows, int qg, DevStatus* st, cudaStream_t s) {
-  const dim3 block(32, 4), grid((W + 31) / 32, (rows + 3) / 4);
+  const dim3 block(kWinTX, kWinTY), grid((W + kWinTX - 1) / kWinTX, (rows + kWinTY - 1) / kWinTY);
+  const size_t smem = 2 * kWinCells * sizeof(unsigned long long);
+  static bool attr_set[2] = {false, false};
+  if (n != 1 && n != 2) return cudaErrorInvalidValue;
+  if (!attr_set[n - 1]) {
+    const cudaError_t e = n == 1
+        ? cudaFuncSetAttribute(k_scatter_d2<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+        : cudaFuncSetAttribute(k_scatter_d2<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set[n - 1] = true;
+  }
   if (n == 1)
-    k_scatter_d2<1><<<grid, block, 0, s>>>((u128*)G, pitch, R, cov, cov_kind, gout, ldg, H, W, row0, rows, qg,
-                                           st);
-  else if (n == 2)
-    k_scatter_d2<2><<<grid, block, 0, s>>>((u128*)G, pitch, R, cov, cov_kind, gout, ldg, H, W, row0, rows, qg,
-                                           st);
+    k_scatter_d2<1><<<grid, block, smem, s>>>((u128*)G, pitch, R, cov, cov_kind, gout, ldg, H, W, row0, rows,
+                                              qg, st);
   else
-    return cudaErrorInvalidValue;
+    k_scatter_d2<2><<<grid, block, smem, s>>>((u128*)G, pitch, R, cov, cov_kind, gout, ldg, H, W, row0, rows,
+                                              qg, st);
   return cudaGetLastError();
 }
 

@@ -285,6 +285,44 @@ def test_image_gradient_bit_exact(n, boundary, kind):
     np.testing.assert_array_equal(gimg.cpu().numpy(), ref)
 
 
+def _window_case_field(case, H, W):
+    if case == "one_pass":     # sigma 0.5-2: every block's samples fit one window
+        return wl.random_cov_field(H, W, seed=31, sigma_range=(0.5, 2.0), rho_range=(1.0, 2.0))
+    if case == "row_bands":    # sigma 12-15: windows of several row bands
+        return wl.random_cov_field(H, W, seed=33, sigma_range=(12.0, 15.0), rho_range=(1.0, 2.0))
+    s2 = np.float32(27.0 ** 2)  # one anisotropic sigma ~ 27: more bands than allowed, direct adds
+    return np.stack([np.full((H, W), s2 * np.float32(1.3)), np.full((H, W), s2 * np.float32(0.2)),
+                     np.full((H, W), s2)]).astype(np.float32)
+
+
+@pytest.mark.parametrize("case,H,W", [("one_pass", 24, 70), ("row_bands", 8, 36), ("direct", 8, 36)])
+def test_image_gradient_sample_windows(case, H, W):
+    # the scatter sums a block's samples in a shared window before adding it
+    # to the global sums: small scales fit one window pass, larger ones take
+    # several row bands, the largest fall back to direct global adds; every
+    # regime gives the oracle's adjoint bit for bit (ragged image sizes)
+    import torch
+    from oracle.rounding import rn_f32_int
+    n, boundary = 2, kernels.SYMMETRIC
+    planes = _window_case_field(case, H, W)
+    gout = wl.uniform_image(H, W, seed=32, lo=-1, hi=1).astype(np.float32)
+    f = _filter(H, W, n, boundary, -1, 2, 0)
+    tc = torch.from_numpy(planes).cuda()
+    f.plan(tc)
+    gimg, _ = f.backward(torch.from_numpy(gout).cuda(), tc, want_gimg=True, want_gcov=False)
+    torch.cuda.synchronize()
+    assert f.status() == 0
+    R = oracle_R(planes, n, "d2", kind=0, gpu=f.info().R)
+    qg = cn.grad_frac_bits_d2(float(np.abs(gout).max()))
+    pix = [(y, x) for y in range(H) for x in range(W)]
+    recs = cn.filter_d2_direct(np.zeros((H, W), dtype=np.int64), planes, n, boundary, pix, kind=0, R=R)
+    gq = {p: cn.quantize_weight_d2(float(gout[p]), recs[p]["M"], qg) for p in pix}
+    acc = cn.adjoint_d2_acc(gq, planes, n, boundary, (H, W), kind=0, R=R)
+    ref = np.array([[np.float32(rn_f32_int(acc[y, x]) * np.float32(2.0 ** -qg)) for x in range(W)]
+                    for y in range(H)], dtype=np.float32)
+    np.testing.assert_array_equal(gimg.cpu().numpy(), ref)
+
+
 def test_autograd_image_and_parameter_gradients():
     import torch
     from paper_1109_5114_gb300 import bsf
