@@ -531,7 +531,10 @@ def run_gpu(args):
     value = world * px * args.steps / (total_ms * 1e-3) / 1e6
     fp64_form["value"] = round(world * px * args.steps / (f64_ms * 1e-3) / 1e6, 2)
     fp64_form["unit"] = UNIT
-    fp64_form["speedup_of_fixed_point"] = round(value / fp64_form["value"], 3)
+    # an accuracy comparison: at the float64 form's error no speed ratio
+    # at equal accuracy exists, so only its time is reported beside it
+    fp64_form["comparison"] = ("accuracy: the float64 running sums lose the output's digits "
+                               "(max_abs_err) while the fixed-point sums are exact; not a speed-up")
     algorithm1["value"] = round(world * px * args.steps / (tp_ms * 1e-3) / 1e6, 2)
     algorithm1["unit"] = UNIT
     for d, ms in ((second, second_ms), (pair, pair_ms)):
