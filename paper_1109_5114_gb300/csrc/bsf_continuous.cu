@@ -32,31 +32,6 @@ __device__ __forceinline__ int grad_q128(unsigned mbits) {
   return q < 0 ? 0 : (q > 126 ? 126 : q);
 }
 
-// 128-bit atomic add from two 64-bit ones: the low word's old value tells
-// this thread whether its addition carried, and the high word receives the
-// high part plus that carry.  The low word then holds the low 64 bits of the
-// sum and the high word every carry out of it, so the pair is the exact sum
-// modulo 2^128 whatever the order of the additions.
-__device__ __forceinline__ void atomic_add_u128(u128* p, u128 v) {
-  unsigned long long* q = reinterpret_cast<unsigned long long*>(p);
-  const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
-  const unsigned long long old = atomicAdd(q, lo);
-  const unsigned long long h = hi + ((old + lo < old) ? 1ull : 0ull);
-  if (h) atomicAdd(q + 1, h);
-}
-
-__device__ __forceinline__ u128 mul_signed(u128 x, int v) {
-  return v >= 0 ? mul_small(x, (unsigned)v) : (u128)0 - mul_small(x, (unsigned)(-v));
-}
-
-// Interpolation weights of one direction (see the stencil): n = 2:
-// 1024 - th, th, -2048, th, 1024 - th; n = 1: 1024 - th, th, -th, th - 1024.
-template <int NF> __device__ __forceinline__ int tap_weight(unsigned th, int i) {
-  const int t = (int)th;
-  if (NF == 2) return i == 0 || i == 4 ? 1024 - t : (i == 2 ? -2048 : t);
-  return i == 0 ? 1024 - t : (i == 1 ? t : (i == 2 ? -t : t - 1024));
-}
-
 // Adjoint of the continuous-step taps: each pixel adds g(p) times the
 // product of its four interpolation weights at each of its samples, g(p) =
 // RNE(RN32(RN32(gout 2^qg) / RN32(M))) the quantised normalised weight.
