@@ -991,8 +991,9 @@ def run_diff(args):
                 "phases_ms": {k: round(ms / max(c, 1), 5) for k, (ms, c) in prof_fw.items() if c}},
         "phases_ms": {k: round(v[0], 5) for k, v in per_phase.items()},
         # over the timed steps, per image: rows, 3 x (agg + apply), stencil,
-        # vjp; backward: absmax, scatter, 3 x (agg + apply), suffix rows, 2 folds
-        "gpu_launches": args.steps * 8 * ((1 + 3 * 2 + 1 + 1) + (1 + 1 + 3 * 2 + 1 + 2)),
+        # vjp; backward: absmax, scatter, 3 x (agg + apply), suffix rows, the
+        # fused extension fold
+        "gpu_launches": args.steps * 8 * ((1 + 3 * 2 + 1 + 1) + (1 + 1 + 3 * 2 + 1 + 1)),
         "loss": loss,
         "clocks": clocks,
     }
