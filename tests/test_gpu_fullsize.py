@@ -12,6 +12,13 @@ q as stated).
 * 8192^2 uint8 blob image, n = 3, smooth random field (sigma 2-32 px, rho 1-3),
   uint128 running sums, q = 0: sampled pixels bit-exact against the exact
   direct correlation.
+* The image gradients of the two benchmarked backward passes: the 2048^2
+  workload (integer steps, 64-bit adjoint sums) on the whole image against
+  the oracle's transposed pipeline, and one 1024^2 image of the
+  differentiation workload (continuous steps, 128-bit adjoint sums, the
+  shared-memory window scatter) with gout nonzero on two windows (one at a
+  corner, where the extension folds, one inside) against the oracle's direct
+  adjoint of those pixels' kernels.
 """
 import numpy as np
 import pytest
@@ -91,6 +98,77 @@ def test_spacevariant_2048_bit_exact_whole_image():
     scale = float(np.abs(ref).max())
     for p in pix:
         assert abs(float(out[p]) - exact[p]) <= 1e-5 * max(abs(exact[p]), 1e-3 * scale)
+
+
+def test_spacevariant_2048_backward_bit_exact_whole_image():
+    """The forward + backward configuration of the benchmark (automatic q,
+    64-bit context, f.backward): the image gradient of a seeded gout, every
+    pixel bit-exact against the oracle's transposed running-sum pipeline."""
+    import torch
+    from oracle import backward
+    from paper_1109_5114_gb300 import bsf
+    H = W = 2048
+    img = wl.blob_image(H, W, seed=0)
+    cov = wl.diagonal_ramp_cov_field(H, W)
+    gout = wl.uniform_image(H, W, seed=77, lo=-1, hi=1).astype(np.float32)
+    f = bsf.BoxSplineFilter(H, W, 2, "symmetric", precision=1, frac_bits=-1,
+                            value_bound=float(np.abs(img).max()))
+    tc = torch.from_numpy(cov).cuda()
+    f.plan(tc)
+    f.filter(torch.from_numpy(img).cuda(), tc)
+    gimg, _ = f.backward(torch.from_numpy(gout).cuda(), tc)
+    torch.cuda.synchronize()
+    assert f.status() == 0
+    R = oracle_R(cov, 2, gpu=f.info().R)
+    got = gimg.cpu().numpy()
+    f.close()
+    L, _ = params.integer_steps(cov[0], cov[1], cov[2], 2)
+    qg = backward.grad_frac_bits(float(np.abs(gout).max()))
+    np.testing.assert_array_equal(got, backward.adjoint_modular(gout, L, 2, kernels.SYMMETRIC, qg, R))
+
+
+def test_differentiation_image_gradient_full_size_windows():
+    """One 1024^2 image of the differentiation workload (the bench's context:
+    uint128, continuous steps, log-parameter fields): gout nonzero on a
+    12 x 24 window at the top-left corner and one inside, zero elsewhere, so
+    that the oracle's direct adjoint stays affordable while the scatter runs
+    over the whole image with the workload's fields; every pixel of the
+    image gradient bit-exact."""
+    import math
+    import torch
+    import bench
+    from oracle import continuous as cn
+    from oracle.rounding import rn_f32_int
+    from paper_1109_5114_gb300 import bsf
+    side = 1024
+    imgs, fields, _ = bench.diff_inputs(1, side)
+    fl = fields[0]
+    u = wl.uniform_image(side, side, seed=78, lo=-1, hi=1).astype(np.float32)
+    gout = np.zeros((side, side), np.float32)
+    for win in ((slice(0, 12), slice(0, 24)), (slice(500, 512), slice(600, 624))):
+        gout[win] = u[win]
+    f = bsf.BoxSplineFilter(side, side, 2, "symmetric", precision=bsf.BSF_FIX128, frac_bits=-1,
+                            value_bound=float(np.abs(imgs[0]).max()), step_rule=bsf.BSF_STEP_D2,
+                            cov_kind=bsf.BSF_COV_LOGSIG_THETA_LOGRHO)
+    tf = torch.from_numpy(fl).cuda()
+    f.plan(tf)
+    gimg, _ = f.backward(torch.from_numpy(gout).cuda(), tf, want_gimg=True, want_gcov=False)
+    torch.cuda.synchronize()
+    assert f.status() == 0
+    R = oracle_R(fl, 2, "d2", kind=1, gpu=f.info().R)
+    got = gimg.cpu().numpy()
+    f.close()
+    qg = cn.grad_frac_bits_d2(float(np.abs(gout).max()))
+    gq = {}
+    for y, x in zip(*np.nonzero(gout)):
+        Hs = cn._pixel_steps(fl, 1, 2, int(y), int(x), R)[0]
+        M = math.prod(cn.line_data(h, 2)[3] for h in Hs)  # the mass of the pixel's kernel
+        gq[(int(y), int(x))] = cn.quantize_weight_d2(float(gout[y, x]), M, qg)
+    acc = cn.adjoint_d2_acc(gq, fl, 2, kernels.SYMMETRIC, (side, side), kind=1, R=R)
+    ref = np.zeros((side, side), np.float32)
+    for y, x in zip(*np.nonzero(acc != 0)):
+        ref[y, x] = np.float32(rn_f32_int(acc[y, x]) * np.float32(2.0 ** -qg))
+    np.testing.assert_array_equal(got, ref)
 
 
 def test_precision_8192_u8_uint128_sampled_bit_exact():
