@@ -63,6 +63,42 @@ def test_batch_bit_exact_all_modes(n):
     bf.close()
 
 
+def test_batch64_full_size_persistent_graph_sampled_images():
+    """The benchmark's batch (64 images, sides log-uniform in [128, 2048],
+    seed 1; sigma 1-24 px; n = 2), planned with the autotuner and run as the
+    bench's headline mode (one persistent launch replayed from a CUDA graph):
+    the largest image, the smallest and six seeded others bit-exact on the
+    whole image against the oracle (the batch's one q, each image's R)."""
+    import torch
+    from paper_1109_5114_gb300 import bsf
+    sizes = wl.batch_sizes_loguniform(64, seed=1, lo=128, hi=2048)
+    imgs, covs = [], []
+    for i, (h, w) in enumerate(sizes):
+        imgs.append(wl.blob_image(h, w, seed=1000 + i))
+        covs.append(wl.random_cov_field(h, w, seed=2000 + 3 * i, sigma_range=(1.0, 24.0), rho_range=(1.0, 3.0)))
+    vmax = max(float(np.abs(a).max()) for a in imgs)
+    d_imgs = [torch.from_numpy(a).cuda() for a in imgs]
+    d_covs = [torch.from_numpy(c).cuda() for c in covs]
+    d_outs = [torch.full(a.shape, float("nan"), dtype=torch.float32, device="cuda") for a in imgs]
+    bf = bsf.BatchFilter(2, "symmetric", frac_bits=-1, value_bound=vmax)
+    torch.cuda.synchronize()
+    info = bf.plan(d_imgs, d_covs, d_outs, autotune=True)
+    mass = max(config.mass_bound(c, 2) for c in covs)
+    q = max(config.auto_frac_bits(vmax, mass, 64), 0)
+    assert info.frac_bits == q
+    bf.run(bsf.BSF_BATCH_PERSISTENT | bsf.BSF_BATCH_GRAPH)
+    bf.run(bsf.BSF_BATCH_PERSISTENT | bsf.BSF_BATCH_GRAPH)
+    assert bf.status() == 0
+    px = np.array([h * w for h, w in sizes])
+    rng = np.random.default_rng(9)
+    pick = {int(px.argmax()), int(px.argmin())} | {int(i) for i in rng.choice(64, 6, replace=False)}
+    for i in sorted(pick):
+        ref = modular.filter_modular(imgs[i], covs[i], 2, 2, q=q, bits=64, out_dtype=np.float32,
+                                     R=config.padding(covs[i], 2))
+        np.testing.assert_array_equal(d_outs[i].cpu().numpy(), ref)
+    bf.close()
+
+
 def _small_batch(n, seed0=0, count=7):
     import torch
     sizes = wl.batch_sizes_loguniform(count, seed=5 + seed0, lo=20, hi=260)
