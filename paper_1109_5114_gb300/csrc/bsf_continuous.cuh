@@ -134,8 +134,13 @@ __device__ __forceinline__ float to_f32(u128 a) { return bsf_rn32((i128)a); }
 
 enum { kOut = 0, kOutJac = 1, kVjp = 2 };
 
+// Resident blocks of 128 threads per SM asked of the register allocator.
+// 128-bit sums: the forward at four (128 registers); with the derivative
+// sums at five (96 registers, a few hundred bytes spilled to L1), measured
+// 0.74-0.79 against 0.79-0.85 ms per 1024^2 image at four; the forward at
+// five or six is slower.
 template <typename T, int NF, int MODE> struct D2Occ {
-  static constexpr int value = sizeof(T) == 8 ? (MODE == kOut ? 6 : 4) : (MODE == kOut ? 4 : 4);
+  static constexpr int value = sizeof(T) == 8 ? (MODE == kOut ? 6 : 4) : (MODE == kOut ? 4 : 5);
 };
 
 template <typename T, int NF, typename Out, int MODE>
