@@ -54,8 +54,10 @@ __device__ __forceinline__ void row_scan_segments(int Wp, Load&& load, Store&& s
   constexpr int VP = V + 1;  // padded stride of the store transpose (fewer bank conflicts)
   // raw storage: the element types with constructors are written before read
   __shared__ __align__(16) unsigned char s_end_raw[NW * NF * sizeof(T)];
+  __shared__ __align__(16) unsigned char s_cin_raw[(NW + 1) * NF * sizeof(T)];
   __shared__ __align__(16) unsigned char s_tr_raw[NW * 32 * VP * sizeof(T)];
   T(*s_end)[NF] = reinterpret_cast<T(*)[NF]>(s_end_raw);
+  T(*s_cin)[NF] = reinterpret_cast<T(*)[NF]>(s_cin_raw);
   T(*s_tr)[32 * VP] = reinterpret_cast<T(*)[32 * VP]>(s_tr_raw);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   T carry[NF];  // fold values just before the pass (uniform across the block)
@@ -84,24 +86,38 @@ __device__ __forceinline__ void row_scan_segments(int Wp, Load&& load, Store&& s
       if (lane == 31) s_end[wid][f] = incl;  // fold f at the segment's last element
     }
     __syncthreads();
-    // carry-in state of this warp's segment, and the block's state after the pass
+    // carry-in state of each warp's segment, and the block's state after the
+    // pass: the chain over the warps runs in warp 0 alone (lane w keeps warp
+    // w's carry-in) and reaches the others through shared memory
     T cin[NF], cnext[NF];
+    if (wid == 0) {
 #pragma unroll
-    for (int f = 0; f < NF; ++f) cnext[f] = carry[f];
-    for (int w = 0; w < NW; ++w) {
-      if (w == wid) {
+      for (int f = 0; f < NF; ++f) cnext[f] = carry[f];
+      for (int w = 0; w < NW; ++w) {
+        if (w == lane) {
 #pragma unroll
-        for (int f = 0; f < NF; ++f) cin[f] = cnext[f];
+          for (int f = 0; f < NF; ++f) s_cin[w][f] = cnext[f];
+        }
+        T e[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          e[f] = s_end[w][f];
+#pragma unroll
+          for (int k = 0; k <= f; ++k) e[f] += bsf_mul_int(cnext[k], binom_small(SEG - 1 + f - k, f - k));
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) cnext[f] = e[f];
       }
-      T e[NF];
+      if (lane == 0) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        e[f] = s_end[w][f];
-#pragma unroll
-        for (int k = 0; k <= f; ++k) e[f] += bsf_mul_int(cnext[k], binom_small(SEG - 1 + f - k, f - k));
+        for (int f = 0; f < NF; ++f) s_cin[NW][f] = cnext[f];
       }
+    }
+    __syncthreads();
 #pragma unroll
-      for (int f = 0; f < NF; ++f) cnext[f] = e[f];
+    for (int f = 0; f < NF; ++f) {
+      cin[f] = s_cin[wid][f];
+      cnext[f] = s_cin[NW][f];
     }
     // n-th fold += a(i) = sum_k cin_k C(i + n - 1 - k, n - 1 - k), i = position in
     // the segment; a is a polynomial of degree n - 1 in i, stepped by its forward
