@@ -674,9 +674,9 @@ static int filter_impl(bsf_t h, const void* img, int dtype, long long ld, const 
       e = bsf_launch_stencil_sampled(h->precision, h->dirset, h->S, h->S2, h->pitch, h->R, cov, cov_kind, h->H,
                                      h->W, row0, rows, h->S_q, out, out_dtype, ldo, h->st, h->stream);
     else if (h->dirset == BSF_DIRS_CARTESIAN)
-      e = bsf_launch_stencil_d1(h->precision, h->n, h->S, h->pitch, h->R, cov, cov_kind,
-                                h->step_rule, h->H, h->W, row0, rows, h->S_q, out, out_dtype, ldo,
-                                h->st, h->stream);
+      e = bsf_launch_stencil_d1_ex(h->precision, h->n, h->S, h->pitch, h->R, cov, cov_kind,
+                                   h->step_rule, h->H, h->W, row0, rows, h->S_q, out, out_dtype, ldo,
+                                   h->st, h->stream, img != nullptr && !h->profiling);
     else
       e = bsf_launch_stencil_sets(h->precision, h->n, h->dirset, h->S, h->S2, h->pitch, h->R, cov,
                                   cov_kind, h->step_rule, h->H, h->W, row0, rows, h->S_q, out,

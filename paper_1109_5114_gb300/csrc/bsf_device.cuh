@@ -11,6 +11,15 @@
 typedef unsigned __int128 u128;
 typedef __int128 i128;
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while the kernel before it on the stream is still
+// running; bsf_grid_dep_wait() blocks until that kernel has completed and its
+// writes are visible (a no-op when the launch had no such dependency), and
+// bsf_grid_dep_launch() lets the dependent kernel's blocks be scheduled once
+// every block of this kernel has called it or exited.
+__device__ __forceinline__ void bsf_grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void bsf_grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ void bsf_set_error(DevStatus* st, int code) {
   atomicCAS(&st->err, 0, code);
 }

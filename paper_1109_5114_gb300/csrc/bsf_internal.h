@@ -150,6 +150,13 @@ cudaError_t bsf_launch_stencil_d1(int prec, int n, const void* S, long long pitc
                                   const float* cov, int cov_kind, int rule, int H, int W, int row0,
                                   int rows, int q, void* out, int out_dtype, long long ldo,
                                   DevStatus* st, cudaStream_t s);
+// The same, and with after_scans the kernel just before on the stream is the
+// last kernel of these running sums: the stencil then starts as its
+// programmatic dependent (the step solve overlaps it; the gathers wait).
+cudaError_t bsf_launch_stencil_d1_ex(int prec, int n, const void* S, long long pitch, int R,
+                                     const float* cov, int cov_kind, int rule, int H, int W, int row0,
+                                     int rows, int q, void* out, int out_dtype, long long ldo,
+                                     DevStatus* st, cudaStream_t s, bool after_scans);
 
 // Continuous-step stencil (BSF_STEP_D2, n = 1, 2; BSF_FIX64 / BSF_FIX128).
 // mode 0: out only; 1: out and the Jacobian planes jac[c * jac_plane + y * ldj + x]

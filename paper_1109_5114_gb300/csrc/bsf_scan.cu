@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(kRowThreads)
 k_scan_rows(const In* __restrict__ img, long long ld, int H, int W, int R, int row0, int boundary,
             float scale_f, int q, T* __restrict__ S, long long pitch, int Hp, int Wp,
             DevStatus* st) {
+  bsf_grid_dep_launch();  // the first vertical reduction may be scheduled (it waits for this grid)
   float amax = 0.f;
   bool all_ok = true;
   for (int yp = blockIdx.x; yp < Hp; yp += gridDim.x)
@@ -65,11 +66,15 @@ int rows_grid(int Hp) {
 // times the threads of one line per thread, for SPLIT times the loads in
 // flight.
 constexpr int kAggSplit = 2;
+constexpr bool kScanPdl = true;
 
 template <typename T, int NF, int SKEW, bool REV, int SPLIT>
 __global__ void __launch_bounds__(128)
 k_vscan_agg(const T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, int Nu, int ch,
             T* __restrict__ agg) {
+  // a programmatic dependent of the kernel before it: wait for it to finish
+  bsf_grid_dep_launch();
+  bsf_grid_dep_wait();
   constexpr int LINES = 128 / SPLIT;
   // raw storage: the element types with constructors are written before read
   __shared__ __align__(16) unsigned char s_raw[SPLIT * NF * LINES * sizeof(T)];
@@ -121,6 +126,10 @@ template <typename T, int NF, int SKEW, bool REV>
 __global__ void __launch_bounds__(128)
 k_vscan_apply(T* __restrict__ S, long long pitch, int Hp, int Wp, int umin, int Nu, int ch,
               const T* __restrict__ agg) {
+  // a programmatic dependent of the reduction before it; the next kernel may
+  // start its own prologue (it waits for this grid)
+  bsf_grid_dep_launch();
+  bsf_grid_dep_wait();
   vscan_apply_body<T, NF, SKEW, REV>(S, pitch, Hp, Wp, umin, Nu, ch, agg, blockIdx.x, blockIdx.y);
 }
 
@@ -377,10 +386,22 @@ cudaError_t launch_v_t(T* S, long long pitch, int Hp, int Wp, int ch, T* agg, T*
   const int threads = 128;
   dim3 grid((Nu + threads - 1) / threads, nchunks);
   (void)carry;
-  k_vscan_agg<T, NF, SKEW, REV, kAggSplit><<<dim3((Nu + 128 / kAggSplit - 1) / (128 / kAggSplit), nchunks), threads, 0,
-                                             s>>>(S, pitch, Hp, Wp, umin, Nu, ch, agg);
-  k_vscan_apply<T, NF, SKEW, REV><<<grid, threads, 0, s>>>(S, pitch, Hp, Wp, umin, Nu, ch, agg);
-  return cudaGetLastError();
+  // both launched as programmatic dependents of the kernel before them (each
+  // waits for it at its start, so only the launch and the ramp-up overlap)
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = kScanPdl ? 1 : 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(threads);
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3((Nu + 128 / kAggSplit - 1) / (128 / kAggSplit), nchunks);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_vscan_agg<T, NF, SKEW, REV, kAggSplit>, (const T*)S, pitch, Hp, Wp,
+                                     umin, Nu, ch, agg);
+  if (e != cudaSuccess) return e;
+  cfg.gridDim = grid;
+  return cudaLaunchKernelEx(&cfg, k_vscan_apply<T, NF, SKEW, REV>, S, pitch, Hp, Wp, umin, Nu, ch, (const T*)agg);
 }
 
 template <typename T, int NF, bool REV>

@@ -17,31 +17,42 @@ k_stencil_d1(const T* __restrict__ S, long long pitch, int R, const float* __res
 template <typename T, int NF>
 cudaError_t launch_t(const T* S, long long pitch, int R, const float* cov, int kind, int rule, int H, int W,
                      int row0, int rows, int q, void* out, int out_dtype, long long ldo,
-                     DevStatus* st, cudaStream_t s) {
+                     DevStatus* st, cudaStream_t s, bool pdl) {
   dim3 block(32, 8);
   dim3 grid((W + 31) / 32, (rows + 7) / 8);
   const float sf = ldexpf(1.f, -q);
   const double sd = ldexp(1.0, -q);
+  // pdl: launched as a programmatic dependent of the last running-sum kernel,
+  // the kernel just before on the stream: its blocks solve their steps while
+  // that kernel finishes, then wait for it before the gathers
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   if (out_dtype == BSF_F32)
-    k_stencil_d1<T, NF, float><<<grid, block, 0, s>>>(S, pitch, R, cov, kind, rule, H, W, row0, rows,
-                                                      sf, sd, (float*)out, ldo, st);
-  else if (out_dtype == BSF_F64)
-    k_stencil_d1<T, NF, double><<<grid, block, 0, s>>>(S, pitch, R, cov, kind, rule, H, W, row0, rows,
-                                                       sf, sd, (double*)out, ldo, st);
-  else
-    return cudaErrorInvalidValue;
-  return cudaGetLastError();
+    return cudaLaunchKernelEx(&cfg, k_stencil_d1<T, NF, float>, S, pitch, R, cov, kind, rule, H, W, row0, rows,
+                              sf, sd, (float*)out, ldo, st);
+  if (out_dtype == BSF_F64)
+    return cudaLaunchKernelEx(&cfg, k_stencil_d1<T, NF, double>, S, pitch, R, cov, kind, rule, H, W, row0, rows,
+                              sf, sd, (double*)out, ldo, st);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-cudaError_t bsf_launch_stencil_d1(int prec, int n, const void* S, long long pitch, int R,
-                                  const float* cov, int cov_kind, int rule, int H, int W, int row0, int rows,
-                                  int q, void* out, int out_dtype, long long ldo, DevStatus* st,
-                                  cudaStream_t s) {
+cudaError_t bsf_launch_stencil_d1_ex(int prec, int n, const void* S, long long pitch, int R,
+                                     const float* cov, int cov_kind, int rule, int H, int W, int row0, int rows,
+                                     int q, void* out, int out_dtype, long long ldo, DevStatus* st,
+                                     cudaStream_t s, bool after_scans) {
 #define BSF_ST(T, NF)                                                                          \
   return launch_t<T, NF>((const T*)S, pitch, R, cov, cov_kind, rule, H, W, row0, rows, q, out, out_dtype, \
-                         ldo, st, s)
+                         ldo, st, s, after_scans)
   switch (prec * 10 + n) {
     case 51: BSF_ST(uint32_t, 1);
     case 52: BSF_ST(uint32_t, 2);
@@ -62,6 +73,14 @@ cudaError_t bsf_launch_stencil_d1(int prec, int n, const void* S, long long pitc
   }
 #undef BSF_ST
   return cudaErrorInvalidValue;
+}
+
+cudaError_t bsf_launch_stencil_d1(int prec, int n, const void* S, long long pitch, int R,
+                                  const float* cov, int cov_kind, int rule, int H, int W, int row0, int rows,
+                                  int q, void* out, int out_dtype, long long ldo, DevStatus* st,
+                                  cudaStream_t s) {
+  return bsf_launch_stencil_d1_ex(prec, n, S, pitch, R, cov, cov_kind, rule, H, W, row0, rows, q, out, out_dtype,
+                                  ldo, st, s, false);
 }
 
 namespace {

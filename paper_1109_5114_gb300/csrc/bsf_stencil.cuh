@@ -223,6 +223,9 @@ __device__ __forceinline__ void stencil_d1_body(const T* __restrict__ S, const T
   else
     in_reach = bsf_solve::pixel_steps_set(DS, C11, C12, C22, NF, rule, R, L, flags, reach, second);
   count_pixel_flags(flags, in_reach, st);
+  // the step solve above reads only the field; the running sums may still be
+  // in the making when this kernel was launched as a programmatic dependent
+  bsf_grid_dep_wait();
   const int L1 = L[0], L2 = L[1], L3 = L[2], L4w = L[3];
   // element strides of d1 = (1,0), d2 = (1,1), d3 = (0,1), d4 = (-1,1), or
   // of e1 = (2,1), e2 = (1,2), e3 = (-1,2), e4 = (-2,1)
