@@ -1178,7 +1178,7 @@ int bsf_filter_backward(bsf_t h, const float* gout, long long ldg, const float* 
     e = bsf_launch_gabsmax(gout, ldg, h->H, h->W, h->st, h->stream);
     if (e == cudaSuccess)
       e = bsf_launch_scatter_d1(h->n, be, h->G, h->pitch, h->R, cov, cov_kind, h->step_rule, gout, ldg, h->H,
-                                h->W, 0, h->H, -1, h->st, h->stream);
+                                h->W, 0, h->H, -1, h->st, h->stream, true);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "backward scatter");
   {

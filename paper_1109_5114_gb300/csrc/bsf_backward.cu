@@ -25,6 +25,7 @@
 namespace {
 
 __global__ void k_gabsmax(const float* __restrict__ g, long long ld, int H, int W, DevStatus* st) {
+  bsf_grid_dep_launch();  // the scatter may solve its steps meanwhile (it waits for this grid)
   float m = 0.f;
   const long long HW = (long long)H * W;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < HW;
@@ -103,6 +104,11 @@ k_scatter_d1(T* __restrict__ G, long long pitch, int R,
     float C11, C12, C22;
     bsf_solve::load_cov(cov, kind, HW, i, C11, C12, C22);
     bsf_solve::pixel_steps(C11, C12, C22, NF, rule, R, L, flags, reach);
+  }
+  // the steps read only the field; max |gout| comes from the kernel before
+  // this one when it was launched as its programmatic dependent
+  bsf_grid_dep_wait();
+  if (in) {
     const int qg = qg_given >= 0 ? qg_given : (kWide ? grad_q_wide(st->max_absg_bits) : grad_q(st->max_absg_bits));
     T D = (T)(unsigned)(L[0] * L[1]) * (T)(unsigned)(L[2] * L[3]);
     const T D1 = D;
@@ -299,11 +305,23 @@ cudaError_t bsf_launch_gabsmax(const float* gout, long long ldg, int H, int W, D
 
 cudaError_t bsf_launch_scatter_d1(int n, int elem_bytes, void* G, long long pitch, int R, const float* cov,
                                   int cov_kind, int rule, const float* gout, long long ldg, int H,
-                                  int W, int row0, int rows, int qg, DevStatus* st, cudaStream_t s) {
-  dim3 block(32, 8), grid((W + 31) / 32, (rows + 7) / 8);
+                                  int W, int row0, int rows, int qg, DevStatus* st, cudaStream_t s,
+                                  bool after_absmax) {
   const int k = cov_kind;
+  // after_absmax: a programmatic dependent of the max |gout| reduction just
+  // before on the stream (the steps are solved while it finishes)
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = after_absmax ? 1 : 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((W + 31) / 32, (rows + 7) / 8);
+  cfg.blockDim = dim3(32, 8);
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
 #define BSF_SC(NF, T) \
-  k_scatter_d1<NF, T><<<grid, block, 0, s>>>((T*)G, pitch, R, cov, k, rule, gout, ldg, H, W, row0, rows, qg, st)
+  return cudaLaunchKernelEx(&cfg, k_scatter_d1<NF, T>, (T*)G, pitch, R, cov, k, rule, gout, ldg, H, W, row0, rows, \
+                            qg, st)
   if (elem_bytes == 8) {
     if (n == 1) BSF_SC(1, uint64_t); else if (n == 2) BSF_SC(2, uint64_t); else if (n == 3) BSF_SC(3, uint64_t);
     else return cudaErrorInvalidValue;

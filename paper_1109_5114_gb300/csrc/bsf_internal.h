@@ -72,7 +72,8 @@ cudaError_t bsf_launch_gabsmax(const float* gout, long long ldg, int H, int W, D
 // device maximum of |gout| (bsf_launch_gabsmax).
 cudaError_t bsf_launch_scatter_d1(int n, int elem_bytes, void* G, long long pitch, int R, const float* cov,
                                   int cov_kind, int rule, const float* gout, long long ldg, int H,
-                                  int W, int row0, int rows, int qg, DevStatus* st, cudaStream_t s);
+                                  int W, int row0, int rows, int qg, DevStatus* st, cudaStream_t s,
+                                  bool after_absmax = false);
 // Band fold: G's Hb padded rows (row 0 = image row row0 - R) folded by the
 // extension rule into image rows [a0, a1) as exact sums (acc: elements of
 // elem_bytes, two's complement, lda elements per row).
