@@ -84,7 +84,7 @@ __device__ __forceinline__ u128 scatter_pixel(const float* __restrict__ cov, int
 // to the direct global adds.  Shared words: low and high 64-bit planes of
 // 128-bit cells, the low add returning the old word for the carry.
 constexpr int kWinTX = 32, kWinTY = 8;
-constexpr int kWinCells = 4096;     // 64 KB: three blocks per SM
+constexpr int kWinCells = 4096;     // 64 KB: three blocks per SM (measured best of 2,048-12,288 cells)
 constexpr int kWinMaxPasses = 8;
 
 // Sample offsets along one direction: [lo, hi] (a0 >= -1).
