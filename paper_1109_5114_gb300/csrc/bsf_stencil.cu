@@ -18,8 +18,10 @@ template <typename T, int NF>
 cudaError_t launch_t(const T* S, long long pitch, int R, const float* cov, int kind, int rule, int H, int W,
                      int row0, int rows, int q, void* out, int out_dtype, long long ldo,
                      DevStatus* st, cudaStream_t s, bool pdl) {
-  dim3 block(32, 8);
-  dim3 grid((W + 31) / 32, (rows + 7) / 8);
+  // 32 x 4 pixels per block (0.2167 against 0.2188 ms per 2048^2 step with
+  // 32 x 8; 32 x 2 0.2171)
+  dim3 block(32, 4);
+  dim3 grid((W + 31) / 32, (rows + 3) / 4);
   const float sf = ldexpf(1.f, -q);
   const double sd = ldexp(1.0, -q);
   // pdl: launched as a programmatic dependent of the last running-sum kernel,
