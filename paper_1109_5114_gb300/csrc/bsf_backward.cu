@@ -206,6 +206,7 @@ __global__ void k_fold_x(const T* __restrict__ G, long long pitch, int Hp, int W
 __global__ void k_fold_xy_out(const unsigned long long* __restrict__ G, long long pitch, int H, int W,
                               int R, int boundary, float* __restrict__ gimg, long long ldo,
                               const DevStatus* st) {
+  bsf_grid_dep_wait();  // a programmatic dependent of the last suffix sums
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   if (x >= W || y >= H) return;
@@ -384,7 +385,15 @@ cudaError_t bsf_launch_fold(const void* G, long long pitch, int Hp, int H, int W
   (void)Hp;
   (void)Gx;
   dim3 blk(128);
-  k_fold_xy_out<<<dim3((W + 127) / 128, H), blk, 0, s>>>((const unsigned long long*)G, pitch, H, W, R,
-                                                          boundary, gimg, ldo, st);
-  return cudaGetLastError();
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((W + 127) / 128, H);
+  cfg.blockDim = blk;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_fold_xy_out, (const unsigned long long*)G, pitch, H, W, R, boundary, gimg,
+                            ldo, st);
 }

@@ -269,6 +269,7 @@ __device__ __forceinline__ void for_preimages128(int i, int N, int R, int bounda
 __global__ void k_fold_xy_out128(const u128* __restrict__ G, long long pitch, int H, int W, int R,
                                  int boundary, float* __restrict__ gimg, long long ldo,
                                  const DevStatus* st) {
+  bsf_grid_dep_wait();  // a programmatic dependent of the last suffix sums
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   if (x >= W || y >= H) return;
@@ -354,8 +355,14 @@ cudaError_t bsf_launch_fold128(const void* G, long long pitch, int Hp, int H, in
                                cudaStream_t s) {
   (void)Hp;
   (void)Gx;
-  dim3 blk(128);
-  k_fold_xy_out128<<<dim3((W + 127) / 128, H), blk, 0, s>>>((const u128*)G, pitch, H, W, R, boundary,
-                                                             gimg, ldo, st);
-  return cudaGetLastError();
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((W + 127) / 128, H);
+  cfg.blockDim = dim3(128);
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_fold_xy_out128, (const u128*)G, pitch, H, W, R, boundary, gimg, ldo, st);
 }

@@ -331,6 +331,10 @@ cudaError_t launch_lb_skew(int skew, T* S, long long pitch, int Hp, int Wp, T* a
 template <typename T, int NF, int V>
 __global__ void __launch_bounds__(kRowThreads)
 k_suffix_rows(T* __restrict__ S, long long pitch, int Wp) {
+  // a programmatic dependent of the kernel before it (waits for it here); the
+  // extension fold after it may be scheduled meanwhile
+  bsf_grid_dep_launch();
+  bsf_grid_dep_wait();
   // suffix sums: scan order runs from the row's end to its start
   T* row = S + (long long)blockIdx.x * pitch;
   row_scan_segments<T, NF, V>(Wp, [&](int xl) -> T { return row[Wp - 1 - xl]; },
@@ -445,15 +449,24 @@ cudaError_t bsf_launch_scan_rows(int prec, int n, const void* img, int dtype, lo
 
 namespace {
 template <typename T, int NF>
-void launch_suffix_t(void* S, long long pitch, int Hp, int Wp, cudaStream_t s) {
+cudaError_t launch_suffix_t(void* S, long long pitch, int Hp, int Wp, cudaStream_t s) {
   // elements per thread chosen like the forward row pass
-  if (Wp <= kRowThreads * 4) {
-    k_suffix_rows<T, NF, 4><<<Hp, kRowThreads, 0, s>>>((T*)S, pitch, Wp);
-  } else if constexpr (sizeof(T) > 8) {
-    k_suffix_rows<T, NF, 9><<<Hp, kRowThreads, 0, s>>>((T*)S, pitch, Wp);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(Hp);
+  cfg.blockDim = dim3(kRowThreads);
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  T* St = (T*)S;
+  if (Wp <= kRowThreads * 4) return cudaLaunchKernelEx(&cfg, k_suffix_rows<T, NF, 4>, St, pitch, Wp);
+  if constexpr (sizeof(T) > 8) {
+    return cudaLaunchKernelEx(&cfg, k_suffix_rows<T, NF, 9>, St, pitch, Wp);
   } else {
-    if (Wp <= kRowThreads * 9) k_suffix_rows<T, NF, 9><<<Hp, kRowThreads, 0, s>>>((T*)S, pitch, Wp);
-    else k_suffix_rows<T, NF, 12><<<Hp, kRowThreads, 0, s>>>((T*)S, pitch, Wp);
+    if (Wp <= kRowThreads * 9) return cudaLaunchKernelEx(&cfg, k_suffix_rows<T, NF, 9>, St, pitch, Wp);
+    return cudaLaunchKernelEx(&cfg, k_suffix_rows<T, NF, 12>, St, pitch, Wp);
   }
 }
 }  // namespace
@@ -461,15 +474,14 @@ void launch_suffix_t(void* S, long long pitch, int Hp, int Wp, cudaStream_t s) {
 cudaError_t bsf_launch_suffix_rows(int elem_bytes, int n, void* S, long long pitch, int Hp, int Wp,
                                    cudaStream_t s) {
   switch (elem_bytes * 10 + n) {
-    case 81: launch_suffix_t<uint64_t, 1>(S, pitch, Hp, Wp, s); break;
-    case 82: launch_suffix_t<uint64_t, 2>(S, pitch, Hp, Wp, s); break;
-    case 83: launch_suffix_t<uint64_t, 3>(S, pitch, Hp, Wp, s); break;
-    case 161: launch_suffix_t<u128, 1>(S, pitch, Hp, Wp, s); break;
-    case 162: launch_suffix_t<u128, 2>(S, pitch, Hp, Wp, s); break;
-    case 163: launch_suffix_t<u128, 3>(S, pitch, Hp, Wp, s); break;
+    case 81: return launch_suffix_t<uint64_t, 1>(S, pitch, Hp, Wp, s);
+    case 82: return launch_suffix_t<uint64_t, 2>(S, pitch, Hp, Wp, s);
+    case 83: return launch_suffix_t<uint64_t, 3>(S, pitch, Hp, Wp, s);
+    case 161: return launch_suffix_t<u128, 1>(S, pitch, Hp, Wp, s);
+    case 162: return launch_suffix_t<u128, 2>(S, pitch, Hp, Wp, s);
+    case 163: return launch_suffix_t<u128, 3>(S, pitch, Hp, Wp, s);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 size_t bsf_vscan_lb_bytes(int elem_bytes, int n, int Hp, int Wp, size_t* sync_bytes) {
